@@ -1,0 +1,711 @@
+/*
+ * skyrme_oracle.c -- plain FP64 CPU reference of the arrested Newton flow of
+ * the Skyrme model in sigma-model form (arXiv 2604.25876).
+ *
+ * TEST INFRASTRUCTURE ONLY: tests, the smoke check and the benchmark's
+ * CPU-baseline leg are its only users.  It is deliberately slow and literal:
+ * every formula is written the way the paper states it (nested sums, explicit
+ * Levi-Civita symbols), with no blocking, fusion or reordering.  Summations
+ * over the lattice are Neumaier-compensated per x-plane and then over planes,
+ * so the result does not depend on the number of OpenMP threads.
+ *
+ * Paper passages followed:
+ *   Section 2.1, Eq. "SkyrmeEnergy_phi"   energy density (e2, e4, e0)
+ *   Section 2.1, Eq. "B0_components"      baryon density
+ *   Section 3,   Eq. "Newton_flow"        second-order flow with projection
+ *   Section 3,   Eq. "Sigma model EL equations"  dE/dphi^A
+ *   Section 3,   first/second-derivative 4th-order stencils
+ *   Section 3,   arrest rule, normalisation after each update, vacuum box
+ *   Section 4.1  rational-map ansatz, Table 1 (B = 1 and B = 4 maps)
+ *   Section 4.2  product ansatz, Eq. "Product ansatz"
+ *   Section 5.6  virial V = integral of T_kk
+ *
+ * Readings where the paper is silent or ambiguous (each is a choice the CUDA
+ * library makes the same way):
+ *   - mixed derivative d_i d_j: tensor product of the first-derivative
+ *     stencil along i and along j (16 taps, radius 2);
+ *   - baryon density sign: B0 = -(1/12 pi^2) eps^{ijk} eps_{ABCD} phi^A
+ *     d_i phi^B d_j phi^C d_k phi^D with eps_{0123} = +1, so that the
+ *     hedgehog with f(0) = pi and the R(z) = z map has B = +1 as Table 1
+ *     states;
+ *   - the arrest compares the static energy of phi_n with that of phi_{n-1}
+ *     (strictly larger => velocity zeroed), the field is kept, and the update
+ *     is symplectic Euler: v += dt F, phi = normalise(phi + dt v);
+ *   - energies are h^3 times the sum over interior sites;
+ *   - delta is the largest |F| over interior sites;
+ *   - virial V = -E2 + E4 - 3 E0 (Derrick scaling of the three terms, which
+ *     equals the integral of T_kk of Eq. "Stress tensor" for static fields).
+ */
+#include "skyrme_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+static size_t site_index(const int n[3], int x, int y, int z)
+{
+    return (((size_t)x * (size_t)n[1]) + (size_t)y) * (size_t)n[2] + (size_t)z;
+}
+
+static int is_interior(const int n[3], int x, int y, int z)
+{
+    return x >= 2 && x <= n[0] - 3 && y >= 2 && y <= n[1] - 3 && z >= 2 &&
+           z <= n[2] - 3;
+}
+
+/* Neumaier (improved Kahan) running sum. */
+typedef struct { double s, c; } nsum;
+static void nsum_add(nsum *a, double v)
+{
+    double t = a->s + v;
+    if (fabs(a->s) >= fabs(v))
+        a->c += (a->s - t) + v;
+    else
+        a->c += (v - t) + a->s;
+    a->s = t;
+}
+static double nsum_get(const nsum *a) { return a->s + a->c; }
+
+/* ------------------------------------------------------------------------
+ * Section 3: fourth-order stencils, weights for offsets -2, -1, 0, +1, +2.
+ *   d_x phi_i   ~ ( phi_{i-2}/12 - 2 phi_{i-1}/3 + 2 phi_{i+1}/3 - phi_{i+2}/12 ) / h
+ *   d_xx phi_i  ~ ( -phi_{i-2}/12 + 4 phi_{i-1}/3 - 5 phi_i/2 + 4 phi_{i+1}/3
+ *                   - phi_{i+2}/12 ) / h^2
+ * ------------------------------------------------------------------------ */
+static const double FIRST[5] = {1.0 / 12.0, -2.0 / 3.0, 0.0, 2.0 / 3.0,
+                                -1.0 / 12.0};
+static const double SECOND[5] = {-1.0 / 12.0, 4.0 / 3.0, -5.0 / 2.0, 4.0 / 3.0,
+                                 -1.0 / 12.0};
+
+void orc_site_derivatives(const int n[3], double h, const double *phi, int x,
+                          int y, int z, double d1[3][4], double d2[3][4],
+                          double dm[3][4])
+{
+    const int unit[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    const int pair[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+    int i, A, k, l, p;
+
+    for (i = 0; i < 3; i++) {
+        for (A = 0; A < 4; A++) {
+            double s1 = 0.0, s2 = 0.0;
+            for (k = 0; k < 5; k++) {
+                int o = k - 2;
+                size_t s = site_index(n, x + o * unit[i][0], y + o * unit[i][1],
+                                      z + o * unit[i][2]);
+                s1 += FIRST[k] * phi[4 * s + A];
+                s2 += SECOND[k] * phi[4 * s + A];
+            }
+            d1[i][A] = s1 / h;
+            d2[i][A] = s2 / (h * h);
+        }
+    }
+    /* mixed derivative: first-derivative stencil along i applied to the
+     * first-derivative stencil along j (16 taps). */
+    for (p = 0; p < 3; p++) {
+        int a = pair[p][0], b = pair[p][1];
+        for (A = 0; A < 4; A++) {
+            double s = 0.0;
+            for (k = 0; k < 5; k++) {
+                for (l = 0; l < 5; l++) {
+                    int oa = k - 2, ob = l - 2;
+                    size_t q;
+                    if (FIRST[k] == 0.0 || FIRST[l] == 0.0) continue;
+                    q = site_index(n, x + oa * unit[a][0] + ob * unit[b][0],
+                                   y + oa * unit[a][1] + ob * unit[b][1],
+                                   z + oa * unit[a][2] + ob * unit[b][2]);
+                    s += FIRST[k] * FIRST[l] * phi[4 * q + A];
+                }
+            }
+            dm[p][A] = s / (h * h);
+        }
+    }
+}
+
+/* Levi-Civita symbols as explicit permutation lists. */
+static int perm_sign(const int *p, int len)
+{
+    int s = 1, i, j;
+    for (i = 0; i < len; i++)
+        for (j = i + 1; j < len; j++)
+            if (p[i] > p[j]) s = -s;
+    return s;
+}
+
+void orc_site_terms(const double phi[4], const double d1[3][4],
+                    const double d2[3][4], const double dm[3][4], double m,
+                    double G[4], double F[4], double dens[4])
+{
+    double H[3][3][4]; /* d_i d_j phi^A */
+    double a[3][3];    /* d_i phi . d_j phi */
+    double tra, Gphi, sumsq;
+    int i, j, k, A, B;
+
+    for (A = 0; A < 4; A++) {
+        H[0][0][A] = d2[0][A];
+        H[1][1][A] = d2[1][A];
+        H[2][2][A] = d2[2][A];
+        H[0][1][A] = H[1][0][A] = dm[0][A];
+        H[0][2][A] = H[2][0][A] = dm[1][A];
+        H[1][2][A] = H[2][1][A] = dm[2][A];
+    }
+    for (i = 0; i < 3; i++)
+        for (j = 0; j < 3; j++) {
+            double s = 0.0;
+            for (B = 0; B < 4; B++) s += d1[i][B] * d1[j][B];
+            a[i][j] = s;
+        }
+    tra = a[0][0] + a[1][1] + a[2][2]; /* (d_j phi^B)^2 */
+
+    /* Eq. "Sigma model EL equations":
+     * dE/dphi^A = -2 { d_ii phi^A [1 + (d_j phi^B)^2]
+     *                + d_i phi^A (d_ij phi^B d_j phi^B - d_jj phi^B d_i phi^B)
+     *                - d_ij phi^A (d_i phi^B d_j phi^B) + m^2 delta^A_0 } */
+    for (A = 0; A < 4; A++) {
+        double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+        for (i = 0; i < 3; i++) t1 += H[i][i][A] * (1.0 + tra);
+        for (i = 0; i < 3; i++) {
+            double inner = 0.0;
+            for (j = 0; j < 3; j++)
+                for (B = 0; B < 4; B++)
+                    inner += H[i][j][B] * d1[j][B] - H[j][j][B] * d1[i][B];
+            t2 += d1[i][A] * inner;
+        }
+        for (i = 0; i < 3; i++)
+            for (j = 0; j < 3; j++) t3 += H[i][j][A] * a[i][j];
+        G[A] = -2.0 * (t1 + t2 - t3 + (A == 0 ? m * m : 0.0));
+    }
+
+    /* Eq. "Newton_flow": phi_tt^A = -dE/dphi^A + (dE/dphi^B phi^B) phi^A */
+    Gphi = 0.0;
+    for (B = 0; B < 4; B++) Gphi += G[B] * phi[B];
+    for (A = 0; A < 4; A++) F[A] = -G[A] + Gphi * phi[A];
+
+    /* Eq. "SkyrmeEnergy_phi" split into its three terms */
+    sumsq = 0.0;
+    for (i = 0; i < 3; i++)
+        for (j = 0; j < 3; j++) sumsq += a[i][j] * a[i][j];
+    dens[0] = tra;
+    dens[1] = 0.5 * (tra * tra - sumsq);
+    dens[2] = 2.0 * m * m * (1.0 - phi[0]);
+
+    /* Eq. "B0_components" (sign reading in the file header) */
+    {
+        static const int p3[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2},
+                                     {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+        int p4[24][4], np4 = 0, q0, q1, q2, q3;
+        double s = 0.0;
+        for (q0 = 0; q0 < 4; q0++)
+            for (q1 = 0; q1 < 4; q1++)
+                for (q2 = 0; q2 < 4; q2++)
+                    for (q3 = 0; q3 < 4; q3++)
+                        if (q0 != q1 && q0 != q2 && q0 != q3 && q1 != q2 &&
+                            q1 != q3 && q2 != q3) {
+                            p4[np4][0] = q0;
+                            p4[np4][1] = q1;
+                            p4[np4][2] = q2;
+                            p4[np4][3] = q3;
+                            np4++;
+                        }
+        for (i = 0; i < 6; i++) {
+            int e3 = perm_sign(p3[i], 3);
+            for (k = 0; k < 24; k++) {
+                int e4 = perm_sign(p4[k], 4);
+                s += (double)(e3 * e4) * phi[p4[k][0]] * d1[p3[i][0]][p4[k][1]] *
+                     d1[p3[i][1]][p4[k][2]] * d1[p3[i][2]][p4[k][3]];
+            }
+        }
+        dens[3] = -s / (12.0 * M_PI * M_PI);
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * whole-lattice passes
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    nsum e[4];
+    double fmax;
+    int bad;
+} plane_acc;
+
+/* Per-site work for one x-plane; writes G/F/dens when requested. */
+static void plane_pass(const int n[3], double h, double m, const double *phi,
+                       int x, double *G, double *F, double *dens,
+                       plane_acc *acc)
+{
+    int y, z, q;
+    memset(acc, 0, sizeof(*acc));
+    for (y = 2; y <= n[1] - 3; y++)
+        for (z = 2; z <= n[2] - 3; z++) {
+            double d1[3][4], d2[3][4], dm[3][4], g[4], f[4], d[4], fn;
+            size_t s = site_index(n, x, y, z);
+            orc_site_derivatives(n, h, phi, x, y, z, d1, d2, dm);
+            orc_site_terms(&phi[4 * s], d1, d2, dm, m, g, f, d);
+            for (q = 0; q < 4; q++) {
+                if (G) G[4 * s + q] = g[q];
+                if (F) F[4 * s + q] = f[q];
+                if (dens) dens[4 * s + q] = d[q];
+                nsum_add(&acc->e[q], d[q]);
+                if (!isfinite(f[q]) || !isfinite(d[q])) acc->bad = 1;
+            }
+            fn = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2] + f[3] * f[3]);
+            if (fn > acc->fmax) acc->fmax = fn;
+        }
+}
+
+static void zero_boundary(const int n[3], double *arr)
+{
+    int x, y, z;
+    if (!arr) return;
+    for (x = 0; x < n[0]; x++)
+        for (y = 0; y < n[1]; y++)
+            for (z = 0; z < n[2]; z++)
+                if (!is_interior(n, x, y, z))
+                    memset(&arr[4 * site_index(n, x, y, z)], 0,
+                           4 * sizeof(double));
+}
+
+/* Sum the per-plane accumulators in plane order. */
+static void lattice_pass(const int n[3], double h, double m, const double *phi,
+                         double *G, double *F, double *dens, double sums[4],
+                         double *fmax, int *bad)
+{
+    int x, q;
+    int nx = n[0];
+    plane_acc *acc = (plane_acc *)calloc((size_t)nx, sizeof(plane_acc));
+    nsum tot[4];
+#pragma omp parallel for schedule(dynamic, 1)
+    for (x = 2; x <= nx - 3; x++) plane_pass(n, h, m, phi, x, G, F, dens, &acc[x]);
+    memset(tot, 0, sizeof(tot));
+    *fmax = 0.0;
+    *bad = 0;
+    for (x = 2; x <= nx - 3; x++) {
+        for (q = 0; q < 4; q++) nsum_add(&tot[q], nsum_get(&acc[x].e[q]));
+        if (acc[x].fmax > *fmax) *fmax = acc[x].fmax;
+        if (acc[x].bad) *bad = 1;
+    }
+    for (q = 0; q < 4; q++) sums[q] = nsum_get(&tot[q]);
+    free(acc);
+}
+
+void orc_forces(const int n[3], double h, double m, const double *phi,
+                double *G, double *F, double *dens)
+{
+    double sums[4], fmax;
+    int bad;
+    zero_boundary(n, G);
+    zero_boundary(n, F);
+    zero_boundary(n, dens);
+    lattice_pass(n, h, m, phi, G, F, dens, sums, &fmax, &bad);
+}
+
+void orc_energy(const int n[3], double h, double m, const double *phi,
+                double out[6])
+{
+    double sums[4], fmax, h3 = h * h * h;
+    int bad;
+    lattice_pass(n, h, m, phi, NULL, NULL, NULL, sums, &fmax, &bad);
+    out[1] = h3 * sums[0];
+    out[2] = h3 * sums[1];
+    out[3] = h3 * sums[2];
+    out[0] = out[1] + out[2] + out[3];
+    out[4] = h3 * sums[3];
+    out[5] = -out[1] + out[2] - 3.0 * out[3];
+}
+
+int orc_anf_step(const int n[3], double h, double m, double dt, int mode,
+                 double *phi, double *v, double *work, double *E_prev,
+                 orc_report *rep)
+{
+    double sums[4], fmax, h3 = h * h * h, E, E2, E4, E0;
+    int bad, arrested = 0, x;
+    size_t nsite = (size_t)n[0] * n[1] * n[2];
+
+    zero_boundary(n, work);
+    lattice_pass(n, h, m, phi, NULL, work, NULL, sums, &fmax, &bad);
+    E2 = h3 * sums[0];
+    E4 = h3 * sums[1];
+    E0 = h3 * sums[2];
+    E = E2 + E4 + E0;
+
+    /* arrest: the static energy rose, so the fictitious velocity is zeroed
+     * while the field is kept (Section 3). */
+    if (mode == ORC_ARRESTED && E > *E_prev) {
+        memset(v, 0, 4 * nsite * sizeof(double));
+        arrested = 1;
+    }
+
+#pragma omp parallel for schedule(static)
+    for (x = 2; x <= n[0] - 3; x++) {
+        int y, z, q;
+        for (y = 2; y <= n[1] - 3; y++)
+            for (z = 2; z <= n[2] - 3; z++) {
+                size_t s = site_index(n, x, y, z);
+                double t[4], nrm = 0.0;
+                for (q = 0; q < 4; q++) {
+                    if (mode == ORC_GRADIENT) {
+                        t[q] = phi[4 * s + q] + dt * work[4 * s + q];
+                    } else {
+                        v[4 * s + q] = v[4 * s + q] + dt * work[4 * s + q];
+                        t[q] = phi[4 * s + q] + dt * v[4 * s + q];
+                    }
+                    nrm += t[q] * t[q];
+                }
+                nrm = sqrt(nrm);
+                for (q = 0; q < 4; q++) phi[4 * s + q] = t[q] / nrm;
+            }
+    }
+
+    *E_prev = E;
+    if (rep) {
+        rep->E = E;
+        rep->E2 = E2;
+        rep->E4 = E4;
+        rep->E0 = E0;
+        rep->B = h3 * sums[3];
+        rep->virial = -E2 + E4 - 3.0 * E0;
+        rep->delta = fmax;
+        rep->arrested = arrested;
+    }
+    return (bad || !isfinite(E)) ? -1 : 0;
+}
+
+long long orc_flow(const int n[3], double h, double m, double dt, int mode,
+                   int nsteps, double *phi, double *v, double *work,
+                   double *E_prev, orc_report *reps)
+{
+    long long arrests = 0;
+    int s;
+    for (s = 0; s < nsteps; s++) {
+        orc_report r;
+        if (orc_anf_step(n, h, m, dt, mode, phi, v, work, E_prev, &r) != 0) {
+            if (reps) reps[s] = r;
+            return -1;
+        }
+        arrests += r.arrested;
+        if (reps) reps[s] = r;
+    }
+    return arrests;
+}
+
+/* ------------------------------------------------------------------------
+ * Section 4: initial fields
+ * ------------------------------------------------------------------------ */
+static double coord(const int n[3], double h, int axis, int i)
+{
+    return ((double)i - 0.5 * (double)(n[axis] - 1)) * h;
+}
+
+void orc_apply_vacuum_boundary(const int n[3], double *phi)
+{
+    int x, y, z;
+    for (x = 0; x < n[0]; x++)
+        for (y = 0; y < n[1]; y++)
+            for (z = 0; z < n[2]; z++)
+                if (!is_interior(n, x, y, z)) {
+                    double *p = &phi[4 * site_index(n, x, y, z)];
+                    p[0] = 1.0;
+                    p[1] = p[2] = p[3] = 0.0;
+                }
+}
+
+void orc_seed_vacuum(const int n[3], double *phi)
+{
+    size_t s, ns = (size_t)n[0] * n[1] * n[2];
+    for (s = 0; s < ns; s++) {
+        phi[4 * s] = 1.0;
+        phi[4 * s + 1] = phi[4 * s + 2] = phi[4 * s + 3] = 0.0;
+    }
+}
+
+/* complex helpers (plain structs, no <complex.h> to keep the C obvious) */
+typedef struct { double re, im; } cplx;
+static cplx cmul(cplx a, cplx b)
+{
+    cplx r = {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+    return r;
+}
+static cplx cadd(cplx a, cplx b)
+{
+    cplx r = {a.re + b.re, a.im + b.im};
+    return r;
+}
+
+/* Unit vector n_R = (2 Re R, 2 Im R, 1 - |R|^2)/(1 + |R|^2) of Section 4.1,
+ * written with R = P/Q in homogeneous form so that no division by zero can
+ * occur: n_R = (2 Re(P conj Q), 2 Im(P conj Q), |Q|^2 - |P|^2)/(|P|^2+|Q|^2).
+ * The Riemann-sphere coordinate z = tan(theta/2) e^{i varphi} = (x+iy)/(r+z3)
+ * is represented by the pair (Z1, Z0) with z = Z1/Z0; for z3 < 0 the
+ * equivalent pair (r - z3, x - iy) is used, which avoids cancellation. */
+static void rational_map_direction(int B, double x, double y, double z3,
+                                   double r, double nhat[3])
+{
+    cplx Z1, Z0, P, Q;
+    double den;
+    if (z3 >= 0.0) {
+        Z1.re = x; Z1.im = y;
+        Z0.re = r + z3; Z0.im = 0.0;
+    } else {
+        Z1.re = r - z3; Z1.im = 0.0;
+        Z0.re = x; Z0.im = -y;
+    }
+    if (B == 1) { /* R(z) = z */
+        P = Z1;
+        Q = Z0;
+    } else { /* B = 4: R(z) = (z^4 + 2 sqrt3 i z^2 + 1)/(z^4 - 2 sqrt3 i z^2 + 1) */
+        cplx Z1s = cmul(Z1, Z1), Z0s = cmul(Z0, Z0);
+        cplx Z14 = cmul(Z1s, Z1s), Z04 = cmul(Z0s, Z0s);
+        cplx mid = cmul(Z1s, Z0s);
+        cplx c = {0.0, 2.0 * sqrt(3.0)};
+        cplx cm = {0.0, -2.0 * sqrt(3.0)};
+        P = cadd(cadd(Z14, cmul(c, mid)), Z04);
+        Q = cadd(cadd(Z14, cmul(cm, mid)), Z04);
+    }
+    den = P.re * P.re + P.im * P.im + Q.re * Q.re + Q.im * Q.im;
+    if (den == 0.0) {
+        nhat[0] = nhat[1] = nhat[2] = 0.0;
+        return;
+    }
+    /* P conj(Q) */
+    nhat[0] = 2.0 * (P.re * Q.re + P.im * Q.im) / den;
+    nhat[1] = 2.0 * (P.im * Q.re - P.re * Q.im) / den;
+    nhat[2] = (Q.re * Q.re + Q.im * Q.im - P.re * P.re - P.im * P.im) / den;
+}
+
+int orc_seed_rational_map(const int n[3], double h, int B,
+                          double profile_scale, double *phi)
+{
+    int x;
+    if (B != 1 && B != 4) return -1;
+#pragma omp parallel for schedule(static)
+    for (x = 0; x < n[0]; x++) {
+        int y, z;
+        for (y = 0; y < n[1]; y++)
+            for (z = 0; z < n[2]; z++) {
+                double cx = coord(n, h, 0, x), cy = coord(n, h, 1, y),
+                       cz = coord(n, h, 2, z);
+                double r = sqrt(cx * cx + cy * cy + cz * cz);
+                double f = M_PI * exp(-r / profile_scale);
+                double nh[3];
+                double *p = &phi[4 * site_index(n, x, y, z)];
+                rational_map_direction(B, cx, cy, cz, r, nh);
+                /* U = exp(i f n.tau) = cos f + i sin f n.tau */
+                p[0] = cos(f);
+                p[1] = sin(f) * nh[0];
+                p[2] = sin(f) * nh[1];
+                p[3] = sin(f) * nh[2];
+            }
+    }
+    orc_apply_vacuum_boundary(n, phi);
+    return 0;
+}
+
+/* Quaternion product in the U = phi^0 + i phi^a tau^a representation:
+ * (a0, a)(b0, b) = (a0 b0 - a.b, a0 b + b0 a - a x b), which follows from
+ * tau^a tau^b = delta^{ab} + i eps^{abc} tau^c. */
+static void qmul(const double a[4], const double b[4], double out[4])
+{
+    double r[4];
+    r[0] = a[0] * b[0] - (a[1] * b[1] + a[2] * b[2] + a[3] * b[3]);
+    r[1] = a[0] * b[1] + b[0] * a[1] - (a[2] * b[3] - a[3] * b[2]);
+    r[2] = a[0] * b[2] + b[0] * a[2] - (a[3] * b[1] - a[1] * b[3]);
+    r[3] = a[0] * b[3] + b[0] * a[3] - (a[1] * b[2] - a[2] * b[1]);
+    memcpy(out, r, sizeof(r));
+}
+
+void orc_seed_product(const int n[3], double h, int K, const double *pos,
+                      const double *quat, double profile_scale,
+                      int symmetrise, double *phi)
+{
+    int x;
+#pragma omp parallel for schedule(static)
+    for (x = 0; x < n[0]; x++) {
+        int y, z, k, q;
+        double *U = (double *)malloc(4 * (size_t)(K > 0 ? K : 1) * sizeof(double));
+        for (y = 0; y < n[1]; y++)
+            for (z = 0; z < n[2]; z++) {
+                double fwd[4] = {1, 0, 0, 0}, rev[4] = {1, 0, 0, 0};
+                double *p = &phi[4 * site_index(n, x, y, z)];
+                for (k = 0; k < K; k++) {
+                    double dx = coord(n, h, 0, x) - pos[3 * k];
+                    double dy = coord(n, h, 1, y) - pos[3 * k + 1];
+                    double dz = coord(n, h, 2, z) - pos[3 * k + 2];
+                    double r = sqrt(dx * dx + dy * dy + dz * dz);
+                    double f = M_PI * exp(-r / profile_scale);
+                    double u0[4], A[4], Ad[4], t[4];
+                    u0[0] = cos(f);
+                    if (r > 0.0) {
+                        u0[1] = sin(f) * dx / r;
+                        u0[2] = sin(f) * dy / r;
+                        u0[3] = sin(f) * dz / r;
+                    } else {
+                        u0[1] = u0[2] = u0[3] = 0.0;
+                    }
+                    /* A U A^dagger with A = q0 + i q.tau, A^dagger = q0 - i q.tau */
+                    for (q = 0; q < 4; q++) A[q] = quat[4 * k + q];
+                    Ad[0] = A[0];
+                    Ad[1] = -A[1];
+                    Ad[2] = -A[2];
+                    Ad[3] = -A[3];
+                    qmul(A, u0, t);
+                    qmul(t, Ad, &U[4 * k]);
+                }
+                for (k = 0; k < K; k++) qmul(fwd, &U[4 * k], fwd);
+                for (k = K - 1; k >= 0; k--) qmul(rev, &U[4 * k], rev);
+                if (symmetrise) {
+                    double s[4], nrm = 0.0;
+                    for (q = 0; q < 4; q++) {
+                        s[q] = fwd[q] + rev[q];
+                        nrm += s[q] * s[q];
+                    }
+                    nrm = sqrt(nrm);
+                    if (nrm < 1e-12) {
+                        for (q = 0; q < 4; q++) p[q] = fwd[q];
+                    } else {
+                        for (q = 0; q < 4; q++) p[q] = s[q] / nrm;
+                    }
+                } else {
+                    for (q = 0; q < 4; q++) p[q] = fwd[q];
+                }
+            }
+        free(U);
+    }
+    orc_apply_vacuum_boundary(n, phi);
+}
+
+/* SplitMix64 (Steele, Lea and Flood, OOPSLA 2014), in counter form: the i-th
+ * output of the generator whose state starts at `seed`. */
+uint64_t orc_splitmix64(uint64_t seed, uint64_t i)
+{
+    uint64_t z = seed + (i + 1) * UINT64_C(0x9E3779B97F4A7C15);
+    z = (z ^ (z >> 30)) * UINT64_C(0xBF58476D1CE4E5B9);
+    z = (z ^ (z >> 27)) * UINT64_C(0x94D049BB133111EB);
+    return z ^ (z >> 31);
+}
+
+/* Box-Muller: u1 in (0, 1], u2 in [0, 1) from the top 53 bits. */
+double orc_normal(uint64_t seed, uint64_t i)
+{
+    double u1 = ((double)(orc_splitmix64(seed, 2 * i) >> 11) + 1.0) *
+                (1.0 / 9007199254740992.0);
+    double u2 = (double)(orc_splitmix64(seed, 2 * i + 1) >> 11) *
+                (1.0 / 9007199254740992.0);
+    return sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+}
+
+void orc_seed_noise(const int n[3], double h, double radius, double sigma,
+                    uint64_t seed, double *phi)
+{
+    size_t ns = (size_t)n[0] * n[1] * n[2], s;
+    int K = (int)ceil(4.0 * sigma / h), k, axis, x, q;
+    double *w = (double *)malloc((size_t)(2 * K + 1) * sizeof(double));
+    double *a = (double *)calloc(4 * ns, sizeof(double));
+    double *b = (double *)calloc(4 * ns, sizeof(double));
+    double wsum = 0.0;
+    nsum mean[4], var[4];
+    double count = 0.0;
+
+    /* i.i.d. N(0,1) per component inside the ball */
+#pragma omp parallel for schedule(static)
+    for (x = 0; x < n[0]; x++) {
+        int y, z, c;
+        for (y = 0; y < n[1]; y++)
+            for (z = 0; z < n[2]; z++) {
+                double cx = coord(n, h, 0, x), cy = coord(n, h, 1, y),
+                       cz = coord(n, h, 2, z);
+                size_t si = site_index(n, x, y, z);
+                if (cx * cx + cy * cy + cz * cz <= radius * radius)
+                    for (c = 0; c < 4; c++)
+                        a[4 * si + c] = orc_normal(seed, 4 * (uint64_t)si + c);
+            }
+    }
+
+    /* Gaussian weights on the lattice, truncated at 4 sigma, summing to one */
+    for (k = -K; k <= K; k++) {
+        w[k + K] = exp(-(k * h) * (k * h) / (2.0 * sigma * sigma));
+        wsum += w[k + K];
+    }
+    for (k = 0; k <= 2 * K; k++) w[k] /= wsum;
+
+    /* separable convolution along x, then y, then z; zero outside the box */
+    for (axis = 0; axis < 3; axis++) {
+#pragma omp parallel for schedule(static)
+        for (x = 0; x < n[0]; x++) {
+            int y, z, c, kk;
+            for (y = 0; y < n[1]; y++)
+                for (z = 0; z < n[2]; z++) {
+                    double acc[4] = {0, 0, 0, 0};
+                    for (kk = -K; kk <= K; kk++) {
+                        int xx = x, yy = y, zz = z;
+                        if (axis == 0) xx += kk;
+                        if (axis == 1) yy += kk;
+                        if (axis == 2) zz += kk;
+                        if (xx < 0 || xx >= n[0] || yy < 0 || yy >= n[1] ||
+                            zz < 0 || zz >= n[2])
+                            continue;
+                        for (c = 0; c < 4; c++)
+                            acc[c] += w[kk + K] *
+                                      a[4 * site_index(n, xx, yy, zz) + c];
+                    }
+                    for (c = 0; c < 4; c++)
+                        b[4 * site_index(n, x, y, z) + c] = acc[c];
+                }
+        }
+        memcpy(a, b, 4 * ns * sizeof(double));
+    }
+
+    /* unit standard deviation per component over the ball sites */
+    memset(mean, 0, sizeof(mean));
+    memset(var, 0, sizeof(var));
+    for (s = 0; s < ns; s++) {
+        int xs = (int)(s / ((size_t)n[1] * n[2]));
+        int ys = (int)((s / (size_t)n[2]) % (size_t)n[1]);
+        int zs = (int)(s % (size_t)n[2]);
+        double cx = coord(n, h, 0, xs), cy = coord(n, h, 1, ys),
+               cz = coord(n, h, 2, zs);
+        if (cx * cx + cy * cy + cz * cz <= radius * radius) {
+            for (q = 0; q < 4; q++) nsum_add(&mean[q], a[4 * s + q]);
+            count += 1.0;
+        }
+    }
+    for (s = 0; s < ns; s++) {
+        int xs = (int)(s / ((size_t)n[1] * n[2]));
+        int ys = (int)((s / (size_t)n[2]) % (size_t)n[1]);
+        int zs = (int)(s % (size_t)n[2]);
+        double cx = coord(n, h, 0, xs), cy = coord(n, h, 1, ys),
+               cz = coord(n, h, 2, zs);
+        if (cx * cx + cy * cy + cz * cz <= radius * radius)
+            for (q = 0; q < 4; q++) {
+                double d = a[4 * s + q] - nsum_get(&mean[q]) / count;
+                nsum_add(&var[q], d * d);
+            }
+    }
+    for (q = 0; q < 4; q++) {
+        double sd = count > 0.0 ? sqrt(nsum_get(&var[q]) / count) : 0.0;
+        if (sd > 0.0)
+            for (s = 0; s < ns; s++) a[4 * s + q] /= sd;
+    }
+
+    /* phi = normalise(vacuum + noise) */
+    for (s = 0; s < ns; s++) {
+        double t[4], nrm;
+        t[0] = 1.0 + a[4 * s];
+        t[1] = a[4 * s + 1];
+        t[2] = a[4 * s + 2];
+        t[3] = a[4 * s + 3];
+        nrm = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2] + t[3] * t[3]);
+        if (nrm < 1e-12) {
+            phi[4 * s] = 1.0;
+            phi[4 * s + 1] = phi[4 * s + 2] = phi[4 * s + 3] = 0.0;
+        } else {
+            for (q = 0; q < 4; q++) phi[4 * s + q] = t[q] / nrm;
+        }
+    }
+    orc_apply_vacuum_boundary(n, phi);
+    free(w);
+    free(a);
+    free(b);
+}

@@ -1,0 +1,113 @@
+/*
+ * skyrme_oracle.h -- plain FP64 CPU reference of the arrested-Newton-flow step
+ * of the 3D Skyrme model in sigma-model form (arXiv 2604.25876, Sections 2-4).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This oracle exists to check the CUDA library.
+ * Only tests, the smoke check and the benchmark's CPU-baseline leg may load
+ * it.  It shares no code, header, table or helper with the CUDA path.
+ *
+ * Conventions (all arrays are host memory, caller-owned):
+ *   - lattice n[3] = {Nx, Ny, Nz}; site (x,y,z) has linear index
+ *     ((x*Ny)+y)*Nz+z, z fastest (Section 7.5.1, the text file format).
+ *   - a field is 4 doubles per site (phi^0, phi^1, phi^2, phi^3), AoS.
+ *   - coordinates x_i = (i - (N-1)/2) * h on every axis.
+ *   - interior sites have every index in [2, N-3]; the two outer layers are
+ *     the fixed vacuum phi = (1,0,0,0) (Section 3, vacuum boundary).
+ */
+#ifndef SKYRME_ORACLE_H
+#define SKYRME_ORACLE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- per-site building blocks (Section 3 and Section 2.1) ---- */
+
+/* 4th-order finite differences at interior site (x,y,z):
+ *   d1[i][A] = d_i phi^A, d2[i][A] = d_ii phi^A,
+ *   dm[p][A] = d_i d_j phi^A for the pairs p = (x,y), (x,z), (y,z). */
+void orc_site_derivatives(const int n[3], double h, const double *phi,
+                          int x, int y, int z,
+                          double d1[3][4], double d2[3][4], double dm[3][4]);
+
+/* Euler-Lagrange gradient G = dE/dphi (Eq. "Sigma model EL equations"),
+ * tangent force F = -G + (G.phi) phi (Eq. "Newton_flow"), and the site
+ * densities dens = {e2, e4, e0, b}: the quadratic, quartic and mass parts of
+ * Eq. "SkyrmeEnergy_phi" and the baryon density of Eq. "B0_components". */
+void orc_site_terms(const double phi[4], const double d1[3][4],
+                    const double d2[3][4], const double dm[3][4], double m,
+                    double G[4], double F[4], double dens[4]);
+
+/* ---- whole-lattice operations ---- */
+
+/* G, F and densities at every interior site (zero on the boundary layers).
+ * Any output pointer may be NULL. */
+void orc_forces(const int n[3], double h, double m, const double *phi,
+                double *G, double *F, double *dens);
+
+/* out = {E, E2, E4, E0, B, V}: h^3 * sums over interior sites;
+ * V = -E2 + E4 - 3 E0 (the virial, Section 5.6). */
+void orc_energy(const int n[3], double h, double m, const double *phi,
+                double out[6]);
+
+typedef struct {
+    double E, E2, E4, E0, B, virial; /* of the field at the start of the step */
+    double delta;                    /* max over interior sites of |F|      */
+    int arrested;                    /* 1 when the velocity was zeroed       */
+} orc_report;
+
+enum { ORC_NEWTON = 0, ORC_ARRESTED = 1, ORC_GRADIENT = 2 };
+
+/* One flow iteration (Section 3), in place on phi and v.
+ *   mode ORC_ARRESTED: E_n of phi_n is compared with *E_prev; when E_n is
+ *     strictly larger, v is set to zero everywhere; then
+ *     v <- v + dt F(phi_n), phi <- normalise(phi_n + dt v).
+ *   mode ORC_NEWTON: the same without the arrest test.
+ *   mode ORC_GRADIENT: phi <- normalise(phi_n + dt F(phi_n)); v untouched.
+ * *E_prev is replaced by E_n.  work holds 4 doubles per site (F).
+ * Returns 0, or -1 when a non-finite value appeared. */
+int orc_anf_step(const int n[3], double h, double m, double dt, int mode,
+                 double *phi, double *v, double *work, double *E_prev,
+                 orc_report *rep);
+
+/* nsteps iterations; reps (nullable) receives one report per iteration.
+ * Returns the number of arrests, or -1 on a non-finite value. */
+long long orc_flow(const int n[3], double h, double m, double dt, int mode,
+                   int nsteps, double *phi, double *v, double *work,
+                   double *E_prev, orc_report *reps);
+
+/* ---- initial fields (Section 4) ---- */
+
+void orc_seed_vacuum(const int n[3], double *phi);
+/* phi = (cos f, sin f n_R(z)) with f(r) = pi exp(-r/profile_scale) and the
+ * rational map of degree B (1: R=z; 4: the cubic map of Table 1), centred at
+ * the origin. */
+int orc_seed_rational_map(const int n[3], double h, int B,
+                          double profile_scale, double *phi);
+/* Product ansatz of K isorotated 1-Skyrmions (Eq. "Product ansatz"):
+ * U_k = A_k U_hedgehog(x - X_k) A_k^dagger, pos[k][3], quat[k][4] (unit).
+ * symmetrise = 1: phi = normalise(U_1..U_K + U_K..U_1). */
+void orc_seed_product(const int n[3], double h, int K, const double *pos,
+                      const double *quat, double profile_scale,
+                      int symmetrise, double *phi);
+/* Smoothed-noise start: i.i.d. N(0,1) per component inside the ball
+ * r <= radius, convolved with a Gaussian of width sigma (truncated at
+ * 4 sigma), each component rescaled to unit standard deviation over the ball
+ * sites, phi = normalise((1,0,0,0) + noise). */
+void orc_seed_noise(const int n[3], double h, double radius, double sigma,
+                    uint64_t seed, double *phi);
+/* Overwrite the two outer layers with the vacuum. */
+void orc_apply_vacuum_boundary(const int n[3], double *phi);
+
+/* SplitMix64 counter stream: value number i of stream `seed`. */
+uint64_t orc_splitmix64(uint64_t seed, uint64_t i);
+/* Standard normal number i of stream `seed` (Box-Muller on two uniforms). */
+double orc_normal(uint64_t seed, uint64_t i);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
