@@ -1,0 +1,405 @@
+#!/usr/bin/env python3
+"""Benchmark of the arrested-Newton-flow step on one GB300 (or N replicas).
+
+Default workload: the B=4 cubic rational map on a 128^3 lattice (h = 0.1,
+m = 1), FP32 field/velocity/force arithmetic with FP64 energy, baryon-number
+and virial sums.  One bench step is one flow iteration over the lattice
+(fused step kernel + the speculative-arrest fix-up check).  The metric is
+interior site-updates per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own replica of the workload on its own GPU
+(independent problems, no data-path collective): value = all ranks' site
+updates / the slowest rank's time.  ``--impl reference`` times the FP64 CPU
+oracle on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+METRIC = "Gsite-updates/s of arrested Newton flow, FP32/batched vs FP64 at 1e-5 rel. energy"
+UNIT = "Gsite-updates/s"
+BYTES_PER_SITE_F32 = 64   # read phi, v; write phi', v' (16 B each)
+BYTES_PER_SITE_F64 = 128
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM = 6800.0     # GB/s, used only when the measured peaks file is absent
+FP64_NOMINAL_TFLOPS = 1.25
+FLOPS_PER_SITE = 590      # algorithmic FP operations per site-update (FMA = 2)
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_config(wl):
+    return {
+        "workload": wl.name,
+        "lattice": list(wl.n),
+        "h": wl.h,
+        "m": wl.m,
+        "dt": wl.dt,
+        "dt_configured": wl.dt_configured,
+        "seed": wl.description,
+        "interior_sites": wl.interior_sites,
+        "precision": "fp32 field/velocity/force, fp64 energy/B/virial sums and arrest test",
+        "l2": "inputs larger than L2: 4 field/velocity buffers of 33.5 MB = 134 MB > 129 MB",
+        "parallelism": "replicas (one lattice per GPU)",
+    }
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid_hint: str | None):
+        self.uuid = (uuid_hint or "").lower()
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 10:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if self.uuid:
+            mine = [r for r in rows if self.uuid in r[1].lower()]
+            rows = mine or rows
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        smax = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[6 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ------------------------------------------------------------ our kernels
+def kernel_fingerprint():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2604_25876_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.startswith("flow_") or name == "skyrme_device.cuh":
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_key: str, per_launch_sites: int):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(kernel_key)
+    except Exception:
+        return None
+    if not rec or rec.get("fingerprint") != kernel_fingerprint():
+        return None
+    scale = per_launch_sites / float(rec["sites"])
+    return float(rec["dram_bytes_per_launch"]) * scale
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+
+    import paper_2604_25876_gb300 as sk
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    sk.load()
+    wl = workloads.b4_cubic_128()
+    lat = sk.Lattice(wl.n, wl.h, wl.m, 32)
+    st = sk.State(lat, dev)
+    seed = sk.Seed.from_spec(wl.seed)
+    sk.init_field(lat, seed, st)
+    stream = torch.cuda.current_stream(dev)
+    K, W = args.steps, args.warmup
+    sites = wl.interior_sites
+
+    for _ in range(W):
+        sk.flow_step(lat, wl.dt, 1, sk.ARRESTED, st, report=False)
+    torch.cuda.synchronize(dev)
+
+    props = torch.cuda.get_device_properties(dev)
+    uuid = str(getattr(props, "uuid", "") or "")
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(K):
+        ev[k][0].record(stream)
+        sk.flow_step(lat, wl.dt, 1, sk.ARRESTED, st, report=False)
+        ev[k][1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    total_ms = t0.elapsed_time(t1)
+    iter_ms = [a.elapsed_time(b) for a, b in ev]
+    rep = sk.read_report(lat, st)
+    if rep["status"] != 0:
+        raise RuntimeError(f"device status {rep['status']}")
+
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = sites * K * ws / (total_ms * 1e-3) / 1e9
+
+    # roofline of the dominant kernel: algorithmic bytes per launch over the
+    # mean duration of one iteration (step launch + fix-up check)
+    hbm, peak_kind = peaks()
+    mean_iter = statistics.fmean(iter_ms)
+    achieved = BYTES_PER_SITE_F32 * sites / (mean_iter * 1e-3) / 1e9
+    traffic = recorded_traffic("step_f32_b4_cubic_128", sites)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "traffic": traffic,
+                "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+                if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "algorithmic_bytes_per_site": BYTES_PER_SITE_F32,
+                "duration_includes": "step kernel + fix-up check launch"}
+
+    out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": K,
+           "warmup": W, "ms_per_step": round(total_ms / K, 5), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": workload_config(wl), "roofline": roofline,
+           "gpu_launches": 2 * K, "clocks": clk,
+           "flow": {"steps_done": rep["steps"], "arrests": rep["arrests"],
+                    "fixups": rep["fixups"], "E": rep["E"], "B": rep["B"],
+                    "virial": rep["virial"], "delta": rep["delta"]}}
+
+    if rank == 0 and not args.no_extras:
+        out["e2e"] = run_e2e(sk, torch, dev, wl, K)
+        out["fp64_gpu"] = run_fp64_compare(sk, torch, dev, wl, K + W, rep)
+        out["cpu_baseline"] = run_cpu_baseline(wl, args.cpu_seconds)
+    return out
+
+
+def run_e2e(sk, torch, dev, wl, K):
+    """The same metric through the public API with host buffers: upload the
+    seed field from pinned host memory, K flow iterations with the report read
+    back, download the final field; all inside the timed region."""
+    lat = sk.Lattice(wl.n, wl.h, wl.m, 32)
+    st = sk.State(lat, dev)
+    sk.init_field(lat, sk.Seed.from_spec(wl.seed), st)
+    host_in = torch.empty(st.phi[0].shape, dtype=torch.float32, pin_memory=True)
+    host_in.copy_(st.phi[0])
+    host_out = torch.empty_like(host_in, pin_memory=True)
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize(dev)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    t_wall = time.perf_counter()
+    a.record(stream)
+    st.phi[0].copy_(host_in, non_blocking=True)
+    sk.load_field(lat, st, st.phi[0])
+    rep = sk.flow_step(lat, wl.dt, K, sk.ARRESTED, st, report=True)
+    host_out.copy_(st.phi[rep["cur"]], non_blocking=True)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t_wall
+    ms = a.elapsed_time(b)
+    bytes_field = host_in.numel() * 4
+    return {"value": round(wl.interior_sites * K / (ms * 1e-3) / 1e9, 4), "unit": UNIT,
+            "h2d_bytes_per_step": bytes_field / K,
+            "d2h_bytes_per_step": (bytes_field + 128) / K,
+            "wall_s": round(wall, 4),
+            "what": f"one job of {K} iterations: seed upload, flow, report and field download"}
+
+
+def run_fp64_compare(sk, torch, dev, wl, nsteps, rep32):
+    """FP64 GPU flow of the same workload for the same iterations (validated
+    against the FP64 oracle by the parity tests): its throughput, its ALU
+    roofline and the FP32 energy error relative to it."""
+    lat = sk.Lattice(wl.n, wl.h, wl.m, 64)
+    st = sk.State(lat, dev)
+    sk.init_field(lat, sk.Seed.from_spec(wl.seed), st)
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize(dev)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    rep = sk.flow_step(lat, wl.dt, nsteps, sk.ARRESTED, st, report=True)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b)
+    gs = wl.interior_sites * nsteps / (ms * 1e-3) / 1e9
+    tfl = gs * FLOPS_PER_SITE / 1e3
+    return {"value": round(gs, 4), "unit": UNIT, "steps": nsteps,
+            "roofline": {"bound": "alu", "achieved": round(tfl, 4),
+                         "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                         "frac": round(tfl / FP64_NOMINAL_TFLOPS, 4),
+                         "peak_source": "nominal GB300 FP64 rate",
+                         "algorithmic_flops_per_site": FLOPS_PER_SITE},
+            "E_fp64": rep["E"],
+            "fp32_energy_rel_err": abs(rep32["E"] - rep["E"]) / abs(rep["E"])
+            if rep32["steps"] == rep["steps"] else None}
+
+
+def run_cpu_baseline(wl, seconds):
+    """The FP64 oracle, as it stands, on the host cores: a bounded sample of
+    the workload (the first iterations of the same lattice and seed)."""
+    import oracle
+    oracle.build()
+    n = wl.n
+    if wl.seed.kind == "rational_map":
+        phi = oracle.seed_rational_map(n, wl.h, wl.seed.B, wl.seed.profile_scale)
+    else:
+        phi = oracle.seed_product(n, wl.h, wl.seed.positions, wl.seed.quaternions,
+                                  wl.seed.profile_scale, wl.seed.symmetrise)
+    st = oracle.new_state(phi)
+    t = time.perf_counter()
+    oracle.flow(st, wl.h, wl.m, wl.dt, 1)
+    one = time.perf_counter() - t
+    steps = max(1, int(seconds / max(one, 1e-6)))
+    t = time.perf_counter()
+    oracle.flow(st, wl.h, wl.m, wl.dt, steps)
+    el = time.perf_counter() - t
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": round(wl.interior_sites * steps / el / 1e9, 6), "unit": UNIT,
+            "cores": cores, "kind": "oracle",
+            "sample": f"{steps} FP64 oracle iterations of the full {n[0]}^3 workload "
+                      f"({el:.1f} s, after one untimed iteration)"}
+
+
+# ------------------------------------------------------------ reference arm
+def run_reference(args):
+    import oracle
+    oracle.build()
+    wl = workloads.b4_cubic_128()
+    K, W = args.steps, args.warmup
+    phi = oracle.seed_rational_map(wl.n, wl.h, wl.seed.B, wl.seed.profile_scale)
+    st = oracle.new_state(phi)
+    t = time.perf_counter()
+    oracle.flow(st, wl.h, wl.m, wl.dt, 1)
+    one = time.perf_counter() - t
+    # bounded sample: each reference step covers a slab of the lattice so that
+    # the whole run stays within about two minutes
+    budget = 120.0
+    frac = min(1.0, budget / max((K + W) * one, 1e-9))
+    nx = max(5, int(round(wl.n[0] * frac)))
+    slab = (nx, wl.n[1], wl.n[2])
+    sphi = np.ascontiguousarray(phi[:nx])
+    oracle.apply_vacuum_boundary(sphi)
+    sst = oracle.new_state(sphi)
+    oracle.flow(sst, wl.h, wl.m, wl.dt, W)
+    t = time.perf_counter()
+    oracle.flow(sst, wl.h, wl.m, wl.dt, K)
+    el = time.perf_counter() - t
+    sites = (nx - 4) * (wl.n[1] - 4) * (wl.n[2] - 4)
+    value = sites * K / el / 1e9
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = (f"{K} FP64 oracle iterations on a {slab[0]}x{slab[1]}x{slab[2]} slab of the "
+              f"{wl.n[0]}^3 workload")
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
+            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": K, "warmup": W,
+            "ms_per_step": round(el * 1e3 / K, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(wl),
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the e2e, FP64 and CPU-baseline legs")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    ws, rank, local = dist_env()
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    out = run_ours(args, ws, rank, local)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

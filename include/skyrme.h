@@ -1,0 +1,156 @@
+/*
+ * skyrme.h -- C ABI of the GB300 arrested-Newton-flow library for the 3D
+ * Skyrme model in sigma-model form (arXiv 2604.25876).
+ *
+ * Every compute step runs in hand-written sm_103a CUDA kernels.  The caller
+ * owns all memory: field, velocity and scratch buffers are device pointers it
+ * allocated (for example with PyTorch), streams are cudaStream_t values passed
+ * as void*.  The library keeps no global state between calls, never allocates
+ * on the flow path, and synchronises a stream only when a host-side result
+ * (a report or an energy) is requested.  Errors are status codes; nothing is
+ * thrown across the ABI and nothing aborts the process.
+ *
+ * Lattice layout (Section 7.5.1, the text/binary file formats): site (x,y,z)
+ * of an n[0] x n[1] x n[2] lattice has index ((x*n[1])+y)*n[2]+z, z fastest.
+ * Each site holds the 4 components (phi^0, phi^1, phi^2, phi^3) contiguously:
+ * a float4 (precision 32) or double4 (precision 64).  Site coordinates are
+ * x_i = (i - (n-1)/2) h.  Interior sites have every index in [2, n-3]; the two
+ * outer layers hold the fixed vacuum (1,0,0,0) and a zero velocity
+ * (Section 3: vacuum boundary, stencil radius 2).
+ */
+#ifndef SKYRME_H
+#define SKYRME_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SKYRME_ABI_VERSION 1
+
+typedef enum {
+    SKYRME_OK = 0,
+    SKYRME_EINVAL = 1,      /* invalid size, spacing, precision, mode, or a null/misaligned pointer */
+    SKYRME_ENOMEM = 2,      /* a caller-provided buffer is smaller than required */
+    SKYRME_ECUDA = 3,       /* a CUDA runtime call failed (the message is in skyrme_last_cuda_error) */
+    SKYRME_ENONFINITE = 4,  /* a NaN/Inf appeared in a force, density or energy sum */
+    SKYRME_ETIMEOUT = 5,    /* a bounded device-side wait gave up */
+    SKYRME_EUNSUPPORTED = 6 /* the request is valid but not implemented for this precision */
+} skyrme_status;
+
+/* Flow equations of Section 3.  ARRESTED is the arrested Newton flow
+ * (velocity zeroed whenever the static energy rises), NEWTON the same flow
+ * without arrest, GRADIENT the first-order flow phi_t = F. */
+typedef enum { SKYRME_NEWTON = 0, SKYRME_ARRESTED = 1, SKYRME_GRADIENT = 2 } skyrme_flow_mode;
+
+typedef struct {
+    int n[3];       /* sites per axis (x slowest, z fastest); each >= 5 */
+    double h;       /* lattice spacing, > 0, equal on every axis */
+    double m;       /* pion mass of the 2 m^2 (1 - phi^0) potential (Eq. SkyrmeEnergy_phi) */
+    int precision;  /* 32: float4 field and velocity, FP64 sums; 64: double4 */
+} skyrme_lattice;
+
+enum {
+    SKYRME_SEED_VACUUM = 0,        /* phi = (1,0,0,0) everywhere */
+    SKYRME_SEED_RATIONAL_MAP = 1,  /* Section 4.1, degree B in {1, 4} (Table 1), centred */
+    SKYRME_SEED_PRODUCT = 2,       /* Section 4.2, Eq. "Product ansatz" of B isorotated hedgehogs */
+    SKYRME_SEED_NOISE = 3          /* vacuum + Gaussian-smoothed N(0,1) noise in a ball, normalised */
+};
+
+typedef struct {
+    int kind;                    /* SKYRME_SEED_* */
+    int B;                       /* rational-map degree, or number of product constituents */
+    double profile_scale;        /* profile f(r) = pi exp(-r / profile_scale), > 0 */
+    const double *positions;     /* host, B x 3: constituent centres (PRODUCT) */
+    const double *quaternions;   /* host, B x 4: unit (q0, q1, q2, q3), A_k = q0 + i q.tau (PRODUCT) */
+    int symmetrise;              /* PRODUCT: 1 -> normalise(U_1..U_B + U_B..U_1), 0 -> U_1..U_B */
+    double radius;               /* NOISE: ball radius carrying the noise */
+    double sigma;                /* NOISE: Gaussian smoothing width (physical units), truncated at 4 sigma */
+    uint64_t seed;               /* NOISE: SplitMix64 stream; normal number k of site s, component c
+                                    uses stream values 2k and 2k+1 with k = 4 s + c (Box-Muller) */
+} skyrme_seed;
+
+/* Caller-owned device buffers of one lattice.  phi[i] and vel[i] each hold
+ * n[0]*n[1]*n[2] sites (16 or 32 bytes per site) and must be 16-byte (FP32)
+ * or 32-byte (FP64) aligned.  scratch holds skyrme_scratch_bytes() bytes,
+ * 256-byte aligned; it carries the flow's control block (current buffer,
+ * previous energy, counters) so that stepping needs no host round trip. */
+typedef struct {
+    void *phi[2];
+    void *vel[2];
+    void *scratch;
+    size_t scratch_bytes;
+} skyrme_state;
+
+/* Result of the latest flow iteration, read back from the control block. */
+typedef struct {
+    double E, E2, E4, E0;  /* static energy of the field at the start of the
+                              iteration and its quadratic, quartic and mass parts */
+    double B;              /* baryon number, Eq. "B0_components" integrated */
+    double virial;         /* V = -E2 + E4 - 3 E0 (Section 5.6) */
+    double delta;          /* max over interior sites of |F| (the residual of Section 3) */
+    double rms_force;      /* sqrt(mean |F|^2) over interior sites */
+    long long steps;       /* iterations completed since the field was set */
+    long long arrests;     /* iterations whose velocity was zeroed */
+    long long fixups;      /* speculative updates corrected after the energy was known */
+    int cur;               /* index (0/1) of the buffers holding the current field */
+    int status;            /* sticky device-side status (skyrme_status) */
+} skyrme_report;
+
+/* ---- queries ---- */
+int skyrme_abi_version(void);
+const char *skyrme_status_string(int status);
+/* Text of the most recent failing CUDA call made by this thread ("" if none). */
+const char *skyrme_last_cuda_error(void);
+/* Bytes of scratch a lattice needs (0 when the lattice is invalid). */
+size_t skyrme_scratch_bytes(const skyrme_lattice *lat);
+
+/* ---- set-up ----
+ * skyrme_init_field: writes the seed field of Section 4 into phi[0] and
+ * phi[1], zeroes vel[0] and vel[1], resets the control block (E_prev = +inf,
+ * counters zero, cur = 0).  PRODUCT reads its host arrays before returning.
+ * Asynchronous on `stream`. */
+skyrme_status skyrme_init_field(const skyrme_lattice *lat, const skyrme_seed *seed,
+                                skyrme_state *st, void *stream);
+/* skyrme_load_field: the caller has written a field into phi[0]; it is
+ * copied to phi[1], its outer layers are set to the vacuum, velocities are
+ * zeroed and the control block reset, as after skyrme_init_field. */
+skyrme_status skyrme_load_field(const skyrme_lattice *lat, skyrme_state *st, void *stream);
+
+/* ---- the flow (Section 3) ----
+ * nsteps iterations of `mode` with time step dt > 0.  One iteration computes
+ * the 4th-order derivatives of phi_n, the Euler-Lagrange gradient G, the
+ * tangent force F = -G + (G.phi) phi, the energy E_n; in ARRESTED mode the
+ * velocity is zeroed when E_n > E_{n-1}; then v += dt F, phi = (phi + dt v)/|.|
+ * at interior sites.  `report` (nullable, host) receives the latest
+ * iteration's results, which synchronises the stream.  Returns
+ * SKYRME_ENONFINITE (sticky) once a non-finite value has appeared. */
+skyrme_status skyrme_flow_step(const skyrme_lattice *lat, double dt, int nsteps, int mode,
+                               skyrme_state *st, skyrme_report *report, void *stream);
+/* Copy the control block to the host (synchronises the stream). */
+skyrme_status skyrme_read_report(const skyrme_lattice *lat, const skyrme_state *st,
+                                 skyrme_report *report, void *stream);
+
+/* ---- reductions of the current field (synchronise the stream) ----
+ * out6 = {E, E2, E4, E0, B, V}: h^3 times FP64 sums over interior sites of
+ * the densities of Eq. SkyrmeEnergy_phi and Eq. B0_components; V as above. */
+skyrme_status skyrme_energy(const skyrme_lattice *lat, skyrme_state *st, double out6[6],
+                            void *stream);
+skyrme_status skyrme_baryon_number(const skyrme_lattice *lat, skyrme_state *st, double *B,
+                                   void *stream);
+skyrme_status skyrme_virial(const skyrme_lattice *lat, skyrme_state *st, double *V,
+                            void *stream);
+
+/* ---- per-site values of the current field (asynchronous) ----
+ * force (device, nullable): F at interior sites, 0 on the boundary layers,
+ * same site layout and precision as phi.  dens (device, nullable): per site
+ * {e2, e4, e0, b} in the same precision. */
+skyrme_status skyrme_forces(const skyrme_lattice *lat, skyrme_state *st, void *force,
+                            void *dens, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

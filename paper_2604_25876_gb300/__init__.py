@@ -1,0 +1,316 @@
+"""GB300 arrested-Newton-flow library for the 3D Skyrme model (arXiv 2604.25876).
+
+Thin ctypes binding over the C ABI of ``include/skyrme.h``.  Every step of the
+flow runs in the library's sm_103a CUDA kernels; this module only marshals
+arguments.  PyTorch provides device memory and streams.  There is no CPU
+fallback: if ``libskyrme.so`` cannot be loaded (or built with nvcc), importing
+the kernels raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _build
+
+NEWTON, ARRESTED, GRADIENT = 0, 1, 2
+SEED_VACUUM, SEED_RATIONAL_MAP, SEED_PRODUCT, SEED_NOISE = 0, 1, 2, 3
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "buffer too small", 3: "CUDA error",
+          4: "non-finite value", 5: "device wait timed out", 6: "unsupported"}
+
+
+class SkyrmeError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        msg = f"{where}: {STATUS.get(status, status)}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+
+
+class c_lattice(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("h", ctypes.c_double), ("m", ctypes.c_double),
+                ("precision", ctypes.c_int)]
+
+
+class c_seed(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("B", ctypes.c_int), ("profile_scale", ctypes.c_double),
+                ("positions", ctypes.POINTER(ctypes.c_double)),
+                ("quaternions", ctypes.POINTER(ctypes.c_double)),
+                ("symmetrise", ctypes.c_int), ("radius", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class c_state(ctypes.Structure):
+    _fields_ = [("phi", ctypes.c_void_p * 2), ("vel", ctypes.c_void_p * 2),
+                ("scratch", ctypes.c_void_p), ("scratch_bytes", ctypes.c_size_t)]
+
+
+class c_report(ctypes.Structure):
+    _fields_ = [("E", ctypes.c_double), ("E2", ctypes.c_double), ("E4", ctypes.c_double),
+                ("E0", ctypes.c_double), ("B", ctypes.c_double), ("virial", ctypes.c_double),
+                ("delta", ctypes.c_double), ("rms_force", ctypes.c_double),
+                ("steps", ctypes.c_longlong), ("arrests", ctypes.c_longlong),
+                ("fixups", ctypes.c_longlong), ("cur", ctypes.c_int), ("status", ctypes.c_int)]
+
+
+# Exported symbols with their ctypes signatures (also checked by the ABI tests).
+_P = ctypes.c_void_p
+_SIGNATURES = {
+    "skyrme_abi_version": (ctypes.c_int, []),
+    "skyrme_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "skyrme_last_cuda_error": (ctypes.c_char_p, []),
+    "skyrme_scratch_bytes": (ctypes.c_size_t, [ctypes.POINTER(c_lattice)]),
+    "skyrme_init_field": (ctypes.c_int, [ctypes.POINTER(c_lattice), ctypes.POINTER(c_seed),
+                                         ctypes.POINTER(c_state), _P]),
+    "skyrme_load_field": (ctypes.c_int, [ctypes.POINTER(c_lattice), ctypes.POINTER(c_state), _P]),
+    "skyrme_flow_step": (ctypes.c_int, [ctypes.POINTER(c_lattice), ctypes.c_double, ctypes.c_int,
+                                        ctypes.c_int, ctypes.POINTER(c_state),
+                                        ctypes.POINTER(c_report), _P]),
+    "skyrme_read_report": (ctypes.c_int, [ctypes.POINTER(c_lattice), ctypes.POINTER(c_state),
+                                          ctypes.POINTER(c_report), _P]),
+    "skyrme_energy": (ctypes.c_int, [ctypes.POINTER(c_lattice), ctypes.POINTER(c_state),
+                                     ctypes.POINTER(ctypes.c_double), _P]),
+    "skyrme_baryon_number": (ctypes.c_int, [ctypes.POINTER(c_lattice), ctypes.POINTER(c_state),
+                                            ctypes.POINTER(ctypes.c_double), _P]),
+    "skyrme_virial": (ctypes.c_int, [ctypes.POINTER(c_lattice), ctypes.POINTER(c_state),
+                                     ctypes.POINTER(ctypes.c_double), _P]),
+    "skyrme_forces": (ctypes.c_int, [ctypes.POINTER(c_lattice), ctypes.POINTER(c_state), _P, _P,
+                                     _P]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libskyrme.so (building it with nvcc when absent or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing; run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        detail = load().skyrme_last_cuda_error().decode() if rc == 3 else ""
+        raise SkyrmeError(rc, where, detail)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream=None, device=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# --------------------------------------------------------------- lattice
+@dataclass
+class Lattice:
+    n: Sequence[int]
+    h: float
+    m: float = 0.0
+    precision: int = 32
+
+    def c(self) -> c_lattice:
+        return c_lattice((ctypes.c_int * 3)(*[int(v) for v in self.n]), float(self.h),
+                         float(self.m), int(self.precision))
+
+    @property
+    def dtype(self):
+        torch = _torch()
+        return torch.float64 if self.precision == 64 else torch.float32
+
+    @property
+    def interior_sites(self) -> int:
+        return int(np.prod([int(v) - 4 for v in self.n]))
+
+    def scratch_bytes(self) -> int:
+        c = self.c()
+        return int(load().skyrme_scratch_bytes(ctypes.byref(c)))
+
+
+@dataclass
+class Seed:
+    kind: int
+    B: int = 1
+    profile_scale: float = 1.0
+    positions: Optional[np.ndarray] = None
+    quaternions: Optional[np.ndarray] = None
+    symmetrise: bool = True
+    radius: float = 0.0
+    sigma: float = 0.0
+    seed: int = 0
+
+    @staticmethod
+    def vacuum():
+        return Seed(SEED_VACUUM)
+
+    @staticmethod
+    def rational_map(B: int, profile_scale: float):
+        return Seed(SEED_RATIONAL_MAP, B=B, profile_scale=profile_scale)
+
+    @staticmethod
+    def product(positions, quaternions, profile_scale: float = 1.0, symmetrise: bool = True):
+        pos = np.ascontiguousarray(positions, dtype=np.float64).reshape(-1, 3)
+        q = np.ascontiguousarray(quaternions, dtype=np.float64).reshape(-1, 4)
+        return Seed(SEED_PRODUCT, B=len(pos), profile_scale=profile_scale, positions=pos,
+                    quaternions=q, symmetrise=symmetrise)
+
+    @staticmethod
+    def noise(radius: float, sigma: float, seed: int):
+        return Seed(SEED_NOISE, radius=radius, sigma=sigma, seed=seed)
+
+    @staticmethod
+    def from_spec(spec):
+        """Seed from a ``workloads.SeedSpec``."""
+        if spec.kind == "rational_map":
+            return Seed.rational_map(spec.B, spec.profile_scale)
+        if spec.kind == "product":
+            return Seed.product(spec.positions, spec.quaternions, spec.profile_scale,
+                                spec.symmetrise)
+        if spec.kind == "noise":
+            return Seed.noise(spec.ball_radius, spec.sigma, spec.seed)
+        if spec.kind == "vacuum":
+            return Seed.vacuum()
+        raise ValueError(spec.kind)
+
+    def c(self):
+        pos = self.positions
+        q = self.quaternions
+        dp = ctypes.POINTER(ctypes.c_double)
+        s = c_seed(self.kind, int(self.B), float(self.profile_scale),
+                   pos.ctypes.data_as(dp) if pos is not None else dp(),
+                   q.ctypes.data_as(dp) if q is not None else dp(),
+                   int(bool(self.symmetrise)), float(self.radius), float(self.sigma),
+                   int(self.seed) & 0xFFFFFFFFFFFFFFFF)
+        return s, (pos, q)  # keep host arrays alive during the call
+
+
+class State:
+    """Device buffers of one lattice: two field and two velocity buffers
+    (torch tensors of shape (2, Nx, Ny, Nz, 4)) and the scratch block."""
+
+    def __init__(self, lat: Lattice, device="cuda"):
+        torch = _torch()
+        self.lat = lat
+        self.device = torch.device(device)
+        shape = (2,) + tuple(int(v) for v in lat.n) + (4,)
+        self.phi = torch.empty(shape, dtype=lat.dtype, device=self.device)
+        self.vel = torch.zeros(shape, dtype=lat.dtype, device=self.device)
+        self.scratch = torch.zeros(lat.scratch_bytes(), dtype=torch.uint8, device=self.device)
+
+    def c(self) -> c_state:
+        return c_state((ctypes.c_void_p * 2)(self.phi[0].data_ptr(), self.phi[1].data_ptr()),
+                       (ctypes.c_void_p * 2)(self.vel[0].data_ptr(), self.vel[1].data_ptr()),
+                       ctypes.c_void_p(self.scratch.data_ptr()),
+                       ctypes.c_size_t(self.scratch.numel()))
+
+    def report(self, stream=None) -> dict:
+        return read_report(self.lat, self, stream)
+
+    def field(self, stream=None):
+        """Tensor view of the buffer that holds the current field."""
+        return self.phi[self.report(stream)["cur"]]
+
+    def velocity(self, stream=None):
+        return self.vel[self.report(stream)["cur"]]
+
+
+def _rep_dict(r: c_report) -> dict:
+    return {k: getattr(r, k) for k, _ in c_report._fields_}
+
+
+def init_field(lat: Lattice, seed: Seed, st: State, stream=None):
+    cl, cs = lat.c(), st.c()
+    sd, keep = seed.c()
+    _check(load().skyrme_init_field(ctypes.byref(cl), ctypes.byref(sd), ctypes.byref(cs),
+                                    _stream_ptr(stream, st.device)), "skyrme_init_field")
+    del keep
+
+
+def load_field(lat: Lattice, st: State, phi, stream=None):
+    """Start a flow from a given field (any device/host tensor or array of
+    shape (Nx, Ny, Nz, 4)); its outer layers are replaced by the vacuum."""
+    torch = _torch()
+    t = torch.as_tensor(np.asarray(phi) if not isinstance(phi, torch.Tensor) else phi)
+    st.phi[0].copy_(t.to(device=st.device, dtype=lat.dtype))
+    cl, cs = lat.c(), st.c()
+    _check(load().skyrme_load_field(ctypes.byref(cl), ctypes.byref(cs),
+                                    _stream_ptr(stream, st.device)), "skyrme_load_field")
+
+
+def flow_step(lat: Lattice, dt: float, nsteps: int, mode: int, st: State, report: bool = True,
+              stream=None):
+    cl, cs = lat.c(), st.c()
+    rep = c_report()
+    rc = load().skyrme_flow_step(ctypes.byref(cl), float(dt), int(nsteps), int(mode),
+                                 ctypes.byref(cs), ctypes.byref(rep) if report else None,
+                                 _stream_ptr(stream, st.device))
+    _check(rc, "skyrme_flow_step")
+    return _rep_dict(rep) if report else None
+
+
+def read_report(lat: Lattice, st: State, stream=None) -> dict:
+    cl, cs = lat.c(), st.c()
+    rep = c_report()
+    _check(load().skyrme_read_report(ctypes.byref(cl), ctypes.byref(cs), ctypes.byref(rep),
+                                     _stream_ptr(stream, st.device)), "skyrme_read_report")
+    return _rep_dict(rep)
+
+
+def energy(lat: Lattice, st: State, stream=None) -> dict:
+    cl, cs = lat.c(), st.c()
+    out = (ctypes.c_double * 6)()
+    _check(load().skyrme_energy(ctypes.byref(cl), ctypes.byref(cs), out,
+                                _stream_ptr(stream, st.device)), "skyrme_energy")
+    return dict(zip(("E", "E2", "E4", "E0", "B", "virial"), list(out)))
+
+
+def baryon_number(lat: Lattice, st: State, stream=None) -> float:
+    cl, cs = lat.c(), st.c()
+    out = ctypes.c_double()
+    _check(load().skyrme_baryon_number(ctypes.byref(cl), ctypes.byref(cs), ctypes.byref(out),
+                                       _stream_ptr(stream, st.device)), "skyrme_baryon_number")
+    return out.value
+
+
+def virial(lat: Lattice, st: State, stream=None) -> float:
+    cl, cs = lat.c(), st.c()
+    out = ctypes.c_double()
+    _check(load().skyrme_virial(ctypes.byref(cl), ctypes.byref(cs), ctypes.byref(out),
+                                _stream_ptr(stream, st.device)), "skyrme_virial")
+    return out.value
+
+
+def forces(lat: Lattice, st: State, want_dens: bool = True, stream=None):
+    """(F, dens) of the current field as device tensors of shape (Nx,Ny,Nz,4)."""
+    torch = _torch()
+    shape = tuple(int(v) for v in lat.n) + (4,)
+    F = torch.empty(shape, dtype=lat.dtype, device=st.device)
+    D = torch.empty(shape, dtype=lat.dtype, device=st.device) if want_dens else None
+    cl, cs = lat.c(), st.c()
+    _check(load().skyrme_forces(ctypes.byref(cl), ctypes.byref(cs), ctypes.c_void_p(F.data_ptr()),
+                                ctypes.c_void_p(D.data_ptr()) if D is not None else None,
+                                _stream_ptr(stream, st.device)), "skyrme_forces")
+    return F, D

@@ -1,0 +1,288 @@
+// api.cu -- the extern "C" entry points of include/skyrme.h: argument
+// validation, the scratch layout, kernel launches and report read-back.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+
+#include "skyrme_device.cuh"
+#include "skyrme_internal.h"
+
+namespace skyrme {
+int max_constituents();
+int max_smoothing_half_width();
+bool f32_fast_path_available(const skyrme_lattice &lat);
+cudaError_t launch_step_f32_fast(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s);
+int f32_fast_blocks(const skyrme_lattice &lat);
+}  // namespace skyrme
+
+using namespace skyrme;
+
+static thread_local std::string g_last_cuda_error;
+
+static skyrme_status cuda_fail(cudaError_t e, const char *what)
+{
+    g_last_cuda_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return SKYRME_ECUDA;
+}
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t _e = (call);                         \
+        if (_e != cudaSuccess) return cuda_fail(_e, what); \
+    } while (0)
+
+static bool lattice_ok(const skyrme_lattice *lat)
+{
+    if (!lat) return false;
+    for (int i = 0; i < 3; ++i)
+        if (lat->n[i] < 5 || lat->n[i] > 4096) return false;
+    if (!(lat->h > 0.0) || !isfinite(lat->h) || !isfinite(lat->m) || lat->m < 0.0) return false;
+    if (lat->precision != 32 && lat->precision != 64) return false;
+    const double sites = (double)lat->n[0] * lat->n[1] * lat->n[2];
+    return sites < 4.0e9;
+}
+
+static size_t site_bytes(const skyrme_lattice &lat) { return lat.precision == 64 ? 32 : 16; }
+
+namespace skyrme {
+ScratchLayout scratch_layout(const skyrme_lattice &lat)
+{
+    ScratchLayout L;
+    const TileGeom g = tile_geometry(lat);
+    int blocks = g.nblocks;
+    if (lat.precision == 32) blocks = std::max(blocks, f32_fast_blocks(lat));
+    blocks = std::max(blocks, 152 * 8);  // pointwise reductions of the seed pass
+    L.max_blocks = blocks;
+    L.ctrl_off = 0;
+    L.step_off = kCtrlBytes;
+    const size_t part = ((size_t)blocks * kPartialDoubles * sizeof(double) + 255) & ~(size_t)255;
+    L.energy_off = L.step_off + part;
+    L.total = L.energy_off + part;
+    return L;
+}
+}  // namespace skyrme
+
+static skyrme_status check_state(const skyrme_lattice *lat, const skyrme_state *st)
+{
+    if (!lattice_ok(lat) || !st) return SKYRME_EINVAL;
+    const size_t align = site_bytes(*lat) == 32 ? 32 : 16;
+    for (int i = 0; i < 2; ++i) {
+        if (!st->phi[i] || !st->vel[i]) return SKYRME_EINVAL;
+        if (((uintptr_t)st->phi[i] % align) || ((uintptr_t)st->vel[i] % align)) return SKYRME_EINVAL;
+    }
+    if (!st->scratch || ((uintptr_t)st->scratch % 256)) return SKYRME_EINVAL;
+    if (st->scratch_bytes < scratch_layout(*lat).total) return SKYRME_ENOMEM;
+    if (st->phi[0] == st->phi[1] || st->vel[0] == st->vel[1]) return SKYRME_EINVAL;
+    return SKYRME_OK;
+}
+
+static FlowArgs make_args(const skyrme_lattice &lat, const skyrme_state &st, double dt, int mode)
+{
+    const ScratchLayout L = scratch_layout(lat);
+    FlowArgs a;
+    for (int i = 0; i < 2; ++i) {
+        a.phi[i] = st.phi[i];
+        a.vel[i] = st.vel[i];
+    }
+    char *base = static_cast<char *>(st.scratch);
+    a.ctrl = base + L.ctrl_off;
+    a.step_parts = reinterpret_cast<double *>(base + L.step_off);
+    a.energy_parts = reinterpret_cast<double *>(base + L.energy_off);
+    for (int i = 0; i < 3; ++i) a.n[i] = lat.n[i];
+    a.h = lat.h;
+    a.m = lat.m;
+    a.dt = dt;
+    a.mode = mode;
+    return a;
+}
+
+static skyrme_status copy_ctrl(const skyrme_state &st, Ctrl *host, cudaStream_t s)
+{
+    CK(cudaMemcpyAsync(host, st.scratch, sizeof(Ctrl), cudaMemcpyDeviceToHost, s), "read control block");
+    CK(cudaStreamSynchronize(s), "synchronise");
+    return SKYRME_OK;
+}
+
+static void fill_report(const Ctrl &c, skyrme_report *r)
+{
+    r->E = c.last[0];
+    r->E2 = c.last[1];
+    r->E4 = c.last[2];
+    r->E0 = c.last[3];
+    r->B = c.last[4];
+    r->virial = c.last[5];
+    r->delta = c.last[6];
+    r->rms_force = c.last[7];
+    r->steps = c.steps;
+    r->arrests = c.arrests;
+    r->fixups = c.fixups;
+    r->cur = c.cur;
+    r->status = c.status;
+}
+
+extern "C" {
+
+int skyrme_abi_version(void) { return SKYRME_ABI_VERSION; }
+
+const char *skyrme_status_string(int status)
+{
+    switch (status) {
+    case SKYRME_OK: return "ok";
+    case SKYRME_EINVAL: return "invalid argument";
+    case SKYRME_ENOMEM: return "buffer too small";
+    case SKYRME_ECUDA: return "CUDA error";
+    case SKYRME_ENONFINITE: return "non-finite value detected";
+    case SKYRME_ETIMEOUT: return "device wait timed out";
+    case SKYRME_EUNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+    }
+}
+
+const char *skyrme_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
+
+size_t skyrme_scratch_bytes(const skyrme_lattice *lat)
+{
+    if (!lattice_ok(lat)) return 0;
+    return scratch_layout(*lat).total;
+}
+
+skyrme_status skyrme_init_field(const skyrme_lattice *lat, const skyrme_seed *seed,
+                                skyrme_state *st, void *stream)
+{
+    skyrme_status rc = check_state(lat, st);
+    if (rc != SKYRME_OK) return rc;
+    if (!seed) return SKYRME_EINVAL;
+    switch (seed->kind) {
+    case SKYRME_SEED_VACUUM: break;
+    case SKYRME_SEED_RATIONAL_MAP:
+        if ((seed->B != 1 && seed->B != 4) || !(seed->profile_scale > 0.0)) return SKYRME_EINVAL;
+        break;
+    case SKYRME_SEED_PRODUCT:
+        if (seed->B < 1 || seed->B > max_constituents() || !seed->positions || !seed->quaternions ||
+            !(seed->profile_scale > 0.0))
+            return SKYRME_EINVAL;
+        for (int k = 0; k < 4 * seed->B; ++k)
+            if (!isfinite(seed->quaternions[k])) return SKYRME_EINVAL;
+        for (int k = 0; k < 3 * seed->B; ++k)
+            if (!isfinite(seed->positions[k])) return SKYRME_EINVAL;
+        break;
+    case SKYRME_SEED_NOISE:
+        if (!(seed->radius > 0.0) || !(seed->sigma > 0.0)) return SKYRME_EINVAL;
+        if (ceil(4.0 * seed->sigma / lat->h) > max_smoothing_half_width()) return SKYRME_EINVAL;
+        break;
+    default: return SKYRME_EINVAL;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    FlowArgs a = make_args(*lat, *st, 0.0, MODE_ARRESTED);
+    CK(launch_reset_ctrl(a.ctrl, s), "reset control block");
+    CK(launch_seed(*lat, *seed, a, s), "seed kernels");
+    CK(launch_load_finish(*lat, a, s), "finish field");
+    return SKYRME_OK;
+}
+
+skyrme_status skyrme_load_field(const skyrme_lattice *lat, skyrme_state *st, void *stream)
+{
+    skyrme_status rc = check_state(lat, st);
+    if (rc != SKYRME_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    FlowArgs a = make_args(*lat, *st, 0.0, MODE_ARRESTED);
+    CK(launch_reset_ctrl(a.ctrl, s), "reset control block");
+    CK(launch_load_finish(*lat, a, s), "finish field");
+    return SKYRME_OK;
+}
+
+skyrme_status skyrme_flow_step(const skyrme_lattice *lat, double dt, int nsteps, int mode,
+                               skyrme_state *st, skyrme_report *report, void *stream)
+{
+    skyrme_status rc = check_state(lat, st);
+    if (rc != SKYRME_OK) return rc;
+    if (!(dt > 0.0) || !isfinite(dt) || nsteps < 0) return SKYRME_EINVAL;
+    if (mode != SKYRME_NEWTON && mode != SKYRME_ARRESTED && mode != SKYRME_GRADIENT)
+        return SKYRME_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    FlowArgs a = make_args(*lat, *st, dt, mode);
+    const bool fast = lat->precision == 32 && f32_fast_path_available(*lat);
+    for (int k = 0; k < nsteps; ++k) {
+        if (fast) CK(launch_step_f32_fast(*lat, a, s), "step kernel (fp32)");
+        else CK(launch_step(*lat, a, s), "step kernel");
+        if (mode == SKYRME_ARRESTED) CK(launch_fixup(*lat, a, s), "fix-up kernel");
+    }
+    if (report) {
+        Ctrl c;
+        rc = copy_ctrl(*st, &c, s);
+        if (rc != SKYRME_OK) return rc;
+        fill_report(c, report);
+        if (c.status) return static_cast<skyrme_status>(c.status);
+    }
+    return SKYRME_OK;
+}
+
+skyrme_status skyrme_read_report(const skyrme_lattice *lat, const skyrme_state *st,
+                                 skyrme_report *report, void *stream)
+{
+    skyrme_status rc = check_state(lat, st);
+    if (rc != SKYRME_OK) return rc;
+    if (!report) return SKYRME_EINVAL;
+    Ctrl c;
+    rc = copy_ctrl(*st, &c, static_cast<cudaStream_t>(stream));
+    if (rc != SKYRME_OK) return rc;
+    fill_report(c, report);
+    return SKYRME_OK;
+}
+
+skyrme_status skyrme_energy(const skyrme_lattice *lat, skyrme_state *st, double out6[6],
+                            void *stream)
+{
+    skyrme_status rc = check_state(lat, st);
+    if (rc != SKYRME_OK) return rc;
+    if (!out6) return SKYRME_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    FlowArgs a = make_args(*lat, *st, 0.0, MODE_ARRESTED);
+    CK(launch_energy(*lat, a, s), "energy kernel");
+    Ctrl c;
+    rc = copy_ctrl(*st, &c, s);
+    if (rc != SKYRME_OK) return rc;
+    for (int i = 0; i < 6; ++i) out6[i] = c.energy[i];
+    if (!isfinite(out6[0]) || !isfinite(out6[4])) return SKYRME_ENONFINITE;
+    return SKYRME_OK;
+}
+
+skyrme_status skyrme_baryon_number(const skyrme_lattice *lat, skyrme_state *st, double *B,
+                                   void *stream)
+{
+    if (!B) return SKYRME_EINVAL;
+    double e[6];
+    skyrme_status rc = skyrme_energy(lat, st, e, stream);
+    if (rc == SKYRME_OK) *B = e[4];
+    return rc;
+}
+
+skyrme_status skyrme_virial(const skyrme_lattice *lat, skyrme_state *st, double *V, void *stream)
+{
+    if (!V) return SKYRME_EINVAL;
+    double e[6];
+    skyrme_status rc = skyrme_energy(lat, st, e, stream);
+    if (rc == SKYRME_OK) *V = e[5];
+    return rc;
+}
+
+skyrme_status skyrme_forces(const skyrme_lattice *lat, skyrme_state *st, void *force, void *dens,
+                            void *stream)
+{
+    skyrme_status rc = check_state(lat, st);
+    if (rc != SKYRME_OK) return rc;
+    const size_t align = site_bytes(*lat);
+    if (((uintptr_t)force % align) || ((uintptr_t)dens % align)) return SKYRME_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    FlowArgs a = make_args(*lat, *st, 0.0, MODE_ARRESTED);
+    const size_t bytes = (size_t)lat->n[0] * lat->n[1] * lat->n[2] * site_bytes(*lat);
+    if (force) CK(cudaMemsetAsync(force, 0, bytes, s), "clear force buffer");
+    if (dens) CK(cudaMemsetAsync(dens, 0, bytes, s), "clear density buffer");
+    CK(launch_forces(*lat, a, force, dens, s), "force kernel");
+    return SKYRME_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,404 @@
+// flow_generic.cu -- tile-staged kernels of the arrested Newton flow in either
+// precision: the fused step (derivatives + Euler-Lagrange gradient + tangent
+// projection + velocity/field update + renormalisation + energy sums), the
+// speculative-arrest fix-up, the energy reduction and the per-site force dump.
+//
+// One CTA owns a TX x TY x TZ block of interior sites and stages the field
+// with a 2-site halo in shared memory (Section 3: stencil radius 2).  The
+// FP64 path is bound by the FP64 pipe, so this straightforward staging is its
+// production kernel; FP32 has a dedicated streaming kernel elsewhere.
+//
+// Arrest without a host round trip: the energy E_n of phi_n is only known
+// after every CTA has finished, but the update needs to know whether v_n is
+// zeroed.  Each step therefore applies the decision predicted from the
+// previous iteration (ctrl.pred); the last CTA compares E_n with E_{n-1},
+// and when the prediction was wrong it sets ctrl.fix = +-1 so that the
+// pointwise fix-up kernel rewrites v_{n+1} = v' -+ v_n and
+// phi_{n+1} = normalise(phi_n + dt v_{n+1}) from the untouched old buffers.
+#include <cuda_runtime.h>
+
+#include "skyrme_device.cuh"
+#include "skyrme_internal.h"
+
+namespace skyrme {
+
+constexpr int GTX = 2, GTY = 4, GTZ = 32;  // interior sites per CTA
+constexpr int GSX = GTX + 4, GSY = GTY + 4, GSZ = GTZ + 4;
+constexpr int GTHREADS = GTX * GTY * GTZ;
+
+template <typename T> struct FlowParams {
+    vec4_t<T> *phi[2];
+    vec4_t<T> *vel[2];
+    Ctrl *ctrl;
+    double *parts;
+    int n0, n1, n2;
+    T inv_h, inv_h2, m2, dt;
+    double h3;
+    int mode;
+};
+
+template <typename T> __device__ __forceinline__ T comp(const vec4_t<T> &v, int A)
+{
+    return A == 0 ? v.x : (A == 1 ? v.y : (A == 2 ? v.z : v.w));
+}
+
+__device__ __forceinline__ size_t site_index(int x, int y, int z, int n1, int n2)
+{
+    return ((size_t)x * n1 + y) * (size_t)n2 + z;
+}
+
+// Stage the field tile with its halo; entries outside the lattice are left
+// unwritten (only sites outside the interior would read them).
+template <typename T>
+__device__ __forceinline__ void load_tile(vec4_t<T> *tile, const vec4_t<T> *phi, int x0, int y0,
+                                          int z0, int n0, int n1, int n2)
+{
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    for (int i = tid; i < GSX * GSY * GSZ; i += GTHREADS) {
+        const int lz = i % GSZ, ly = (i / GSZ) % GSY, lx = i / (GSZ * GSY);
+        const int x = x0 - 2 + lx, y = y0 - 2 + ly, z = z0 - 2 + lz;
+        if (x < n0 && y < n1 && z < n2) tile[i] = load4<T>(phi + site_index(x, y, z, n1, n2));
+    }
+}
+
+// All derivatives of the site at local interior coordinate (lx, ly, lz).
+template <typename T>
+__device__ __forceinline__ void tile_derivatives(const vec4_t<T> *tile, int lx, int ly, int lz,
+                                                 T inv_h, T inv_h2, T phi[4], T d1[3][4],
+                                                 T d2[3][4], T dm[3][4])
+{
+    auto P = [&](int dx, int dy, int dz) -> vec4_t<T> {
+        return tile[((lx + 2 + dx) * GSY + (ly + 2 + dy)) * GSZ + (lz + 2 + dz)];
+    };
+    const vec4_t<T> c = P(0, 0, 0);
+    const int off[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const vec4_t<T> m2v = P(-2 * off[i][0], -2 * off[i][1], -2 * off[i][2]);
+        const vec4_t<T> m1v = P(-off[i][0], -off[i][1], -off[i][2]);
+        const vec4_t<T> p1v = P(off[i][0], off[i][1], off[i][2]);
+        const vec4_t<T> p2v = P(2 * off[i][0], 2 * off[i][1], 2 * off[i][2]);
+#pragma unroll
+        for (int A = 0; A < 4; ++A) {
+            d1[i][A] = fd1<T>(comp<T>(m2v, A), comp<T>(m1v, A), comp<T>(p1v, A), comp<T>(p2v, A)) * inv_h;
+            d2[i][A] = fd2<T>(comp<T>(m2v, A), comp<T>(m1v, A), comp<T>(c, A), comp<T>(p1v, A),
+                              comp<T>(p2v, A)) * inv_h2;
+        }
+    }
+#pragma unroll
+    for (int A = 0; A < 4; ++A) phi[A] = comp<T>(c, A);
+    // mixed derivatives: outer stencil along the first axis of the pair applied
+    // to the inner stencil along the second
+    const int pr[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        const int a = pr[p][0], b = pr[p][1];
+        T inner[4][4];  // [outer offset index][A]
+        const int offs[4] = {-2, -1, 1, 2};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int oa = offs[k];
+            const vec4_t<T> q0 = P(oa * off[a][0] - 2 * off[b][0], oa * off[a][1] - 2 * off[b][1],
+                                   oa * off[a][2] - 2 * off[b][2]);
+            const vec4_t<T> q1 = P(oa * off[a][0] - off[b][0], oa * off[a][1] - off[b][1],
+                                   oa * off[a][2] - off[b][2]);
+            const vec4_t<T> q2 = P(oa * off[a][0] + off[b][0], oa * off[a][1] + off[b][1],
+                                   oa * off[a][2] + off[b][2]);
+            const vec4_t<T> q3 = P(oa * off[a][0] + 2 * off[b][0], oa * off[a][1] + 2 * off[b][1],
+                                   oa * off[a][2] + 2 * off[b][2]);
+#pragma unroll
+            for (int A = 0; A < 4; ++A)
+                inner[k][A] = fd1<T>(comp<T>(q0, A), comp<T>(q1, A), comp<T>(q2, A), comp<T>(q3, A));
+        }
+#pragma unroll
+        for (int A = 0; A < 4; ++A)
+            dm[p][A] = fd1<T>(inner[0][A], inner[1][A], inner[2][A], inner[3][A]) * inv_h2;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void normalise_store(vec4_t<T> *dst, const T t[4])
+{
+    const T nn = t[0] * t[0] + t[1] * t[1] + t[2] * t[2] + t[3] * t[3];
+    const T r = T(1) / sqrt(nn);
+    store4<T>(dst, make4<T>(t[0] * r, t[1] * r, t[2] * r, t[3] * r));
+}
+
+// Per-CTA partial record + last-CTA finish.
+template <typename T>
+__device__ __forceinline__ void reduce_and_finish(const FlowParams<T> &p, double (&acc)[6],
+                                                  bool energy_only, int pred)
+{
+    __shared__ double red[8 * (GTHREADS / 32)];
+    __shared__ int s_last;
+    double tot6[6];
+    block_reduce<6, 5>(acc, red, tot6);
+    const int nblocks = gridDim.x * gridDim.y * gridDim.z;
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    if (tid == 0) {
+        double *rec = p.parts + (size_t)bid * kPartialDoubles;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) rec[q] = tot6[q];
+        rec[6] = 0.0;
+        rec[7] = 0.0;
+        __threadfence();
+        unsigned int *ctr = energy_only ? &p.ctrl->edone : &p.ctrl->done;
+        const unsigned int t = atomicAdd(ctr, 1u);
+        s_last = (t == (unsigned int)(nblocks - 1));
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double tot[kPartialDoubles];
+    reduce_partials(p.parts, nblocks, red, tot);
+    if (tid == 0) {
+        const double nsites = (double)(p.n0 - 4) * (double)(p.n1 - 4) * (double)(p.n2 - 4);
+        tot[6] = nsites;
+        if (energy_only) {
+            Ctrl *c = p.ctrl;
+            const double E2 = p.h3 * tot[0], E4 = p.h3 * tot[1], E0 = p.h3 * tot[2];
+            c->energy[0] = E2 + E4 + E0;
+            c->energy[1] = E2;
+            c->energy[2] = E4;
+            c->energy[3] = E0;
+            c->energy[4] = p.h3 * tot[3];
+            c->energy[5] = -E2 + E4 - 3.0 * E0;
+            c->energy[6] = sqrt(tot[5]);
+            c->energy[7] = sqrt(tot[4] / nsites);
+            if (!(isfinite(c->energy[0]) && isfinite(c->energy[4]))) c->status = DEV_NONFINITE;
+            c->edone = 0;
+        } else {
+            finish_step(p.ctrl, tot, p.h3, p.mode, pred);
+        }
+    }
+}
+
+// kind 0: fused step; kind 1: energy only; kind 2: per-site dump
+template <typename T, int KIND>
+__global__ void __launch_bounds__(GTHREADS) k_tile(FlowParams<T> p, vec4_t<T> *fout,
+                                                   vec4_t<T> *dout)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    vec4_t<T> *tile = reinterpret_cast<vec4_t<T> *>(smem_raw);
+    const int cur = __ldcg(&p.ctrl->cur);
+    const int pred = (KIND == 0 && p.mode == MODE_ARRESTED) ? __ldcg(&p.ctrl->pred) : 0;
+    const vec4_t<T> *phi = p.phi[cur];
+    const int x0 = 2 + blockIdx.z * GTX, y0 = 2 + blockIdx.y * GTY, z0 = 2 + blockIdx.x * GTZ;
+    load_tile<T>(tile, phi, x0, y0, z0, p.n0, p.n1, p.n2);
+    __syncthreads();
+
+    const int lz = threadIdx.x, ly = threadIdx.y, lx = threadIdx.z;
+    const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
+    const bool valid = (x <= p.n0 - 3) && (y <= p.n1 - 3) && (z <= p.n2 - 3);
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    if (valid) {
+        T ph[4], d1[3][4], d2[3][4], dm[3][4], F[4], dens[4];
+        tile_derivatives<T>(tile, lx, ly, lz, p.inv_h, p.inv_h2, ph, d1, d2, dm);
+        site_physics<T>(ph, d1, d2, dm, p.m2, F, dens);
+        const size_t s = site_index(x, y, z, p.n1, p.n2);
+        if (KIND == 0) {
+            T t[4];
+            if (p.mode == MODE_GRADIENT) {
+#pragma unroll
+                for (int A = 0; A < 4; ++A) t[A] = ph[A] + p.dt * F[A];
+            } else {
+                T v[4] = {T(0), T(0), T(0), T(0)};
+                if (!pred) {
+                    const vec4_t<T> vv = load4<T>(p.vel[cur] + s);
+                    v[0] = vv.x; v[1] = vv.y; v[2] = vv.z; v[3] = vv.w;
+                }
+#pragma unroll
+                for (int A = 0; A < 4; ++A) {
+                    v[A] = v[A] + p.dt * F[A];
+                    t[A] = ph[A] + p.dt * v[A];
+                }
+                store4<T>(p.vel[cur ^ 1] + s, make4<T>(v[0], v[1], v[2], v[3]));
+            }
+            normalise_store<T>(p.phi[cur ^ 1] + s, t);
+        } else if (KIND == 2) {
+            if (fout) store4<T>(fout + s, make4<T>(F[0], F[1], F[2], F[3]));
+            if (dout) store4<T>(dout + s, make4<T>(dens[0], dens[1], dens[2], dens[3]));
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] = (double)dens[q];
+        const double f2 = (double)F[0] * F[0] + (double)F[1] * F[1] + (double)F[2] * F[2] +
+                          (double)F[3] * F[3];
+        acc[4] = f2;
+        acc[5] = f2;
+    }
+    if (KIND == 2) return;
+    reduce_and_finish<T>(p, acc, KIND == 1, pred);
+}
+
+// Pointwise correction of a mispredicted arrest decision.
+template <typename T> __global__ void k_fixup(FlowParams<T> p)
+{
+    const int fix = __ldcg(&p.ctrl->fix);
+    if (fix == 0) return;
+    const int nb = __ldcg(&p.ctrl->cur);  // new buffers (already flipped)
+    const int ob = nb ^ 1;
+    const int ix = p.n0 - 4, iy = p.n1 - 4, iz = p.n2 - 4;
+    const size_t total = (size_t)ix * iy * iz;
+    const T sgn = T(fix);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int z = 2 + (int)(i % iz);
+        const int y = 2 + (int)((i / iz) % iy);
+        const int x = 2 + (int)(i / ((size_t)iz * iy));
+        const size_t s = site_index(x, y, z, p.n1, p.n2);
+        const vec4_t<T> vn = load4<T>(p.vel[nb] + s);
+        const vec4_t<T> vo = load4<T>(p.vel[ob] + s);
+        const vec4_t<T> fo = load4<T>(p.phi[ob] + s);
+        T v[4] = {vn.x + sgn * vo.x, vn.y + sgn * vo.y, vn.z + sgn * vo.z, vn.w + sgn * vo.w};
+        T t[4] = {fo.x + p.dt * v[0], fo.y + p.dt * v[1], fo.z + p.dt * v[2], fo.w + p.dt * v[3]};
+        store4<T>(p.vel[nb] + s, make4<T>(v[0], v[1], v[2], v[3]));
+        normalise_store<T>(p.phi[nb] + s, t);
+    }
+}
+
+// phi[1] <- phi[0]; outer layers <- vacuum in both; velocities <- 0.
+template <typename T> __global__ void k_load_finish(FlowParams<T> p)
+{
+    const size_t total = (size_t)p.n0 * p.n1 * p.n2;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int z = (int)(i % p.n2);
+        const int y = (int)((i / p.n2) % p.n1);
+        const int x = (int)(i / ((size_t)p.n2 * p.n1));
+        const bool inner = x >= 2 && x <= p.n0 - 3 && y >= 2 && y <= p.n1 - 3 && z >= 2 &&
+                           z <= p.n2 - 3;
+        vec4_t<T> f = inner ? load4<T>(p.phi[0] + i) : make4<T>(T(1), T(0), T(0), T(0));
+        store4<T>(p.phi[0] + i, f);
+        store4<T>(p.phi[1] + i, f);
+        store4<T>(p.vel[0] + i, make4<T>(T(0), T(0), T(0), T(0)));
+        store4<T>(p.vel[1] + i, make4<T>(T(0), T(0), T(0), T(0)));
+    }
+}
+
+__global__ void k_reset_ctrl(Ctrl *c)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        c->E_prev = __longlong_as_double(0x7ff0000000000000LL);  // +inf
+        for (int i = 0; i < 8; ++i) c->last[i] = 0.0, c->energy[i] = 0.0;
+        c->steps = 0;
+        c->arrests = 0;
+        c->fixups = 0;
+        c->cur = 0;
+        c->pred = 0;
+        c->fix = 0;
+        c->status = 0;
+        c->done = 0;
+        c->edone = 0;
+    }
+}
+
+// ------------------------------------------------------------- launchers
+TileGeom tile_geometry(const skyrme_lattice &lat)
+{
+    TileGeom g;
+    const int ix = lat.n[0] - 4, iy = lat.n[1] - 4, iz = lat.n[2] - 4;
+    g.grid = dim3((iz + GTZ - 1) / GTZ, (iy + GTY - 1) / GTY, (ix + GTX - 1) / GTX);
+    g.block = dim3(GTZ, GTY, GTX);
+    g.nblocks = (int)(g.grid.x * g.grid.y * g.grid.z);
+    g.smem = (size_t)GSX * GSY * GSZ * (lat.precision == 64 ? sizeof(dvec4) : sizeof(float4));
+    return g;
+}
+
+template <typename T> static FlowParams<T> make_params(const FlowArgs &a, double *parts)
+{
+    FlowParams<T> p;
+    p.phi[0] = static_cast<vec4_t<T> *>(a.phi[0]);
+    p.phi[1] = static_cast<vec4_t<T> *>(a.phi[1]);
+    p.vel[0] = static_cast<vec4_t<T> *>(a.vel[0]);
+    p.vel[1] = static_cast<vec4_t<T> *>(a.vel[1]);
+    p.ctrl = static_cast<Ctrl *>(a.ctrl);
+    p.parts = parts;
+    p.n0 = a.n[0];
+    p.n1 = a.n[1];
+    p.n2 = a.n[2];
+    p.inv_h = T(1.0 / a.h);
+    p.inv_h2 = T(1.0 / (a.h * a.h));
+    p.m2 = T(a.m * a.m);
+    p.dt = T(a.dt);
+    p.h3 = a.h * a.h * a.h;
+    p.mode = a.mode;
+    return p;
+}
+
+template <typename T, int KIND>
+static cudaError_t launch_tile(const skyrme_lattice &lat, const FlowParams<T> &p, vec4_t<T> *fo,
+                               vec4_t<T> *dout, cudaStream_t s)
+{
+    const TileGeom g = tile_geometry(lat);
+    static thread_local bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_tile<T, KIND>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(GSX * GSY * GSZ * sizeof(vec4_t<T>)));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    k_tile<T, KIND><<<g.grid, g.block, g.smem, s>>>(p, fo, dout);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s)
+{
+    if (lat.precision == 64)
+        return launch_tile<double, 0>(lat, make_params<double>(a, a.step_parts), nullptr, nullptr, s);
+    return launch_tile<float, 0>(lat, make_params<float>(a, a.step_parts), nullptr, nullptr, s);
+}
+
+cudaError_t launch_energy(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s)
+{
+    if (lat.precision == 64)
+        return launch_tile<double, 1>(lat, make_params<double>(a, a.energy_parts), nullptr, nullptr, s);
+    return launch_tile<float, 1>(lat, make_params<float>(a, a.energy_parts), nullptr, nullptr, s);
+}
+
+cudaError_t launch_forces(const skyrme_lattice &lat, const FlowArgs &a, void *force, void *dens,
+                          cudaStream_t s)
+{
+    if (lat.precision == 64)
+        return launch_tile<double, 2>(lat, make_params<double>(a, a.energy_parts),
+                                      static_cast<dvec4 *>(force), static_cast<dvec4 *>(dens), s);
+    return launch_tile<float, 2>(lat, make_params<float>(a, a.energy_parts),
+                                 static_cast<float4 *>(force), static_cast<float4 *>(dens), s);
+}
+
+static int pointwise_blocks(size_t total)
+{
+    size_t b = (total + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+cudaError_t launch_fixup(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s)
+{
+    const size_t total = (size_t)(lat.n[0] - 4) * (lat.n[1] - 4) * (lat.n[2] - 4);
+    if (lat.precision == 64)
+        k_fixup<double><<<pointwise_blocks(total), 256, 0, s>>>(make_params<double>(a, a.step_parts));
+    else
+        k_fixup<float><<<pointwise_blocks(total), 256, 0, s>>>(make_params<float>(a, a.step_parts));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_load_finish(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s)
+{
+    const size_t total = (size_t)lat.n[0] * lat.n[1] * lat.n[2];
+    if (lat.precision == 64)
+        k_load_finish<double><<<pointwise_blocks(total), 256, 0, s>>>(make_params<double>(a, a.step_parts));
+    else
+        k_load_finish<float><<<pointwise_blocks(total), 256, 0, s>>>(make_params<float>(a, a.step_parts));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset_ctrl(void *ctrl, cudaStream_t s)
+{
+    k_reset_ctrl<<<1, 32, 0, s>>>(static_cast<Ctrl *>(ctrl));
+    return cudaGetLastError();
+}
+
+}  // namespace skyrme

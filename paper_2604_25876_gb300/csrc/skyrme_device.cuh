@@ -1,0 +1,273 @@
+// skyrme_device.cuh -- device-side building blocks shared by the kernels of
+// the arrested-Newton-flow library: vector types, the control block that
+// carries the flow state across launches, the per-site physics (Section 3,
+// Eq. "Sigma model EL equations", Eq. "Newton_flow"; Section 2.1,
+// Eq. "SkyrmeEnergy_phi", Eq. "B0_components") and the deterministic block
+// reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace skyrme {
+
+// ---------------------------------------------------------------- vectors
+// One lattice site: 4 components, 16 bytes (float4) or 32 bytes (dvec4).
+struct __align__(32) dvec4 {
+    double x, y, z, w;
+};
+template <typename T> struct V4;
+template <> struct V4<float> { using type = float4; };
+template <> struct V4<double> { using type = dvec4; };
+template <typename T> using vec4_t = typename V4<T>::type;
+
+template <typename T> __device__ __forceinline__ vec4_t<T> load4(const vec4_t<T> *p);
+template <> __device__ __forceinline__ float4 load4<float>(const float4 *p) { return *p; }
+template <> __device__ __forceinline__ dvec4 load4<double>(const dvec4 *p)
+{
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    const double2 a = q[0], b = q[1];
+    return dvec4{a.x, a.y, b.x, b.y};
+}
+template <typename T> __device__ __forceinline__ void store4(vec4_t<T> *p, vec4_t<T> v);
+template <> __device__ __forceinline__ void store4<float>(float4 *p, float4 v) { *p = v; }
+template <> __device__ __forceinline__ void store4<double>(dvec4 *p, dvec4 v)
+{
+    double2 *q = reinterpret_cast<double2 *>(p);
+    q[0] = make_double2(v.x, v.y);
+    q[1] = make_double2(v.z, v.w);
+}
+
+template <typename T> __device__ __forceinline__ vec4_t<T> make4(T a, T b, T c, T d);
+template <> __device__ __forceinline__ float4 make4<float>(float a, float b, float c, float d)
+{
+    return make_float4(a, b, c, d);
+}
+template <> __device__ __forceinline__ dvec4 make4<double>(double a, double b, double c, double d)
+{
+    return dvec4{a, b, c, d};
+}
+
+// ---------------------------------------------------------- control block
+// Lives at the start of the caller's scratch buffer.  Written by the last
+// CTA of each step launch; read by the next launch.
+struct Ctrl {
+    double E_prev;        // energy of the previous iteration's start field
+    double last[8];       // E, E2, E4, E0, B, virial, delta, rms |F|
+    long long steps;
+    long long arrests;
+    long long fixups;
+    int cur;              // buffers holding the current field
+    int pred;             // predicted arrest of the next iteration
+    int fix;              // 0, or +1/-1: velocity correction the fix-up applies
+    int status;           // sticky status (0 or an error code)
+    unsigned int done;    // arrival counter of the step launch
+    unsigned int edone;   // arrival counter of the energy launch
+    double energy[8];     // E, E2, E4, E0, B, V, max|F|, rms|F| of skyrme_energy
+    double pad[6];
+};
+static_assert(sizeof(Ctrl) <= 512, "control block must fit its 512-byte slot");
+
+constexpr int kCtrlBytes = 512;
+constexpr int kPartialDoubles = 8;  // per CTA: e2, e4, e0, b, sum|F|^2, max|F|^2, nsites, pad
+
+enum Mode { MODE_NEWTON = 0, MODE_ARRESTED = 1, MODE_GRADIENT = 2 };
+enum DevStatus { DEV_OK = 0, DEV_NONFINITE = 4, DEV_TIMEOUT = 5 };
+
+// --------------------------------------------------------- stencil weights
+// Section 3: first derivative (-phi_{+2} + 8 phi_{+1} - 8 phi_{-1} + phi_{-2})/(12 h),
+// second derivative (-phi_{+2} + 16 phi_{+1} - 30 phi_0 + 16 phi_{-1} - phi_{-2})/(12 h^2),
+// mixed derivative: first-derivative stencil along i of the one along j.
+template <typename T> struct W {
+    static constexpr T c1 = T(2) / T(3);
+    static constexpr T c2 = T(-1) / T(12);
+    static constexpr T s1 = T(4) / T(3);
+    static constexpr T s2 = T(-1) / T(12);
+    static constexpr T s0 = T(-5) / T(2);
+};
+
+// Unscaled symmetric stencils on scalars: fd1 = c1 (p1 - m1) + c2 (p2 - m2)
+template <typename T>
+__device__ __forceinline__ T fd1(T m2v, T m1v, T p1v, T p2v)
+{
+    return W<T>::c1 * (p1v - m1v) + W<T>::c2 * (p2v - m2v);
+}
+template <typename T>
+__device__ __forceinline__ T fd2(T m2v, T m1v, T c, T p1v, T p2v)
+{
+    return W<T>::s1 * (p1v + m1v) + W<T>::s2 * (p2v + m2v) + W<T>::s0 * c;
+}
+
+// ------------------------------------------------------------ site physics
+// Inputs: phi (4), first derivatives d1[i][A], second derivatives d2[i][A]
+// (d_ii) and mixed dm[p][A] for p = xy, xz, yz, all already scaled by 1/h, 1/h^2.
+// Outputs: tangent force F (4) and densities {e2, e4, e0, b}.
+template <typename T>
+__device__ __forceinline__ void site_physics(const T phi[4], const T d1[3][4], const T d2[3][4],
+                                             const T dm[3][4], T m2, T F[4], T dens[4])
+{
+    auto dot = [](const T *a, const T *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2] + a[3] * b[3]; };
+    const T a00 = dot(d1[0], d1[0]), a11 = dot(d1[1], d1[1]), a22 = dot(d1[2], d1[2]);
+    const T a01 = dot(d1[0], d1[1]), a02 = dot(d1[0], d1[2]), a12 = dot(d1[1], d1[2]);
+    const T tra = a00 + a11 + a22;
+    T L[4];
+#pragma unroll
+    for (int A = 0; A < 4; ++A) L[A] = d2[0][A] + d2[1][A] + d2[2][A];
+    // g_i = sum_j d_ij phi . d_j phi ;  s_i = Laplacian(phi) . d_i phi
+    const T g0 = dot(d2[0], d1[0]) + dot(dm[0], d1[1]) + dot(dm[1], d1[2]);
+    const T g1 = dot(dm[0], d1[0]) + dot(d2[1], d1[1]) + dot(dm[2], d1[2]);
+    const T g2 = dot(dm[1], d1[0]) + dot(dm[2], d1[1]) + dot(d2[2], d1[2]);
+    const T c0 = g0 - dot(L, d1[0]);
+    const T c1 = g1 - dot(L, d1[1]);
+    const T c2 = g2 - dot(L, d1[2]);
+    const T one_tra = T(1) + tra;
+    const T b01 = T(2) * a01, b02 = T(2) * a02, b12 = T(2) * a12;
+    T G[4];
+#pragma unroll
+    for (int A = 0; A < 4; ++A) {
+        // d_ij phi^A a_ij over all i, j (symmetric)
+        const T Ha = d2[0][A] * a00 + d2[1][A] * a11 + d2[2][A] * a22 + dm[0][A] * b01 +
+                     dm[1][A] * b02 + dm[2][A] * b12;
+        const T brace = L[A] * one_tra + d1[0][A] * c0 + d1[1][A] * c1 + d1[2][A] * c2 - Ha;
+        G[A] = T(-2) * brace;
+    }
+    G[0] -= T(2) * m2;
+    const T Gphi = G[0] * phi[0] + G[1] * phi[1] + G[2] * phi[2] + G[3] * phi[3];
+#pragma unroll
+    for (int A = 0; A < 4; ++A) F[A] = Gphi * phi[A] - G[A];
+
+    dens[0] = tra;
+    const T sq = a00 * a00 + a11 * a11 + a22 * a22 + T(2) * (a01 * a01 + a02 * a02 + a12 * a12);
+    dens[1] = T(0.5) * (tra * tra - sq);
+    dens[2] = T(2) * m2 * (T(1) - phi[0]);
+    // b = -(1/2 pi^2) det[phi, d_x phi, d_y phi, d_z phi] (Laplace expansion in 2x2 minors)
+    const T *r0 = phi, *r1 = d1[0], *r2 = d1[1], *r3 = d1[2];
+    const T s0 = r0[0] * r1[1] - r1[0] * r0[1];
+    const T s1 = r0[0] * r1[2] - r1[0] * r0[2];
+    const T s2 = r0[0] * r1[3] - r1[0] * r0[3];
+    const T s3 = r0[1] * r1[2] - r1[1] * r0[2];
+    const T s4 = r0[1] * r1[3] - r1[1] * r0[3];
+    const T s5 = r0[2] * r1[3] - r1[2] * r0[3];
+    const T q5 = r2[2] * r3[3] - r3[2] * r2[3];
+    const T q4 = r2[1] * r3[3] - r3[1] * r2[3];
+    const T q3 = r2[1] * r3[2] - r3[1] * r2[2];
+    const T q2 = r2[0] * r3[3] - r3[0] * r2[3];
+    const T q1 = r2[0] * r3[2] - r3[0] * r2[2];
+    const T q0 = r2[0] * r3[1] - r3[0] * r2[1];
+    const T det = s0 * q5 - s1 * q4 + s2 * q3 + s3 * q2 - s4 * q1 + s5 * q0;
+    dens[3] = T(-0.050660591821168885) * det;  // -1/(2 pi^2)
+}
+
+// ------------------------------------------------------ block reductions
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Reduce NQ values per thread (sums, except index MAXQ which is a max) over
+// the block; thread 0 ends with the totals in out[].  Fixed order: the result
+// is bitwise reproducible for a given launch shape.  red must hold
+// NQ * (blockDim/32) doubles.
+template <int NQ, int MAXQ>
+__device__ __forceinline__ void block_reduce(double (&v)[NQ], double *red, double (&out)[NQ])
+{
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int lane = tid & 31, warp = tid >> 5;
+    const int nw = (blockDim.x * blockDim.y * blockDim.z) >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[q] = (q == MAXQ) ? warp_max(v[q]) : warp_sum(v[q]);
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) red[q * nw + warp] = v[q];
+    }
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            double acc = red[q * nw];
+            for (int w = 1; w < nw; ++w)
+                acc = (q == MAXQ) ? fmax(acc, red[q * nw + w]) : acc + red[q * nw + w];
+            out[q] = acc;
+        }
+    }
+}
+
+// Sum the per-CTA partial records (count of them = nparts) in a fixed order
+// with the threads of one block; the totals land in tot[] of thread 0.
+__device__ __forceinline__ void reduce_partials(const double *parts, int nparts, double *red,
+                                                double (&tot)[kPartialDoubles])
+{
+    double v[kPartialDoubles];
+#pragma unroll
+    for (int q = 0; q < kPartialDoubles; ++q) v[q] = 0.0;
+    const int nthr = blockDim.x * blockDim.y * blockDim.z;
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    for (int i = tid; i < nparts; i += nthr) {
+        const double *p = parts + (size_t)i * kPartialDoubles;
+#pragma unroll
+        for (int q = 0; q < kPartialDoubles; ++q) {
+            const double x = __ldcg(p + q);
+            v[q] = (q == 5) ? fmax(v[q], x) : v[q] + x;
+        }
+    }
+    const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+#pragma unroll
+    for (int q = 0; q < kPartialDoubles; ++q) v[q] = (q == 5) ? warp_max(v[q]) : warp_sum(v[q]);
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < kPartialDoubles; ++q) red[q * nw + warp] = v[q];
+    }
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < kPartialDoubles; ++q) {
+            double acc = red[q * nw];
+            for (int w = 1; w < nw; ++w)
+                acc = (q == 5) ? fmax(acc, red[q * nw + w]) : acc + red[q * nw + w];
+            tot[q] = acc;
+        }
+    }
+}
+
+// End-of-step bookkeeping, run by thread 0 of the last CTA to arrive.
+// tot = {sum e2, sum e4, sum e0, sum b, sum |F|^2, max |F|^2, n_sites, -}.
+__device__ __forceinline__ void finish_step(Ctrl *c, const double (&tot)[kPartialDoubles],
+                                            double h3, int mode, int pred)
+{
+    const double E2 = h3 * tot[0], E4 = h3 * tot[1], E0 = h3 * tot[2];
+    const double E = E2 + E4 + E0;
+    const double B = h3 * tot[3];
+    const double delta = sqrt(tot[5]);
+    const double rms = tot[6] > 0.0 ? sqrt(tot[4] / tot[6]) : 0.0;
+    int actual = 0;
+    if (mode == MODE_ARRESTED) actual = (E > c->E_prev) ? 1 : 0;
+    const int fix = (actual == pred) ? 0 : (actual ? -1 : +1);
+    c->fix = fix;
+    c->pred = actual;
+    c->arrests += actual;
+    c->fixups += (fix != 0);
+    c->E_prev = E;
+    c->steps += 1;
+    c->cur ^= 1;
+    c->last[0] = E;
+    c->last[1] = E2;
+    c->last[2] = E4;
+    c->last[3] = E0;
+    c->last[4] = B;
+    c->last[5] = -E2 + E4 - 3.0 * E0;
+    c->last[6] = delta;
+    c->last[7] = rms;
+    if (!(isfinite(E) && isfinite(B) && isfinite(tot[4]))) c->status = DEV_NONFINITE;
+    c->done = 0;
+}
+
+}  // namespace skyrme

@@ -1,0 +1,57 @@
+// skyrme_internal.h -- host-side declarations shared by the library's
+// translation units (launchers and the scratch layout).  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/skyrme.h"
+
+namespace skyrme {
+
+// Scratch layout: [control block 512 B][step partials][energy partials]
+struct ScratchLayout {
+    size_t ctrl_off = 0;
+    size_t step_off = 0;
+    size_t energy_off = 0;
+    size_t total = 0;
+    int max_blocks = 0;
+};
+
+// Launch geometry of a lattice for the generic tile kernels.
+struct TileGeom {
+    dim3 grid;
+    dim3 block;
+    int nblocks;
+    size_t smem;
+};
+
+TileGeom tile_geometry(const skyrme_lattice &lat);
+ScratchLayout scratch_layout(const skyrme_lattice &lat);
+
+struct FlowArgs {
+    void *phi[2];
+    void *vel[2];
+    void *ctrl;
+    double *step_parts;
+    double *energy_parts;
+    int n[3];
+    double h, m, dt;
+    int mode;
+};
+
+// Kernels (asynchronous, return the launch error)
+cudaError_t launch_step(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s);
+cudaError_t launch_fixup(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s);
+cudaError_t launch_energy(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s);
+cudaError_t launch_forces(const skyrme_lattice &lat, const FlowArgs &a, void *force, void *dens,
+                          cudaStream_t s);
+cudaError_t launch_load_finish(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s);
+cudaError_t launch_reset_ctrl(void *ctrl, cudaStream_t s);
+
+// Seeds (init_fields.cu)
+cudaError_t launch_seed(const skyrme_lattice &lat, const skyrme_seed &seed, const FlowArgs &a,
+                        cudaStream_t s);
+
+}  // namespace skyrme

@@ -1,0 +1,87 @@
+"""Host-side checks of the C ABI (no GPU needed): every function declared in
+include/skyrme.h is exported by libskyrme.so, and argument validation
+rejects bad input before any CUDA call is made."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2604_25876_gb300 as sk
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for hdr in os.listdir(os.path.join(ROOT, "include")):
+        if not hdr.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", hdr)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(skyrme_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = sk.load()
+    names = declared_functions()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(lib, name), name
+    # and the binding declares a signature for each of them
+    assert set(names) <= set(sk._SIGNATURES), set(names) - set(sk._SIGNATURES)
+
+
+def test_abi_version_and_status_strings():
+    lib = sk.load()
+    assert lib.skyrme_abi_version() == 1
+    assert lib.skyrme_status_string(0) == b"ok"
+    assert lib.skyrme_status_string(4) == b"non-finite value detected"
+
+
+def test_scratch_bytes_and_lattice_validation():
+    lib = sk.load()
+    good = sk.Lattice((48, 48, 48), 0.2, 0.0, 64).c()
+    assert lib.skyrme_scratch_bytes(ctypes.byref(good)) >= 512
+    for bad in (sk.Lattice((4, 48, 48), 0.2, 0.0, 64), sk.Lattice((48, 48, 48), 0.0, 0.0, 64),
+                sk.Lattice((48, 48, 48), 0.2, -1.0, 64), sk.Lattice((48, 48, 48), 0.2, 0.0, 16)):
+        c = bad.c()
+        assert lib.skyrme_scratch_bytes(ctypes.byref(c)) == 0
+
+
+def test_invalid_arguments_are_rejected_without_cuda():
+    lib = sk.load()
+    lat = sk.Lattice((16, 16, 16), 0.2, 1.0, 32).c()
+    # null state
+    assert lib.skyrme_flow_step(ctypes.byref(lat), 0.01, 1, 1, None, None, None) == 1
+    # misaligned and too-small buffers (fake addresses: never dereferenced)
+    st = sk.c_state((ctypes.c_void_p * 2)(0x10000, 0x20000), (ctypes.c_void_p * 2)(0x30000, 0x40008),
+                    ctypes.c_void_p(0x50000), ctypes.c_size_t(1 << 30))
+    assert lib.skyrme_flow_step(ctypes.byref(lat), 0.01, 1, 1, ctypes.byref(st), None, None) == 1
+    st = sk.c_state((ctypes.c_void_p * 2)(0x10000, 0x20000), (ctypes.c_void_p * 2)(0x30000, 0x40000),
+                    ctypes.c_void_p(0x50000), ctypes.c_size_t(16))
+    assert lib.skyrme_flow_step(ctypes.byref(lat), 0.01, 1, 1, ctypes.byref(st), None, None) == 2
+    st = sk.c_state((ctypes.c_void_p * 2)(0x10000, 0x20000), (ctypes.c_void_p * 2)(0x30000, 0x40000),
+                    ctypes.c_void_p(0x50000), ctypes.c_size_t(1 << 30))
+    # bad dt / mode / nsteps
+    assert lib.skyrme_flow_step(ctypes.byref(lat), 0.0, 1, 1, ctypes.byref(st), None, None) == 1
+    assert lib.skyrme_flow_step(ctypes.byref(lat), 0.01, 1, 7, ctypes.byref(st), None, None) == 1
+    assert lib.skyrme_flow_step(ctypes.byref(lat), 0.01, -1, 1, ctypes.byref(st), None, None) == 1
+    # bad seeds
+    for seed in (sk.Seed(sk.SEED_RATIONAL_MAP, B=3, profile_scale=1.0),
+                 sk.Seed(sk.SEED_RATIONAL_MAP, B=4, profile_scale=0.0),
+                 sk.Seed(sk.SEED_PRODUCT, B=2),  # no arrays
+                 sk.Seed(sk.SEED_NOISE, radius=3.0, sigma=100.0, seed=1),  # too wide
+                 sk.Seed(9)):
+        cs, keep = seed.c()
+        assert lib.skyrme_init_field(ctypes.byref(lat), ctypes.byref(cs), ctypes.byref(st),
+                                     None) == 1
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    monkeypatch.setattr(sk, "_lib", None)
+    monkeypatch.setattr(sk._build, "LIB", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError):
+        sk.load(build_if_missing=False)
