@@ -5,8 +5,8 @@
 // Eq. "Newton_flow", v += dt F, phi = normalise(phi + dt v); Section 2.1
 // densities summed in FP64), organised for GB300:
 //
-//  * one persistent CTA per SM; the CTAs split the (column, x-plane) work of
-//    the lattice evenly.  A column is an 8 x 32 block of interior (y, z)
+//  * two persistent CTAs per SM (16 warps); the CTAs split the (column,
+//    x-plane) work of the lattice evenly.  A column is an 8 x 32 block of interior (y, z)
 //    sites; a CTA marches along x through contiguous runs of planes.
 //  * each x-plane of the column tile, with its 2-site halo (12 x 36 sites,
 //    6.9 KB), is streamed into a 4-slot shared-memory ring by TMA
@@ -15,16 +15,22 @@
 //  * in-plane derivatives (d_y, d_z, d_yy, d_zz) come from the staged plane;
 //    d_yz = d_z(d_y phi) uses a shared-memory exchange of d_y phi (with the
 //    4 z-halo columns computed by 4 lanes per warp); d_x, d_xx, d_xy = d_x(d_y
-//    phi), d_xz = d_x(d_z phi) come from a 5-plane register ring that the
-//    x-loop cycles through (unrolled by 5 so no register is ever moved).
+//    phi), d_xz = d_x(d_z phi) come from a 5-plane register ring of (phi, d_y
+//    phi, d_z phi) that the x-loop cycles through (unrolled by 5 so no
+//    register is ever moved).  The in-plane contractions a plane contributes
+//    to its own centre two planes later wait in a per-thread shared-memory
+//    ring, and the velocity of each centre plane arrives by TMA together with
+//    the field plane two planes ahead: this keeps the kernel at 128 registers,
+//    two CTAs (16 warps) per SM.
 //  * 4-vector arithmetic uses the packed FP32 pair instructions of sm_100+
 //    (__ffma2_rn / __fadd2_rn / __fmul2_rn): two components per instruction.
-//  * per-site densities are summed in FP32 over at most 5 consecutive planes
+//  * per-site densities are summed in FP32 over at most 20 consecutive planes
 //    and then accumulated in FP64; the block and grid reductions are FP64 in
 //    a fixed order, as in the tile kernel.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
+#include <stdlib.h>
 
 #include "skyrme_device.cuh"
 #include "skyrme_internal.h"
@@ -35,7 +41,8 @@ constexpr int FTY = 8, FTZ = 32;
 constexpr int FTHREADS = FTY * FTZ;  // 256: warp w owns row w of the tile
 constexpr int FSY = FTY + 4, FSZ = FTZ + 4;
 constexpr int NSLOT = 4;
-constexpr unsigned PLANE_BYTES = FSY * FSZ * 16;  // 6912
+constexpr unsigned PLANE_BYTES = FSY * FSZ * 16;   // 6912
+constexpr unsigned VPLANE_BYTES = FTY * FTZ * 16;  // 4096
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per plane copy
 
 struct F32Params {
@@ -55,8 +62,10 @@ struct F32Params {
 };
 
 struct __align__(128) F32Smem {
-    float4 plane[NSLOT][FSY][FSZ];
-    float4 dy[2][FTY][FSZ];
+    float4 plane[NSLOT][FSY][FSZ];   // haloed field planes (TMA)
+    float4 vpl[NSLOT][FTY][FTZ];     // velocity planes of the centre sites (TMA)
+    float4 dy[2][FTY][FSZ];          // d_y phi exchange for d_yz
+    float4 inpl[3][4][FTHREADS];     // per-thread in-plane values of the last 3 planes
     unsigned long long bar[NSLOT];
     double red[8 * (FTHREADS / 32)];
     int flag;
@@ -161,32 +170,41 @@ __device__ __forceinline__ P4 fd2(const P4 &m2, const P4 &m1, const P4 &c, const
     return fma(bc(s0), c, fma(bc(s2), add(p2, m2), mul(bc(s1), add(p1, m1))));
 }
 
-// Per-plane values of one column kept in the x-ring.
+// Per-plane values of one column kept in the register x-ring.
 struct PlaneVals {
     P4 phi, dy, dz;
-    P4 lin;      // d_yy phi + d_zz phi
-    P4 qin;      // d_yy phi a_yy + d_zz phi a_zz + 2 d_yz phi a_yz
-    float gy, gz;  // d_yy.d_y + d_yz.d_z and d_yz.d_y + d_zz.d_z
-    float ayy, azz, ayz;
 };
 
 struct Acc {
     float e2, e4, e0, b, f2, fmax2;
 };
 
+__device__ __forceinline__ void flush(double (&acc)[6], Acc &a)
+{
+    acc[0] += (double)a.e2;
+    acc[1] += (double)a.e4;
+    acc[2] += (double)a.e0;
+    acc[3] += (double)a.b;
+    acc[4] += (double)a.f2;
+    acc[5] = fmax(acc[5], (double)a.fmax2);
+    a = {0, 0, 0, 0, 0, 0};
+}
+
 // ------------------------------------------------------------------ kernel
-__global__ void __launch_bounds__(FTHREADS, 1)
+__global__ void __launch_bounds__(FTHREADS, 2)
     k_step_f32(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1,
+               const __grid_constant__ CUtensorMap vmap0, const __grid_constant__ CUtensorMap vmap1,
                F32Params p)
 {
-    __shared__ F32Smem sm;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    F32Smem &sm = *reinterpret_cast<F32Smem *>(smem_raw);
     const int tid = threadIdx.x;
     const int ty = tid >> 5, tz = tid & 31;
     Ctrl *ctrl = p.ctrl;
     const int cur = __ldcg(&ctrl->cur);
     const int pred = (p.mode == MODE_ARRESTED) ? __ldcg(&ctrl->pred) : 0;
     const CUtensorMap *map = cur ? &map1 : &map0;
-    const float4 *__restrict__ vin = p.vel[cur];
+    const CUtensorMap *vmap = cur ? &vmap1 : &vmap0;
     float4 *__restrict__ phiout = p.phi[cur ^ 1];
     float4 *__restrict__ vout = p.vel[cur ^ 1];
     const bool use_v = (p.mode != MODE_GRADIENT) && !pred;
@@ -219,15 +237,17 @@ __global__ void __launch_bounds__(FTHREADS, 1)
         const bool valid = (y <= p.n1 - 3) && (z <= p.n2 - 3);
         const size_t col_off = (size_t)y * p.n2 + z;
         const int pf = xs - 2, pl = xe + 1;  // planes needed by this run
-        if (tid == 0) {
-            for (int q = 0; q < NSLOT && pf + q <= pl; ++q) {
-                const int s = (g + q) % NSLOT;
-                mbar_expect_tx(&sm.bar[s], PLANE_BYTES);
-                tma_plane(&sm.plane[s][0][0], map, &sm.bar[s], 4 * (z0 - 2), y0 - 2, pf + q);
-            }
-        }
+        // plane q travels with the velocity of centre q - 2 (when that is a centre)
+        auto issue = [&](int q, int slot) {
+            const bool wv = use_v && q - 2 >= xs && q - 2 < xe;
+            mbar_expect_tx(&sm.bar[slot], PLANE_BYTES + (wv ? VPLANE_BYTES : 0u));
+            tma_plane(&sm.plane[slot][0][0], map, &sm.bar[slot], 4 * (z0 - 2), y0 - 2, q);
+            if (wv) tma_plane(&sm.vpl[slot][0][0], vmap, &sm.bar[slot], 4 * z0, y0, q - 2);
+        };
+        if (tid == 0)
+            for (int q = 0; q < NSLOT && pf + q <= pl; ++q) issue(pf + q, (g + q) % NSLOT);
         PlaneVals ring[5];
-        float4 vpre[5];
+        int nouter = 0;
         for (int base = pf; base <= pl && !failed; base += 5) {
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
@@ -235,9 +255,8 @@ __global__ void __launch_bounds__(FTHREADS, 1)
                 if (pp > pl) break;
                 const int s = g % NSLOT;
                 const uint32_t par = (g / NSLOT) & 1u;
-                const bool ok = mbar_wait(&sm.bar[s], par);
-                if (!ok) sm.flag = 1;
-                // ---- arrival of plane pp: in-plane derivatives
+                if (!mbar_wait(&sm.bar[s], par)) sm.flag = 1;
+                // ---- arrival of plane pp: in-plane first and second derivatives
                 const float4(*P)[FSZ] = sm.plane[s];
                 const P4 c = ld4(P[ty + 2][tz + 2]);
                 const P4 ym2 = ld4(P[ty][tz + 2]), ym1 = ld4(P[ty + 1][tz + 2]);
@@ -255,39 +274,21 @@ __global__ void __launch_bounds__(FTHREADS, 1)
                     DY[ty][hc] = st4(fd1(ld4(P[ty][hc]), ld4(P[ty + 1][hc]), ld4(P[ty + 3][hc]),
                                          ld4(P[ty + 4][hc]), p.c1, p.c2));
                 }
-                if (use_v && pp >= xs && pp < xe && valid)
-                    vpre[k] = __ldcs(vin + (size_t)pp * plane_stride + col_off);
-                __syncthreads();
-                if (sm.flag) {
-                    failed = true;
-                    break;
-                }
-                // the plane slot is free again: stream plane pp + NSLOT into it
-                if (tid == 0 && pp + NSLOT <= pl) {
-                    mbar_expect_tx(&sm.bar[s], PLANE_BYTES);
-                    tma_plane(&sm.plane[s][0][0], map, &sm.bar[s], 4 * (z0 - 2), y0 - 2, pp + NSLOT);
-                }
-                const P4 dyz = fd1(ld4(DY[ty][tz]), ld4(DY[ty][tz + 1]), ld4(DY[ty][tz + 3]),
-                                   ld4(DY[ty][tz + 4]), p.c1, p.c2);
-                PlaneVals &R = ring[k];
-                R.phi = c;
-                R.dy = dy;
-                R.dz = dz;
-                R.ayy = dot(dy, dy);
-                R.azz = dot(dz, dz);
-                R.ayz = dot(dy, dz);
-                R.lin = add(dyy, dzz);
-                R.qin = fma(bc(2.f * R.ayz), dyz, fma(bc(R.azz), dzz, mul(bc(R.ayy), dyy)));
-                R.gy = hsum(dot2(dyz, dz, __ffma2_rn(dyy.b, dy.b, __fmul2_rn(dyy.a, dy.a))));
-                R.gz = hsum(dot2(dzz, dz, __ffma2_rn(dyz.b, dy.b, __fmul2_rn(dyz.a, dy.a))));
-                ++g;
+                ring[k].phi = c;
+                ring[k].dy = dy;
+                ring[k].dz = dz;
 
-                // ---- centre x = pp - 2: everything else, then the update
+                // ---- centre x = pp - 2: x-derivatives, physics, update
                 const int x = pp - 2;
                 if (x >= xs) {
                     const PlaneVals &M2 = ring[(k + 1) % 5], &M1 = ring[(k + 2) % 5];
                     const PlaneVals &C = ring[(k + 3) % 5], &Q1 = ring[(k + 4) % 5];
                     const PlaneVals &Q2 = ring[k];
+                    const float4 *rec = &sm.inpl[(g + 1) % 3][0][tid];  // plane x = pp - 2
+                    const P4 lin = ld4(rec[0]), qin = ld4(rec[FTHREADS]);
+                    const float4 r2 = rec[2 * FTHREADS];
+                    const float Cgy = r2.x, Cgz = r2.y, Cayy = r2.z, Cazz = r2.w;
+                    const float Cayz = rec[3 * FTHREADS].x;
                     const P4 ph = C.phi;
                     const P4 dx = fd1(M2.phi, M1.phi, Q1.phi, Q2.phi, p.c1, p.c2);
                     const P4 dxx = fd2(M2.phi, M1.phi, ph, Q1.phi, Q2.phi, p.s1, p.s2, p.s0);
@@ -295,36 +296,36 @@ __global__ void __launch_bounds__(FTHREADS, 1)
                     const P4 dxz = fd1(M2.dz, M1.dz, Q1.dz, Q2.dz, p.c1, p.c2);
                     const P4 dyc = C.dy, dzc = C.dz;
                     const float axx = dot(dx, dx), axy = dot(dx, dyc), axz = dot(dx, dzc);
-                    const float tra = axx + C.ayy + C.azz;
-                    const P4 L = add(dxx, C.lin);
+                    const float tra = axx + Cayy + Cazz;
+                    const P4 L = add(dxx, lin);
+                    // g_i = sum_j d_ij phi.d_j phi; c_i = g_i - Laplacian.d_i phi
                     const float gx = hsum(dot2(dxz, dzc, dot2(dxy, dyc,
                                                    __ffma2_rn(dxx.b, dx.b, __fmul2_rn(dxx.a, dx.a)))));
-                    const float gy = dot(dxy, dx) + C.gy;
-                    const float gz = dot(dxz, dx) + C.gz;
-                    const float cx = gx - dot(L, dx), cy = gy - dot(L, dyc), cz = gz - dot(L, dzc);
+                    const float gy = dot(dxy, dx) + Cgy;
+                    const float gz = dot(dxz, dx) + Cgz;
+                    const float ccx = gx - dot(L, dx), ccy = gy - dot(L, dyc), ccz = gz - dot(L, dzc);
                     // d_ij phi a_ij summed over i, j
-                    const P4 Ha = fma(bc(2.f * axz), dxz, fma(bc(2.f * axy), dxy, fma(bc(axx), dxx, C.qin)));
+                    const P4 Ha = fma(bc(2.f * axz), dxz, fma(bc(2.f * axy), dxy, fma(bc(axx), dxx, qin)));
                     // brace of the Euler-Lagrange equation; G = -2 (brace + m^2 e_0)
-                    P4 br = fma(bc(cz), dzc, fma(bc(cy), dyc, fma(bc(cx), dx, fma(bc(1.f + tra), L, mul(bc(-1.f), Ha)))));
+                    P4 br = fma(bc(ccz), dzc, fma(bc(ccy), dyc, fma(bc(ccx), dx,
+                                fma(bc(1.f + tra), L, mul(bc(-1.f), Ha)))));
                     br.a.x += p.m2;
                     // F = -G + (G.phi) phi = 2 (br - (br.phi) phi)
                     const float bp = dot(br, ph);
                     const P4 Fh = fma(bc(-bp), ph, br);
                     const float f2 = 4.f * dot(Fh, Fh);
-                    P4 t;
-                    P4 vnew;
+                    P4 t, vnew;
                     if (p.mode == MODE_GRADIENT) {
                         t = fma(bc(dt2), Fh, ph);
                     } else {
-                        const P4 vo = use_v ? ld4(vpre[(k + 3) % 5]) : P4{bc(0.f), bc(0.f)};
+                        const P4 vo = use_v ? ld4(sm.vpl[s][ty][tz]) : P4{bc(0.f), bc(0.f)};
                         vnew = fma(bc(dt2), Fh, vo);
                         t = fma(bc(dt), vnew, ph);
                     }
                     const float r = rsqrtf(dot(t, t));
                     const P4 pn = mul(bc(r), t);
-                    // densities: e2 = tr a, e4 = (tr a^2 - a_ij a_ij)/2, e0 ~ 1 - phi^0, b ~ det
-                    const float sq = axx * axx + C.ayy * C.ayy + C.azz * C.azz +
-                                     2.f * (axy * axy + axz * axz + C.ayz * C.ayz);
+                    const float sq = axx * axx + Cayy * Cayy + Cazz * Cazz +
+                                     2.f * (axy * axy + axz * axz + Cayz * Cayz);
                     const float e4 = 0.5f * (tra * tra - sq);
                     // det[phi, d_x phi, d_y phi, d_z phi] by 2x2 minors of rows (phi, d_x) and (d_y, d_z)
                     const float s0 = ph.a.x * dx.a.y - dx.a.x * ph.a.y;
@@ -335,7 +336,6 @@ __global__ void __launch_bounds__(FTHREADS, 1)
                     const float2 q12 = __ffma2_rn(bc(-dzc.a.x), dyc.b, __fmul2_rn(bc(dyc.a.x), dzc.b));
                     const float2 q34 = __ffma2_rn(bc(-dzc.a.y), dyc.b, __fmul2_rn(bc(dyc.a.y), dzc.b));
                     const float q5 = dyc.b.x * dzc.b.y - dzc.b.x * dyc.b.y;
-                    // s1 = s12.x, s2 = s12.y, s3 = s34.x, s4 = s34.y (likewise q)
                     const float det = s0 * q5 - s12.x * q34.y + s12.y * q34.x + s34.x * q12.y -
                                       s34.y * q12.x + s5 * q0;
                     if (valid) {
@@ -350,16 +350,32 @@ __global__ void __launch_bounds__(FTHREADS, 1)
                         a32.fmax2 = fmaxf(a32.fmax2, f2);
                     }
                 }
+                __syncthreads();
+                if (sm.flag) {
+                    failed = true;
+                    break;
+                }
+                // slot s is free again: stream plane pp + NSLOT (and its velocity) into it
+                if (tid == 0 && pp + NSLOT <= pl) issue(pp + NSLOT, s);
+                // ---- in-plane values of plane pp for its own centre, two planes on
+                const P4 dyz = fd1(ld4(DY[ty][tz]), ld4(DY[ty][tz + 1]), ld4(DY[ty][tz + 3]),
+                                   ld4(DY[ty][tz + 4]), p.c1, p.c2);
+                const float ayy = dot(dy, dy), azz = dot(dz, dz), ayz = dot(dy, dz);
+                const P4 lin = add(dyy, dzz);
+                const P4 qin = fma(bc(2.f * ayz), dyz, fma(bc(azz), dzz, mul(bc(ayy), dyy)));
+                const float gyv = hsum(dot2(dyz, dz, __ffma2_rn(dyy.b, dy.b, __fmul2_rn(dyy.a, dy.a))));
+                const float gzv = hsum(dot2(dzz, dz, __ffma2_rn(dyz.b, dy.b, __fmul2_rn(dyz.a, dy.a))));
+                float4 *wrec = &sm.inpl[g % 3][0][tid];
+                wrec[0] = st4(lin);
+                wrec[FTHREADS] = st4(qin);
+                wrec[2 * FTHREADS] = make_float4(gyv, gzv, ayy, azz);
+                wrec[3 * FTHREADS] = make_float4(ayz, 0.f, 0.f, 0.f);
+                ++g;
             }
-            // flush the FP32 partial sums of these (at most 5) planes to FP64
-            acc_d[0] += (double)a32.e2;
-            acc_d[1] += (double)a32.e4;
-            acc_d[2] += (double)a32.e0;
-            acc_d[3] += (double)a32.b;
-            acc_d[4] += (double)a32.f2;
-            acc_d[5] = fmax(acc_d[5], (double)a32.fmax2);
-            a32 = {0, 0, 0, 0, 0, 0};
+            // FP32 partial sums cover at most 20 planes before entering FP64
+            if ((++nouter & 3) == 0) flush(acc_d, a32);
         }
+        flush(acc_d, a32);
     }
 
     if (failed) {
@@ -376,8 +392,8 @@ __global__ void __launch_bounds__(FTHREADS, 1)
     }
 
     // ---- block and grid reductions (FP64, fixed order)
-    acc_d[2] *= 2.0 * (double)p.m2;           // e0 = 2 m^2 (1 - phi^0)
-    acc_d[3] *= -0.050660591821168885;        // b = -det / (2 pi^2)
+    acc_d[2] *= 2.0 * (double)p.m2;     // e0 = 2 m^2 (1 - phi^0)
+    acc_d[3] *= -0.050660591821168885;  // b = -det / (2 pi^2)
     double tot6[6];
     block_reduce<6, 5>(acc_d, sm.red, tot6);
     if (tid == 0) {
@@ -413,13 +429,16 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-static bool make_plane_map(CUtensorMap *m, const void *base, const skyrme_lattice &lat)
+// 3D view (4 n2 floats, n1, n0) of a float4 site array; one box is a
+// box_z-float by box_y-row tile of a single x-plane.
+static bool make_plane_map(CUtensorMap *m, const void *base, const skyrme_lattice &lat,
+                           unsigned box_z, unsigned box_y)
 {
     auto fn = encode_fn();
     if (!fn) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)4 * lat.n[2], (cuuint64_t)lat.n[1], (cuuint64_t)lat.n[0]};
     const cuuint64_t strides[2] = {(cuuint64_t)lat.n[2] * 16, (cuuint64_t)lat.n[1] * lat.n[2] * 16};
-    const cuuint32_t box[3] = {4 * FSZ, FSY, 1};
+    const cuuint32_t box[3] = {box_z, box_y, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), dims, strides,
                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -450,9 +469,21 @@ int f32_fast_blocks(const skyrme_lattice &lat)
 
 cudaError_t launch_step_f32_fast(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s)
 {
-    CUtensorMap m0, m1;
-    if (!make_plane_map(&m0, a.phi[0], lat) || !make_plane_map(&m1, a.phi[1], lat))
+    CUtensorMap m0, m1, v0, v1;
+    if (!make_plane_map(&m0, a.phi[0], lat, 4 * FSZ, FSY) ||
+        !make_plane_map(&m1, a.phi[1], lat, 4 * FSZ, FSY) ||
+        !make_plane_map(&v0, a.vel[0], lat, 4 * FTZ, FTY) ||
+        !make_plane_map(&v1, a.vel[1], lat, 4 * FTZ, FTY))
         return cudaErrorInvalidValue;
+    static thread_local int smem_set_device = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (smem_set_device != dev) {
+        cudaError_t e = cudaFuncSetAttribute(k_step_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sizeof(F32Smem));
+        if (e != cudaSuccess) return e;
+        smem_set_device = dev;
+    }
     F32Params p;
     p.phi[0] = static_cast<float4 *>(a.phi[0]);
     p.phi[1] = static_cast<float4 *>(a.phi[1]);
@@ -477,11 +508,11 @@ cudaError_t launch_step_f32_fast(const skyrme_lattice &lat, const FlowArgs &a, c
     p.dt = (float)a.dt;
     p.h3 = lat.h * lat.h * lat.h;
     p.mode = a.mode;
-    long long grid = sm_count();
+    long long grid = 2LL * sm_count();
     if (grid > p.units) grid = p.units;
     if (grid > f32_fast_blocks(lat)) grid = f32_fast_blocks(lat);
     if (grid < 1) grid = 1;
-    k_step_f32<<<(unsigned)grid, FTHREADS, 0, s>>>(m0, m1, p);
+    k_step_f32<<<(unsigned)grid, FTHREADS, sizeof(F32Smem), s>>>(m0, m1, v0, v1, p);
     return cudaGetLastError();
 }
 
