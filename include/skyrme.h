@@ -150,6 +150,30 @@ skyrme_status skyrme_virial(const skyrme_lattice *lat, skyrme_state *st, double 
 skyrme_status skyrme_forces(const skyrme_lattice *lat, skyrme_state *st, void *force,
                             void *dens, void *stream);
 
+/* ---- allocation-free variant ----
+ * skyrme_energy_static: the six values of skyrme_energy (E, E2, E4, E0, B, V)
+ * for the field `phi` (device; n[0]*n[1]*n[2] sites in the layout and
+ * precision described above), for callers that cannot allocate device memory:
+ * for example code whose device memory is all owned by a host application's
+ * own pool, or a plug-in that may only use the buffers it is handed.  It needs
+ * no skyrme_state and no scratch buffer: its scratch is a fixed 128 KiB array
+ * inside the library, which every GPU that loads the library keeps until the
+ * process exits.  The paper has no counterpart; this is a packaging variant of
+ * the reduction above.
+ *   - Lattices with more than 2048 interior x-planes (n[0] - 4 > 2048) do not
+ *     fit the array and are rejected with SKYRME_EINVAL, as are misaligned or
+ *     null pointers.
+ *   - The first call on each device looks up the array's device address with
+ *     that device current; make that first call before any stream capture.
+ *   - Every call on a device shares the array and leaves its contents behind;
+ *     each call clears what must start at zero.  Calls that overlap on the
+ *     GPU (on other streams or host threads) race, so the caller serialises
+ *     them.
+ *   - It allocates nothing (no cudaMalloc or cudaFree, no library allocator)
+ *     and synchronises `stream` to return the values on the host. */
+skyrme_status skyrme_energy_static(const skyrme_lattice *lat, const void *phi, double out6[6],
+                                   void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -82,6 +82,8 @@ _SIGNATURES = {
                                      ctypes.POINTER(ctypes.c_double), _P]),
     "skyrme_forces": (ctypes.c_int, [ctypes.POINTER(c_lattice), ctypes.POINTER(c_state), _P, _P,
                                      _P]),
+    "skyrme_energy_static": (ctypes.c_int, [ctypes.POINTER(c_lattice), _P,
+                                            ctypes.POINTER(ctypes.c_double), _P]),
 }
 
 _lib = None
