@@ -129,6 +129,57 @@ skyrme_status skyrme_load_field(const skyrme_lattice *lat, skyrme_state *st, voi
  * SKYRME_ENONFINITE (sticky) once a non-finite value has appeared. */
 skyrme_status skyrme_flow_step(const skyrme_lattice *lat, double dt, int nsteps, int mode,
                                skyrme_state *st, skyrme_report *report, void *stream);
+/* ---- the flow as a CUDA graph ----
+ * skyrme_graph_create captures `nsteps` iterations exactly as
+ * skyrme_flow_step launches them (the step kernel and, in ARRESTED mode, the
+ * fix-up check) on `stream`, which must be a stream that can be captured
+ * (not the legacy default stream), and instantiates the graph.  The flow
+ * state lives on the device, so one graph advances the flow by nsteps
+ * iterations every time it is launched, for as long as the state's buffers
+ * exist.  Creation and destruction allocate host and driver resources; a
+ * launch does not.  skyrme_graph_destroy releases them (NULL is accepted). */
+typedef struct skyrme_graph skyrme_graph;
+skyrme_status skyrme_graph_create(const skyrme_lattice *lat, double dt, int nsteps, int mode,
+                                  skyrme_state *st, void *stream, skyrme_graph **out);
+skyrme_status skyrme_graph_launch(skyrme_graph *g, void *stream);
+skyrme_status skyrme_graph_destroy(skyrme_graph *g);
+
+/* ---- batched flow (FP32) ----
+ * Many independent lattices, of uneven sizes, advanced together: every step
+ * is one persistent launch over all of their work (plus, in ARRESTED mode,
+ * one fix-up check launch), and each lattice's energy sums and arrest
+ * decision close as soon as the CTAs that touched it are done.  Each lattice
+ * keeps its own skyrme_state (initialise it with skyrme_init_field or
+ * skyrme_load_field; read its results with skyrme_read_report).
+ *   skyrme_batch_scratch_bytes: size of the caller-owned batch scratch
+ *     (lattice table and per-CTA partial records), 256-byte aligned.
+ *   skyrme_batch_create: validates the states (precision 32 only), encodes
+ *     the lattice table for the default tile shape and uploads it (a
+ *     synchronous copy); the handle owns no device memory.
+ *   skyrme_batch_step: nsteps iterations, asynchronous.
+ *   skyrme_batch_autotune: times every candidate tile shape on these
+ *     lattices with `trials` dry steps each (outputs go to the inactive
+ *     buffers; the flows do not advance) and keeps the fastest.
+ *   skyrme_batch_set_tile / skyrme_batch_tile: choose or query the tile
+ *     shape (0: 8x32, 1: 4x32, 2: 16x16, 3: 8x16 interior sites per CTA) and
+ *     the persistent grid.
+ *   skyrme_batch_graph_create: capture nsteps batched iterations as a
+ *     skyrme_graph (launch and destroy it with skyrme_graph_launch /
+ *     skyrme_graph_destroy).  Re-capture after changing the tile shape. */
+typedef struct skyrme_batch skyrme_batch;
+size_t skyrme_batch_scratch_bytes(int ninst, const skyrme_lattice *lats);
+skyrme_status skyrme_batch_create(int ninst, const skyrme_lattice *lats, skyrme_state *states,
+                                  const double *dt, int mode, void *scratch, size_t scratch_bytes,
+                                  skyrme_batch **out);
+skyrme_status skyrme_batch_step(skyrme_batch *b, int nsteps, void *stream);
+skyrme_status skyrme_batch_autotune(skyrme_batch *b, int trials, void *stream, int *best_tile,
+                                    double *best_ms);
+skyrme_status skyrme_batch_set_tile(skyrme_batch *b, int tile);
+skyrme_status skyrme_batch_tile(const skyrme_batch *b, int *tile, int *ty, int *tz, int *grid);
+skyrme_status skyrme_batch_graph_create(skyrme_batch *b, int nsteps, void *stream,
+                                        skyrme_graph **out);
+skyrme_status skyrme_batch_destroy(skyrme_batch *b);
+
 /* Copy the control block to the host (synchronises the stream). */
 skyrme_status skyrme_read_report(const skyrme_lattice *lat, const skyrme_state *st,
                                  skyrme_report *report, void *stream);

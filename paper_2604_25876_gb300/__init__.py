@@ -84,6 +84,26 @@ _SIGNATURES = {
                                      _P]),
     "skyrme_energy_static": (ctypes.c_int, [ctypes.POINTER(c_lattice), _P,
                                             ctypes.POINTER(ctypes.c_double), _P]),
+    "skyrme_batch_scratch_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.POINTER(c_lattice)]),
+    "skyrme_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(c_lattice),
+                                           ctypes.POINTER(c_state), ctypes.POINTER(ctypes.c_double),
+                                           ctypes.c_int, _P, ctypes.c_size_t,
+                                           ctypes.POINTER(ctypes.c_void_p)]),
+    "skyrme_batch_step": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "skyrme_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int),
+                                             ctypes.POINTER(ctypes.c_double)]),
+    "skyrme_batch_set_tile": (ctypes.c_int, [_P, ctypes.c_int]),
+    "skyrme_batch_tile": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int)]),
+    "skyrme_batch_graph_create": (ctypes.c_int, [_P, ctypes.c_int, _P,
+                                                 ctypes.POINTER(ctypes.c_void_p)]),
+    "skyrme_batch_destroy": (ctypes.c_int, [_P]),
+    "skyrme_graph_create": (ctypes.c_int, [ctypes.POINTER(c_lattice), ctypes.c_double,
+                                           ctypes.c_int, ctypes.c_int, ctypes.POINTER(c_state), _P,
+                                           ctypes.POINTER(ctypes.c_void_p)]),
+    "skyrme_graph_launch": (ctypes.c_int, [_P, _P]),
+    "skyrme_graph_destroy": (ctypes.c_int, [_P]),
 }
 
 _lib = None
@@ -316,3 +336,103 @@ def forces(lat: Lattice, st: State, want_dens: bool = True, stream=None):
                                 ctypes.c_void_p(D.data_ptr()) if D is not None else None,
                                 _stream_ptr(stream, st.device)), "skyrme_forces")
     return F, D
+
+
+class FlowGraph:
+    """A captured CUDA graph of ``nsteps`` flow iterations (skyrme_graph_*).
+    ``stream`` must be a capturable (non-default) torch stream.  Pass
+    ``batch`` instead of (lat, st, dt, mode) to capture batched iterations."""
+
+    def __init__(self, lat: Lattice = None, st: State = None, dt: float = 0.0, nsteps: int = 1,
+                 mode: int = ARRESTED, stream=None, batch=None):
+        torch = _torch()
+        dev = st.device if st is not None else batch.states[0].device
+        self.stream = stream if stream is not None else torch.cuda.Stream(dev)
+        self.nsteps = int(nsteps)
+        h = ctypes.c_void_p()
+        sp = ctypes.c_void_p(self.stream.cuda_stream)
+        if batch is not None:
+            _check(load().skyrme_batch_graph_create(batch._h, self.nsteps, sp, ctypes.byref(h)),
+                   "skyrme_batch_graph_create")
+        else:
+            cl, cs = lat.c(), st.c()
+            _check(load().skyrme_graph_create(ctypes.byref(cl), float(dt), self.nsteps, int(mode),
+                                              ctypes.byref(cs), sp, ctypes.byref(h)),
+                   "skyrme_graph_create")
+        self._h = h
+
+    def launch(self, stream=None):
+        s = stream if stream is not None else self.stream
+        _check(load().skyrme_graph_launch(self._h, ctypes.c_void_p(s.cuda_stream)),
+               "skyrme_graph_launch")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().skyrme_graph_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+TILES = [(8, 32), (4, 32), (16, 16), (8, 16)]
+
+
+class Batch:
+    """Many independent FP32 lattices advanced by one persistent launch per
+    iteration (skyrme_batch_*).  ``states`` keep their own control blocks;
+    read each with :func:`read_report`."""
+
+    def __init__(self, lats, states, dts, mode: int = ARRESTED):
+        torch = _torch()
+        self.lats, self.states = list(lats), list(states)
+        n = len(self.lats)
+        self._cl = (c_lattice * n)(*[l.c() for l in self.lats])
+        self._cs = (c_state * n)(*[st.c() for st in self.states])
+        self._dt = (ctypes.c_double * n)(*[float(d) for d in dts])
+        nbytes = int(load().skyrme_batch_scratch_bytes(n, self._cl))
+        self.scratch = torch.zeros(nbytes, dtype=torch.uint8, device=self.states[0].device)
+        h = ctypes.c_void_p()
+        _check(load().skyrme_batch_create(n, self._cl, self._cs, self._dt, int(mode),
+                                          ctypes.c_void_p(self.scratch.data_ptr()), nbytes,
+                                          ctypes.byref(h)), "skyrme_batch_create")
+        self._h = h
+
+    def step(self, nsteps: int, stream=None):
+        _check(load().skyrme_batch_step(self._h, int(nsteps),
+                                        _stream_ptr(stream, self.states[0].device)),
+               "skyrme_batch_step")
+
+    def autotune(self, trials: int = 3, stream=None):
+        t, ms = ctypes.c_int(), ctypes.c_double()
+        _check(load().skyrme_batch_autotune(self._h, int(trials),
+                                            _stream_ptr(stream, self.states[0].device),
+                                            ctypes.byref(t), ctypes.byref(ms)),
+               "skyrme_batch_autotune")
+        return t.value, ms.value
+
+    def set_tile(self, tile: int):
+        _check(load().skyrme_batch_set_tile(self._h, int(tile)), "skyrme_batch_set_tile")
+
+    def tile(self):
+        t, ty, tz, g = (ctypes.c_int() for _ in range(4))
+        _check(load().skyrme_batch_tile(self._h, ctypes.byref(t), ctypes.byref(ty),
+                                        ctypes.byref(tz), ctypes.byref(g)), "skyrme_batch_tile")
+        return {"tile": t.value, "ty": ty.value, "tz": tz.value, "grid": g.value}
+
+    def reports(self):
+        return [read_report(l, st) for l, st in zip(self.lats, self.states)]
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().skyrme_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

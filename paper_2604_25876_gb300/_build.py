@@ -18,8 +18,9 @@ LIBDIR = os.path.join(HERE, "_lib")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(LIBDIR, "libskyrme.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-fast-math",
-         "--expt-relaxed-constexpr"]
+         "--expt-relaxed-constexpr", "-I" + INCLUDE]
 
 
 def nvcc() -> str:

@@ -20,6 +20,12 @@ int f32_fast_blocks(const skyrme_lattice &lat);
 
 using namespace skyrme;
 
+struct skyrme_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int nsteps = 0;
+};
+
 static thread_local std::string g_last_cuda_error;
 
 static skyrme_status cuda_fail(cudaError_t e, const char *what)
@@ -78,6 +84,42 @@ static skyrme_status check_state(const skyrme_lattice *lat, const skyrme_state *
     if (st->phi[0] == st->phi[1] || st->vel[0] == st->vel[1]) return SKYRME_EINVAL;
     return SKYRME_OK;
 }
+
+namespace skyrme {
+bool state_ok_for_batch(const skyrme_lattice *lat, const skyrme_state *st)
+{
+    return check_state(lat, st) == SKYRME_OK;
+}
+skyrme_status batch_capture(skyrme_batch *b, int nsteps, cudaStream_t s);
+
+// Capture nsteps batched iterations into a graph.
+skyrme_status make_graph(skyrme_batch *b, int nsteps, cudaStream_t s, skyrme_graph **out)
+{
+    *out = nullptr;
+    skyrme_graph *g = new skyrme_graph();
+    g->nsteps = nsteps;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        delete g;
+        return cuda_fail(e, "begin stream capture");
+    }
+    skyrme_status rc = batch_capture(b, nsteps, s);
+    e = cudaStreamEndCapture(s, &g->graph);
+    if (rc != SKYRME_OK || e != cudaSuccess) {
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        return rc != SKYRME_OK ? rc : cuda_fail(e, "end stream capture");
+    }
+    e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g->graph);
+        delete g;
+        return cuda_fail(e, "instantiate graph");
+    }
+    *out = g;
+    return SKYRME_OK;
+}
+}  // namespace skyrme
 
 static FlowArgs make_args(const skyrme_lattice &lat, const skyrme_state &st, double dt, int mode)
 {
@@ -194,22 +236,35 @@ skyrme_status skyrme_load_field(const skyrme_lattice *lat, skyrme_state *st, voi
     return SKYRME_OK;
 }
 
+static skyrme_status launch_iterations(const skyrme_lattice &lat, const FlowArgs &a, int nsteps,
+                                       cudaStream_t s)
+{
+    const bool fast = lat.precision == 32 && f32_fast_path_available(lat);
+    for (int k = 0; k < nsteps; ++k) {
+        if (fast) CK(launch_step_f32_fast(lat, a, s), "step kernel (fp32)");
+        else CK(launch_step(lat, a, s), "step kernel");
+        if (a.mode == SKYRME_ARRESTED) CK(launch_fixup(lat, a, s), "fix-up kernel");
+    }
+    return SKYRME_OK;
+}
+
+static bool mode_ok(int mode)
+{
+    return mode == SKYRME_NEWTON || mode == SKYRME_ARRESTED || mode == SKYRME_GRADIENT;
+}
+
+
 skyrme_status skyrme_flow_step(const skyrme_lattice *lat, double dt, int nsteps, int mode,
                                skyrme_state *st, skyrme_report *report, void *stream)
 {
     skyrme_status rc = check_state(lat, st);
     if (rc != SKYRME_OK) return rc;
     if (!(dt > 0.0) || !isfinite(dt) || nsteps < 0) return SKYRME_EINVAL;
-    if (mode != SKYRME_NEWTON && mode != SKYRME_ARRESTED && mode != SKYRME_GRADIENT)
-        return SKYRME_EINVAL;
+    if (!mode_ok(mode)) return SKYRME_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     FlowArgs a = make_args(*lat, *st, dt, mode);
-    const bool fast = lat->precision == 32 && f32_fast_path_available(*lat);
-    for (int k = 0; k < nsteps; ++k) {
-        if (fast) CK(launch_step_f32_fast(*lat, a, s), "step kernel (fp32)");
-        else CK(launch_step(*lat, a, s), "step kernel");
-        if (mode == SKYRME_ARRESTED) CK(launch_fixup(*lat, a, s), "fix-up kernel");
-    }
+    rc = launch_iterations(*lat, a, nsteps, s);
+    if (rc != SKYRME_OK) return rc;
     if (report) {
         Ctrl c;
         rc = copy_ctrl(*st, &c, s);
@@ -217,6 +272,56 @@ skyrme_status skyrme_flow_step(const skyrme_lattice *lat, double dt, int nsteps,
         fill_report(c, report);
         if (c.status) return static_cast<skyrme_status>(c.status);
     }
+    return SKYRME_OK;
+}
+
+skyrme_status skyrme_graph_create(const skyrme_lattice *lat, double dt, int nsteps, int mode,
+                                  skyrme_state *st, void *stream, skyrme_graph **out)
+{
+    if (!out) return SKYRME_EINVAL;
+    *out = nullptr;
+    skyrme_status rc = check_state(lat, st);
+    if (rc != SKYRME_OK) return rc;
+    if (!(dt > 0.0) || !isfinite(dt) || nsteps < 1 || !mode_ok(mode)) return SKYRME_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    FlowArgs a = make_args(*lat, *st, dt, mode);
+    skyrme_graph *g = new skyrme_graph();
+    g->nsteps = nsteps;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        delete g;
+        return cuda_fail(e, "begin stream capture");
+    }
+    rc = launch_iterations(*lat, a, nsteps, s);
+    e = cudaStreamEndCapture(s, &g->graph);
+    if (rc != SKYRME_OK || e != cudaSuccess) {
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        return rc != SKYRME_OK ? rc : cuda_fail(e, "end stream capture");
+    }
+    e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g->graph);
+        delete g;
+        return cuda_fail(e, "instantiate graph");
+    }
+    *out = g;
+    return SKYRME_OK;
+}
+
+skyrme_status skyrme_graph_launch(skyrme_graph *g, void *stream)
+{
+    if (!g || !g->exec) return SKYRME_EINVAL;
+    CK(cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)), "launch graph");
+    return SKYRME_OK;
+}
+
+skyrme_status skyrme_graph_destroy(skyrme_graph *g)
+{
+    if (!g) return SKYRME_OK;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
     return SKYRME_OK;
 }
 

@@ -1,75 +1,76 @@
-// flow_f32.cu -- FP32 streaming step kernel of the arrested Newton flow.
+// flow_f32.cu -- FP32 streaming step kernel of the arrested Newton flow, for
+// one lattice or a batch of independent lattices of uneven sizes.
 //
 // Same iteration as the tile kernel (Section 3: 4th-order first, second and
 // mixed derivatives, Euler-Lagrange gradient, tangent projection of
 // Eq. "Newton_flow", v += dt F, phi = normalise(phi + dt v); Section 2.1
 // densities summed in FP64), organised for GB300:
 //
-//  * two persistent CTAs per SM (16 warps); the CTAs split the (column,
-//    x-plane) work of the lattice evenly.  A column is an 8 x 32 block of interior (y, z)
-//    sites; a CTA marches along x through contiguous runs of planes.
-//  * each x-plane of the column tile, with its 2-site halo (12 x 36 sites,
-//    6.9 KB), is streamed into a 4-slot shared-memory ring by TMA
-//    (cp.async.bulk.tensor.3d) and an mbarrier per slot; every wait is
-//    bounded and reports SKYRME_ETIMEOUT instead of hanging.
+//  * persistent CTAs (as many as fit, normally two or four per SM) split the
+//    (column, x-plane) work of every lattice in the batch evenly.  A column
+//    is a TY x TZ block of interior (y, z) sites; a CTA marches along x
+//    through contiguous runs of planes, crossing from one lattice into the
+//    next.  Each lattice's energy sums close as soon as the CTAs that
+//    touched it are done (per-lattice arrival counter, last-CTA finish), so
+//    lattices of different sizes need no global barrier.
+//  * each x-plane of the column tile, with its 2-site halo, is streamed into
+//    a 4-slot shared-memory ring by TMA (cp.async.bulk.tensor.3d) with an
+//    mbarrier per slot; every wait is bounded and reports SKYRME_ETIMEOUT
+//    instead of hanging.
 //  * in-plane derivatives (d_y, d_z, d_yy, d_zz) come from the staged plane;
 //    d_yz = d_z(d_y phi) uses a shared-memory exchange of d_y phi (with the
-//    4 z-halo columns computed by 4 lanes per warp); d_x, d_xx, d_xy = d_x(d_y
+//    4 z-halo columns computed by 4 lanes per row); d_x, d_xx, d_xy = d_x(d_y
 //    phi), d_xz = d_x(d_z phi) come from a 5-plane register ring of (phi, d_y
 //    phi, d_z phi) that the x-loop cycles through (unrolled by 5 so no
 //    register is ever moved).  The in-plane contractions a plane contributes
 //    to its own centre two planes later wait in a per-thread shared-memory
 //    ring, and the velocity of each centre plane arrives by TMA together with
-//    the field plane two planes ahead: this keeps the kernel at 128 registers,
-//    two CTAs (16 warps) per SM.
+//    the field plane two planes ahead: 128 registers per thread.
 //  * 4-vector arithmetic uses the packed FP32 pair instructions of sm_100+
 //    (__ffma2_rn / __fadd2_rn / __fmul2_rn): two components per instruction.
 //  * per-site densities are summed in FP32 over at most 20 consecutive planes
-//    and then accumulated in FP64; the block and grid reductions are FP64 in
-//    a fixed order, as in the tile kernel.
+//    and then accumulated in FP64; block and per-lattice reductions are FP64
+//    in a fixed order.
+//  * the tile shape (TY, TZ) is a template parameter; the batch autotuner
+//    times the candidates on the actual lattices and keeps the fastest.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 #include <stdlib.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string.h>
+
+#include <vector>
 
 #include "skyrme_device.cuh"
 #include "skyrme_internal.h"
 
 namespace skyrme {
 
-constexpr int FTY = 8, FTZ = 32;
-constexpr int FTHREADS = FTY * FTZ;  // 256: warp w owns row w of the tile
-constexpr int FSY = FTY + 4, FSZ = FTZ + 4;
 constexpr int NSLOT = 4;
-constexpr unsigned PLANE_BYTES = FSY * FSZ * 16;   // 6912
-constexpr unsigned VPLANE_BYTES = FTY * FTZ * 16;  // 4096
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per plane copy
 
-struct F32Params {
+// One lattice of a step launch: a kernel parameter for a single lattice, an
+// entry of a device table for a batch.
+struct InstDesc {
+    CUtensorMap map[2];   // haloed field planes of phi[0], phi[1]
+    CUtensorMap vmap[2];  // centre-site velocity planes of vel[0], vel[1]
     float4 *phi[2];
     float4 *vel[2];
     Ctrl *ctrl;
-    double *parts;
+    double *parts;         // per-CTA partial records of this lattice
+    long long unit_start;  // first global work unit (column-plane) of the lattice
+    long long units;       // columns * interior planes
     int n0, n1, n2;
-    int nzt;                // column tiles along z
-    int nix;                // interior planes along x
-    long long units;        // columns * nix
-    float c1, c2;           // first-derivative weights / h
-    float s1, s2, s0;       // second-derivative weights / h^2
+    int nzt, nix;          // column tiles along z, interior planes along x
+    int cta_first, cta_count;
+    float c1, c2;          // first-derivative weights / h
+    float s1, s2, s0;      // second-derivative weights / h^2
     float m2, dt;
     double h3;
     int mode;
-};
-
-struct __align__(128) F32Smem {
-    float4 plane[NSLOT][FSY][FSZ];   // haloed field planes (TMA)
-    float4 vpl[NSLOT][FTY][FTZ];     // velocity planes of the centre sites (TMA)
-    float4 dy[2][FTY][FSZ];          // d_y phi exchange for d_yz
-    float4 inpl[3][4][FTHREADS];     // per-thread in-plane values of the last 3 planes
-    unsigned long long bar[NSLOT];
-    double red[8 * (FTHREADS / 32)];
-    int flag;
-    int last;
 };
 
 // ------------------------------------------------------------- PTX helpers
@@ -170,11 +171,6 @@ __device__ __forceinline__ P4 fd2(const P4 &m2, const P4 &m1, const P4 &c, const
     return fma(bc(s0), c, fma(bc(s2), add(p2, m2), mul(bc(s1), add(p1, m1))));
 }
 
-// Per-plane values of one column kept in the register x-ring.
-struct PlaneVals {
-    P4 phi, dy, dz;
-};
-
 struct Acc {
     float e2, e4, e0, b, f2, fmax2;
 };
@@ -190,25 +186,39 @@ __device__ __forceinline__ void flush(double (&acc)[6], Acc &a)
     a = {0, 0, 0, 0, 0, 0};
 }
 
-// ------------------------------------------------------------------ kernel
-__global__ void __launch_bounds__(FTHREADS, 2)
-    k_step_f32(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1,
-               const __grid_constant__ CUtensorMap vmap0, const __grid_constant__ CUtensorMap vmap1,
-               F32Params p)
+// Per-plane values of one column kept in the register x-ring.
+struct PlaneVals {
+    P4 phi, dy, dz;
+};
+
+template <int TY, int TZ> struct __align__(128) StepSmem {
+    float4 plane[NSLOT][TY + 4][TZ + 4];  // haloed field planes (TMA)
+    float4 vpl[NSLOT][TY][TZ];            // velocity planes of the centre sites (TMA)
+    float4 dy[2][TY][TZ + 4];             // d_y phi exchange for d_yz
+    float4 inpl[3][4][TY * TZ];           // per-thread in-plane values of the last 3 planes
+    unsigned long long bar[NSLOT];
+    double red[8 * 16];
+    int flag;
+    int last;
+};
+
+// The step for every lattice of the launch.  BATCHED: lattices come from
+// `table` (ninst entries, ordered by unit_start); otherwise from `one`.
+// dry != 0 (autotuning): outputs land in the inactive buffers and the
+// control blocks are left as they were.
+template <int TY, int TZ, bool BATCHED>
+__global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
+    k_step_f32(const __grid_constant__ InstDesc one, const InstDesc *__restrict__ table, int ninst,
+               long long total_units, int dry)
 {
+    constexpr int THREADS = TY * TZ;
+    constexpr unsigned PLANE_BYTES = (TY + 4) * (TZ + 4) * 16;
+    constexpr unsigned VPLANE_BYTES = TY * TZ * 16;
+    using Smem = StepSmem<TY, TZ>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    F32Smem &sm = *reinterpret_cast<F32Smem *>(smem_raw);
+    Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     const int tid = threadIdx.x;
-    const int ty = tid >> 5, tz = tid & 31;
-    Ctrl *ctrl = p.ctrl;
-    const int cur = __ldcg(&ctrl->cur);
-    const int pred = (p.mode == MODE_ARRESTED) ? __ldcg(&ctrl->pred) : 0;
-    const CUtensorMap *map = cur ? &map1 : &map0;
-    const CUtensorMap *vmap = cur ? &vmap1 : &vmap0;
-    float4 *__restrict__ phiout = p.phi[cur ^ 1];
-    float4 *__restrict__ vout = p.vel[cur ^ 1];
-    const bool use_v = (p.mode != MODE_GRADIENT) && !pred;
-    const float dt = p.dt, dt2 = 2.0f * p.dt;
+    const int ty = tid / TZ, tz = tid % TZ;
 
     if (tid == 0) {
         for (int s = 0; s < NSLOT; ++s) mbar_init(&sm.bar[s], 1);
@@ -217,204 +227,269 @@ __global__ void __launch_bounds__(FTHREADS, 2)
     }
     __syncthreads();
 
-    double acc_d[6] = {0, 0, 0, 0, 0, 0};
-    Acc a32 = {0, 0, 0, 0, 0, 0};
+    const long long u0 = total_units * blockIdx.x / gridDim.x;
+    const long long u1 = total_units * (blockIdx.x + 1) / gridDim.x;
+    int inst = 0;
+    if (BATCHED)
+        while (inst + 1 < ninst && table[inst + 1].unit_start <= u0) ++inst;
     uint32_t g = 0;  // planes consumed by this CTA (ring sequence number)
     bool failed = false;
 
-    const long long u0 = p.units * blockIdx.x / gridDim.x;
-    const long long u1 = p.units * (blockIdx.x + 1) / gridDim.x;
-    const size_t plane_stride = (size_t)p.n1 * p.n2;
+    for (long long us = u0; us < u1 && !failed; ++inst) {
+        // for a single lattice D names the kernel parameter itself, so its
+        // fields stay constant-bank operands instead of occupying registers
+        const InstDesc &D = BATCHED ? table[inst] : one;
+        const long long seg_hi = min(u1, D.unit_start + D.units);
+        Ctrl *ctrl = D.ctrl;
+        const int cur = __ldcg(&ctrl->cur);
+        const int pred = (D.mode == MODE_ARRESTED) ? __ldcg(&ctrl->pred) : 0;
+        const CUtensorMap *map = &D.map[cur];
+        const CUtensorMap *vmap = &D.vmap[cur];
+        float4 *__restrict__ phiout = D.phi[cur ^ 1];
+        float4 *__restrict__ vout = D.vel[cur ^ 1];
+        const int mode = D.mode;
+        const bool use_v = (mode != MODE_GRADIENT) && !pred;
+#define c1 D.c1
+#define c2 D.c2
+#define s1 D.s1
+#define s2 D.s2
+#define s0 D.s0
+#define m2 D.m2
+        const float dt = D.dt, dt2 = 2.0f * D.dt;
+        const int nix = D.nix, nzt = D.nzt, n1 = D.n1, n2 = D.n2;
+        const size_t plane_stride = (size_t)n1 * n2;
+        double acc_d[6] = {0, 0, 0, 0, 0, 0};
+        Acc a32 = {0, 0, 0, 0, 0, 0};
 
-    for (long long us = u0; us < u1 && !failed;) {
-        const long long col = us / p.nix;
-        const long long ue = min(u1, (col + 1) * (long long)p.nix);
-        const int xs = 2 + (int)(us - col * p.nix);
-        const int xe = 2 + (int)(ue - col * p.nix);  // exclusive
-        us = ue;
-        const int y0 = 2 + (int)(col / p.nzt) * FTY, z0 = 2 + (int)(col % p.nzt) * FTZ;
-        const int y = y0 + ty, z = z0 + tz;
-        const bool valid = (y <= p.n1 - 3) && (z <= p.n2 - 3);
-        const size_t col_off = (size_t)y * p.n2 + z;
-        const int pf = xs - 2, pl = xe + 1;  // planes needed by this run
-        // plane q travels with the velocity of centre q - 2 (when that is a centre)
-        auto issue = [&](int q, int slot) {
-            const bool wv = use_v && q - 2 >= xs && q - 2 < xe;
-            mbar_expect_tx(&sm.bar[slot], PLANE_BYTES + (wv ? VPLANE_BYTES : 0u));
-            tma_plane(&sm.plane[slot][0][0], map, &sm.bar[slot], 4 * (z0 - 2), y0 - 2, q);
-            if (wv) tma_plane(&sm.vpl[slot][0][0], vmap, &sm.bar[slot], 4 * z0, y0, q - 2);
-        };
-        if (tid == 0)
-            for (int q = 0; q < NSLOT && pf + q <= pl; ++q) issue(pf + q, (g + q) % NSLOT);
-        PlaneVals ring[5];
-        int nouter = 0;
-        for (int base = pf; base <= pl && !failed; base += 5) {
+        while (us < seg_hi && !failed) {
+            const long long local = us - D.unit_start;
+            const long long col = local / nix;
+            const long long ue = min(seg_hi, D.unit_start + (col + 1) * (long long)nix);
+            const int xs = 2 + (int)(local - col * nix);
+            const int xe = 2 + (int)(ue - D.unit_start - col * nix);  // exclusive
+            us = ue;
+            const int y0 = 2 + (int)(col / nzt) * TY, z0 = 2 + (int)(col % nzt) * TZ;
+            const int y = y0 + ty, z = z0 + tz;
+            const bool valid = (y <= n1 - 3) && (z <= n2 - 3);
+            const size_t col_off = (size_t)y * n2 + z;
+            const int pf = xs - 2, pl = xe + 1;  // planes needed by this run
+            // plane q travels with the velocity of centre q - 2 (when that is a centre)
+            auto issue = [&](int q, int slot) {
+                const bool wv = use_v && q - 2 >= xs && q - 2 < xe;
+                mbar_expect_tx(&sm.bar[slot], PLANE_BYTES + (wv ? VPLANE_BYTES : 0u));
+                tma_plane(&sm.plane[slot][0][0], map, &sm.bar[slot], 4 * (z0 - 2), y0 - 2, q);
+                if (wv) tma_plane(&sm.vpl[slot][0][0], vmap, &sm.bar[slot], 4 * z0, y0, q - 2);
+            };
+            if (tid == 0)
+                for (int q = 0; q < NSLOT && pf + q <= pl; ++q) issue(pf + q, (g + q) % NSLOT);
+            PlaneVals ring[5];
+            int nouter = 0;
+            for (int base = pf; base <= pl && !failed; base += 5) {
 #pragma unroll
-            for (int k = 0; k < 5; ++k) {
-                const int pp = base + k;
-                if (pp > pl) break;
-                const int s = g % NSLOT;
-                const uint32_t par = (g / NSLOT) & 1u;
-                if (!mbar_wait(&sm.bar[s], par)) sm.flag = 1;
-                // ---- arrival of plane pp: in-plane first and second derivatives
-                const float4(*P)[FSZ] = sm.plane[s];
-                const P4 c = ld4(P[ty + 2][tz + 2]);
-                const P4 ym2 = ld4(P[ty][tz + 2]), ym1 = ld4(P[ty + 1][tz + 2]);
-                const P4 yp1 = ld4(P[ty + 3][tz + 2]), yp2 = ld4(P[ty + 4][tz + 2]);
-                const P4 zm2 = ld4(P[ty + 2][tz]), zm1 = ld4(P[ty + 2][tz + 1]);
-                const P4 zp1 = ld4(P[ty + 2][tz + 3]), zp2 = ld4(P[ty + 2][tz + 4]);
-                const P4 dy = fd1(ym2, ym1, yp1, yp2, p.c1, p.c2);
-                const P4 dz = fd1(zm2, zm1, zp1, zp2, p.c1, p.c2);
-                const P4 dyy = fd2(ym2, ym1, c, yp1, yp2, p.s1, p.s2, p.s0);
-                const P4 dzz = fd2(zm2, zm1, c, zp1, zp2, p.s1, p.s2, p.s0);
-                float4(*DY)[FSZ] = sm.dy[g & 1];
-                DY[ty][tz + 2] = st4(dy);
-                if (tz < 4) {  // z-halo columns of d_y phi for this row
-                    const int hc = tz < 2 ? tz : FTZ + tz;
-                    DY[ty][hc] = st4(fd1(ld4(P[ty][hc]), ld4(P[ty + 1][hc]), ld4(P[ty + 3][hc]),
-                                         ld4(P[ty + 4][hc]), p.c1, p.c2));
-                }
-                ring[k].phi = c;
-                ring[k].dy = dy;
-                ring[k].dz = dz;
+                for (int k = 0; k < 5; ++k) {
+                    const int pp = base + k;
+                    if (pp > pl) break;
+                    const int s = g % NSLOT;
+                    const uint32_t par = (g / NSLOT) & 1u;
+                    if (!mbar_wait(&sm.bar[s], par)) sm.flag = 1;
+                    // ---- arrival of plane pp: in-plane first and second derivatives
+                    const float4(*P)[TZ + 4] = sm.plane[s];
+                    const P4 c = ld4(P[ty + 2][tz + 2]);
+                    const P4 ym2 = ld4(P[ty][tz + 2]), ym1 = ld4(P[ty + 1][tz + 2]);
+                    const P4 yp1 = ld4(P[ty + 3][tz + 2]), yp2 = ld4(P[ty + 4][tz + 2]);
+                    const P4 zm2 = ld4(P[ty + 2][tz]), zm1 = ld4(P[ty + 2][tz + 1]);
+                    const P4 zp1 = ld4(P[ty + 2][tz + 3]), zp2 = ld4(P[ty + 2][tz + 4]);
+                    const P4 dy = fd1(ym2, ym1, yp1, yp2, c1, c2);
+                    const P4 dz = fd1(zm2, zm1, zp1, zp2, c1, c2);
+                    const P4 dyy = fd2(ym2, ym1, c, yp1, yp2, s1, s2, s0);
+                    const P4 dzz = fd2(zm2, zm1, c, zp1, zp2, s1, s2, s0);
+                    float4(*DY)[TZ + 4] = sm.dy[g & 1];
+                    DY[ty][tz + 2] = st4(dy);
+                    if (tz < 4) {  // z-halo columns of d_y phi for this row
+                        const int hc = tz < 2 ? tz : TZ + tz;
+                        DY[ty][hc] = st4(fd1(ld4(P[ty][hc]), ld4(P[ty + 1][hc]), ld4(P[ty + 3][hc]),
+                                             ld4(P[ty + 4][hc]), c1, c2));
+                    }
+                    ring[k].phi = c;
+                    ring[k].dy = dy;
+                    ring[k].dz = dz;
 
-                // ---- centre x = pp - 2: x-derivatives, physics, update
-                const int x = pp - 2;
-                if (x >= xs) {
-                    const PlaneVals &M2 = ring[(k + 1) % 5], &M1 = ring[(k + 2) % 5];
-                    const PlaneVals &C = ring[(k + 3) % 5], &Q1 = ring[(k + 4) % 5];
-                    const PlaneVals &Q2 = ring[k];
-                    const float4 *rec = &sm.inpl[(g + 1) % 3][0][tid];  // plane x = pp - 2
-                    const P4 lin = ld4(rec[0]), qin = ld4(rec[FTHREADS]);
-                    const float4 r2 = rec[2 * FTHREADS];
-                    const float Cgy = r2.x, Cgz = r2.y, Cayy = r2.z, Cazz = r2.w;
-                    const float Cayz = rec[3 * FTHREADS].x;
-                    const P4 ph = C.phi;
-                    const P4 dx = fd1(M2.phi, M1.phi, Q1.phi, Q2.phi, p.c1, p.c2);
-                    const P4 dxx = fd2(M2.phi, M1.phi, ph, Q1.phi, Q2.phi, p.s1, p.s2, p.s0);
-                    const P4 dxy = fd1(M2.dy, M1.dy, Q1.dy, Q2.dy, p.c1, p.c2);
-                    const P4 dxz = fd1(M2.dz, M1.dz, Q1.dz, Q2.dz, p.c1, p.c2);
-                    const P4 dyc = C.dy, dzc = C.dz;
-                    const float axx = dot(dx, dx), axy = dot(dx, dyc), axz = dot(dx, dzc);
-                    const float tra = axx + Cayy + Cazz;
-                    const P4 L = add(dxx, lin);
-                    // g_i = sum_j d_ij phi.d_j phi; c_i = g_i - Laplacian.d_i phi
-                    const float gx = hsum(dot2(dxz, dzc, dot2(dxy, dyc,
-                                                   __ffma2_rn(dxx.b, dx.b, __fmul2_rn(dxx.a, dx.a)))));
-                    const float gy = dot(dxy, dx) + Cgy;
-                    const float gz = dot(dxz, dx) + Cgz;
-                    const float ccx = gx - dot(L, dx), ccy = gy - dot(L, dyc), ccz = gz - dot(L, dzc);
-                    // d_ij phi a_ij summed over i, j
-                    const P4 Ha = fma(bc(2.f * axz), dxz, fma(bc(2.f * axy), dxy, fma(bc(axx), dxx, qin)));
-                    // brace of the Euler-Lagrange equation; G = -2 (brace + m^2 e_0)
-                    P4 br = fma(bc(ccz), dzc, fma(bc(ccy), dyc, fma(bc(ccx), dx,
-                                fma(bc(1.f + tra), L, mul(bc(-1.f), Ha)))));
-                    br.a.x += p.m2;
-                    // F = -G + (G.phi) phi = 2 (br - (br.phi) phi)
-                    const float bp = dot(br, ph);
-                    const P4 Fh = fma(bc(-bp), ph, br);
-                    const float f2 = 4.f * dot(Fh, Fh);
-                    P4 t, vnew;
-                    if (p.mode == MODE_GRADIENT) {
-                        t = fma(bc(dt2), Fh, ph);
-                    } else {
-                        const P4 vo = use_v ? ld4(sm.vpl[s][ty][tz]) : P4{bc(0.f), bc(0.f)};
-                        vnew = fma(bc(dt2), Fh, vo);
-                        t = fma(bc(dt), vnew, ph);
+                    // ---- centre x = pp - 2: x-derivatives, physics, update
+                    const int x = pp - 2;
+                    if (x >= xs) {
+                        const PlaneVals &M2 = ring[(k + 1) % 5], &M1 = ring[(k + 2) % 5];
+                        const PlaneVals &C = ring[(k + 3) % 5], &Q1 = ring[(k + 4) % 5];
+                        const PlaneVals &Q2 = ring[k];
+                        const float4 *rec = &sm.inpl[(g + 1) % 3][0][tid];  // plane x = pp - 2
+                        const P4 lin = ld4(rec[0]), qin = ld4(rec[THREADS]);
+                        const float4 r2 = rec[2 * THREADS];
+                        const float Cgy = r2.x, Cgz = r2.y, Cayy = r2.z, Cazz = r2.w;
+                        const float Cayz = rec[3 * THREADS].x;
+                        const P4 ph = C.phi;
+                        const P4 dx = fd1(M2.phi, M1.phi, Q1.phi, Q2.phi, c1, c2);
+                        const P4 dxx = fd2(M2.phi, M1.phi, ph, Q1.phi, Q2.phi, s1, s2, s0);
+                        const P4 dxy = fd1(M2.dy, M1.dy, Q1.dy, Q2.dy, c1, c2);
+                        const P4 dxz = fd1(M2.dz, M1.dz, Q1.dz, Q2.dz, c1, c2);
+                        const P4 dyc = C.dy, dzc = C.dz;
+                        const float axx = dot(dx, dx), axy = dot(dx, dyc), axz = dot(dx, dzc);
+                        const float tra = axx + Cayy + Cazz;
+                        const P4 L = add(dxx, lin);
+                        // g_i = sum_j d_ij phi.d_j phi; c_i = g_i - Laplacian.d_i phi
+                        const float gx = hsum(dot2(dxz, dzc, dot2(dxy, dyc,
+                                                       __ffma2_rn(dxx.b, dx.b, __fmul2_rn(dxx.a, dx.a)))));
+                        const float gy = dot(dxy, dx) + Cgy;
+                        const float gz = dot(dxz, dx) + Cgz;
+                        const float ccx = gx - dot(L, dx), ccy = gy - dot(L, dyc), ccz = gz - dot(L, dzc);
+                        // d_ij phi a_ij summed over i, j
+                        const P4 Ha = fma(bc(2.f * axz), dxz, fma(bc(2.f * axy), dxy, fma(bc(axx), dxx, qin)));
+                        // brace of the Euler-Lagrange equation; G = -2 (brace + m^2 e_0)
+                        P4 br = fma(bc(ccz), dzc, fma(bc(ccy), dyc, fma(bc(ccx), dx,
+                                    fma(bc(1.f + tra), L, mul(bc(-1.f), Ha)))));
+                        br.a.x += m2;
+                        // F = -G + (G.phi) phi = 2 (br - (br.phi) phi)
+                        const float bp = dot(br, ph);
+                        const P4 Fh = fma(bc(-bp), ph, br);
+                        const float f2 = 4.f * dot(Fh, Fh);
+                        P4 t, vnew;
+                        if (mode == MODE_GRADIENT) {
+                            t = fma(bc(dt2), Fh, ph);
+                        } else {
+                            const P4 vo = use_v ? ld4(sm.vpl[s][ty][tz]) : P4{bc(0.f), bc(0.f)};
+                            vnew = fma(bc(dt2), Fh, vo);
+                            t = fma(bc(dt), vnew, ph);
+                        }
+                        const float r = rsqrtf(dot(t, t));
+                        const P4 pn = mul(bc(r), t);
+                        const float sq = axx * axx + Cayy * Cayy + Cazz * Cazz +
+                                         2.f * (axy * axy + axz * axz + Cayz * Cayz);
+                        const float e4 = 0.5f * (tra * tra - sq);
+                        // det[phi, d_x phi, d_y phi, d_z phi] by 2x2 minors of rows (phi, d_x), (d_y, d_z)
+                        const float q_s0 = ph.a.x * dx.a.y - dx.a.x * ph.a.y;
+                        const float2 s12 = __ffma2_rn(bc(-dx.a.x), ph.b, __fmul2_rn(bc(ph.a.x), dx.b));
+                        const float2 s34 = __ffma2_rn(bc(-dx.a.y), ph.b, __fmul2_rn(bc(ph.a.y), dx.b));
+                        const float q_s5 = ph.b.x * dx.b.y - dx.b.x * ph.b.y;
+                        const float q0 = dyc.a.x * dzc.a.y - dzc.a.x * dyc.a.y;
+                        const float2 q12 = __ffma2_rn(bc(-dzc.a.x), dyc.b, __fmul2_rn(bc(dyc.a.x), dzc.b));
+                        const float2 q34 = __ffma2_rn(bc(-dzc.a.y), dyc.b, __fmul2_rn(bc(dyc.a.y), dzc.b));
+                        const float q5 = dyc.b.x * dzc.b.y - dzc.b.x * dyc.b.y;
+                        const float det = q_s0 * q5 - s12.x * q34.y + s12.y * q34.x + s34.x * q12.y -
+                                          s34.y * q12.x + q_s5 * q0;
+                        if (valid) {
+                            const size_t si = (size_t)x * plane_stride + col_off;
+                            __stcs(phiout + si, st4(pn));
+                            if (mode != MODE_GRADIENT) __stcs(vout + si, st4(vnew));
+                            a32.e2 += tra;
+                            a32.e4 += e4;
+                            a32.e0 += 1.f - ph.a.x;
+                            a32.b += det;
+                            a32.f2 += f2;
+                            a32.fmax2 = fmaxf(a32.fmax2, f2);
+                        }
                     }
-                    const float r = rsqrtf(dot(t, t));
-                    const P4 pn = mul(bc(r), t);
-                    const float sq = axx * axx + Cayy * Cayy + Cazz * Cazz +
-                                     2.f * (axy * axy + axz * axz + Cayz * Cayz);
-                    const float e4 = 0.5f * (tra * tra - sq);
-                    // det[phi, d_x phi, d_y phi, d_z phi] by 2x2 minors of rows (phi, d_x) and (d_y, d_z)
-                    const float s0 = ph.a.x * dx.a.y - dx.a.x * ph.a.y;
-                    const float2 s12 = __ffma2_rn(bc(-dx.a.x), ph.b, __fmul2_rn(bc(ph.a.x), dx.b));
-                    const float2 s34 = __ffma2_rn(bc(-dx.a.y), ph.b, __fmul2_rn(bc(ph.a.y), dx.b));
-                    const float s5 = ph.b.x * dx.b.y - dx.b.x * ph.b.y;
-                    const float q0 = dyc.a.x * dzc.a.y - dzc.a.x * dyc.a.y;
-                    const float2 q12 = __ffma2_rn(bc(-dzc.a.x), dyc.b, __fmul2_rn(bc(dyc.a.x), dzc.b));
-                    const float2 q34 = __ffma2_rn(bc(-dzc.a.y), dyc.b, __fmul2_rn(bc(dyc.a.y), dzc.b));
-                    const float q5 = dyc.b.x * dzc.b.y - dzc.b.x * dyc.b.y;
-                    const float det = s0 * q5 - s12.x * q34.y + s12.y * q34.x + s34.x * q12.y -
-                                      s34.y * q12.x + s5 * q0;
-                    if (valid) {
-                        const size_t si = (size_t)x * plane_stride + col_off;
-                        __stcs(phiout + si, st4(pn));
-                        if (p.mode != MODE_GRADIENT) __stcs(vout + si, st4(vnew));
-                        a32.e2 += tra;
-                        a32.e4 += e4;
-                        a32.e0 += 1.f - ph.a.x;
-                        a32.b += det;
-                        a32.f2 += f2;
-                        a32.fmax2 = fmaxf(a32.fmax2, f2);
+                    __syncthreads();
+                    if (sm.flag) {
+                        failed = true;
+                        break;
                     }
+                    // slot s is free again: stream plane pp + NSLOT (and its velocity) into it
+                    if (tid == 0 && pp + NSLOT <= pl) issue(pp + NSLOT, s);
+                    // ---- in-plane values of plane pp for its own centre, two planes on
+                    const P4 dyz = fd1(ld4(DY[ty][tz]), ld4(DY[ty][tz + 1]), ld4(DY[ty][tz + 3]),
+                                       ld4(DY[ty][tz + 4]), c1, c2);
+                    const float ayy = dot(dy, dy), azz = dot(dz, dz), ayz = dot(dy, dz);
+                    const P4 lin = add(dyy, dzz);
+                    const P4 qin = fma(bc(2.f * ayz), dyz, fma(bc(azz), dzz, mul(bc(ayy), dyy)));
+                    const float gyv = hsum(dot2(dyz, dz, __ffma2_rn(dyy.b, dy.b, __fmul2_rn(dyy.a, dy.a))));
+                    const float gzv = hsum(dot2(dzz, dz, __ffma2_rn(dyz.b, dy.b, __fmul2_rn(dyz.a, dy.a))));
+                    float4 *wrec = &sm.inpl[g % 3][0][tid];
+                    wrec[0] = st4(lin);
+                    wrec[THREADS] = st4(qin);
+                    wrec[2 * THREADS] = make_float4(gyv, gzv, ayy, azz);
+                    wrec[3 * THREADS] = make_float4(ayz, 0.f, 0.f, 0.f);
+                    ++g;
                 }
-                __syncthreads();
-                if (sm.flag) {
-                    failed = true;
-                    break;
-                }
-                // slot s is free again: stream plane pp + NSLOT (and its velocity) into it
-                if (tid == 0 && pp + NSLOT <= pl) issue(pp + NSLOT, s);
-                // ---- in-plane values of plane pp for its own centre, two planes on
-                const P4 dyz = fd1(ld4(DY[ty][tz]), ld4(DY[ty][tz + 1]), ld4(DY[ty][tz + 3]),
-                                   ld4(DY[ty][tz + 4]), p.c1, p.c2);
-                const float ayy = dot(dy, dy), azz = dot(dz, dz), ayz = dot(dy, dz);
-                const P4 lin = add(dyy, dzz);
-                const P4 qin = fma(bc(2.f * ayz), dyz, fma(bc(azz), dzz, mul(bc(ayy), dyy)));
-                const float gyv = hsum(dot2(dyz, dz, __ffma2_rn(dyy.b, dy.b, __fmul2_rn(dyy.a, dy.a))));
-                const float gzv = hsum(dot2(dzz, dz, __ffma2_rn(dyz.b, dy.b, __fmul2_rn(dyz.a, dy.a))));
-                float4 *wrec = &sm.inpl[g % 3][0][tid];
-                wrec[0] = st4(lin);
-                wrec[FTHREADS] = st4(qin);
-                wrec[2 * FTHREADS] = make_float4(gyv, gzv, ayy, azz);
-                wrec[3 * FTHREADS] = make_float4(ayz, 0.f, 0.f, 0.f);
-                ++g;
+                // FP32 partial sums cover at most 20 planes before entering FP64
+                if ((++nouter & 3) == 0) flush(acc_d, a32);
             }
-            // FP32 partial sums cover at most 20 planes before entering FP64
-            if ((++nouter & 3) == 0) flush(acc_d, a32);
+            flush(acc_d, a32);
         }
-        flush(acc_d, a32);
+#undef c1
+#undef c2
+#undef s1
+#undef s2
+#undef s0
+        if (failed) break;
+
+        // ---- this CTA is done with lattice D: block reduction, per-lattice finish
+        acc_d[2] *= 2.0 * (double)m2;        // e0 = 2 m^2 (1 - phi^0)
+#undef m2
+        acc_d[3] *= -0.050660591821168885;  // b = -det / (2 pi^2)
+        double tot6[6];
+        // the in-plane ring is free between lattices: it hosts the block reduction
+        block_reduce_wide<6, 5>(acc_d, reinterpret_cast<double *>(&sm.inpl[0][0][0]), tot6);
+        if (tid == 0) {
+            double *recp = D.parts + (size_t)(blockIdx.x - D.cta_first) * kPartialDoubles;
+            for (int q = 0; q < 6; ++q) recp[q] = tot6[q];
+            recp[6] = recp[7] = 0.0;
+            __threadfence();
+            sm.last = (atomicAdd(&ctrl->done, 1u) == (unsigned)(D.cta_count - 1));
+        }
+        __syncthreads();
+        if (sm.last) {
+            __threadfence();
+            double tot[kPartialDoubles];
+            reduce_partials(D.parts, D.cta_count, sm.red, tot);
+            if (tid == 0) {
+                tot[6] = (double)(D.n0 - 4) * (double)(n1 - 4) * (double)(n2 - 4);
+                if (dry)
+                    ctrl->done = 0;
+                else
+                    finish_step(ctrl, tot, D.h3, mode, pred);
+            }
+        }
+        __syncthreads();
     }
 
     if (failed) {
         // a plane copy never landed: record it, let in-flight copies finish
-        // (bounded), and leave without touching the reduction counter
+        // (bounded), and leave without closing the lattice's reduction
         if (tid == 0) {
-            atomicExch(&ctrl->status, (int)DEV_TIMEOUT);
+            const InstDesc &Df = BATCHED ? table[inst] : one;
+            atomicExch(&Df.ctrl->status, (int)DEV_TIMEOUT);
             for (int s = 0; s < NSLOT; ++s) {
                 (void)mbar_wait(&sm.bar[s], 0, 50000000ull);
                 (void)mbar_wait(&sm.bar[s], 1, 50000000ull);
             }
         }
-        return;
-    }
-
-    // ---- block and grid reductions (FP64, fixed order)
-    acc_d[2] *= 2.0 * (double)p.m2;     // e0 = 2 m^2 (1 - phi^0)
-    acc_d[3] *= -0.050660591821168885;  // b = -det / (2 pi^2)
-    double tot6[6];
-    block_reduce<6, 5>(acc_d, sm.red, tot6);
-    if (tid == 0) {
-        double *rec = p.parts + (size_t)blockIdx.x * kPartialDoubles;
-        for (int q = 0; q < 6; ++q) rec[q] = tot6[q];
-        rec[6] = rec[7] = 0.0;
-        __threadfence();
-        sm.last = (atomicAdd(&ctrl->done, 1u) == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!sm.last) return;
-    __threadfence();
-    double tot[kPartialDoubles];
-    reduce_partials(p.parts, gridDim.x, sm.red, tot);
-    if (tid == 0) {
-        tot[6] = (double)(p.n0 - 4) * (double)(p.n1 - 4) * (double)(p.n2 - 4);
-        finish_step(ctrl, tot, p.h3, p.mode, pred);
     }
 }
 
-// ------------------------------------------------------------------- host
+// Pointwise correction of a mispredicted arrest in any lattice of a batch:
+// blockIdx.y selects the lattice, whose CTAs leave at once when its flag is 0.
+__global__ void k_fixup_batch(const InstDesc *__restrict__ table)
+{
+    const InstDesc *D = table + blockIdx.y;
+    const int fix = __ldcg(&D->ctrl->fix);
+    if (fix == 0) return;
+    const int nb = __ldcg(&D->ctrl->cur), ob = nb ^ 1;
+    const int ix = D->n0 - 4, iy = D->n1 - 4, iz = D->n2 - 4;
+    const size_t total = (size_t)ix * iy * iz;
+    const float sgn = (float)fix, dt = D->dt;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int z = 2 + (int)(i % iz), y = 2 + (int)((i / iz) % iy), x = 2 + (int)(i / ((size_t)iz * iy));
+        const size_t s = ((size_t)x * D->n1 + y) * D->n2 + z;
+        const float4 vn = D->vel[nb][s], vo = D->vel[ob][s], fo = D->phi[ob][s];
+        const float4 v = make_float4(vn.x + sgn * vo.x, vn.y + sgn * vo.y, vn.z + sgn * vo.z,
+                                     vn.w + sgn * vo.w);
+        const float4 t = make_float4(fo.x + dt * v.x, fo.y + dt * v.y, fo.z + dt * v.z, fo.w + dt * v.w);
+        const float r = rsqrtf(t.x * t.x + t.y * t.y + t.z * t.z + t.w * t.w);
+        D->vel[nb][s] = v;
+        D->phi[nb][s] = make_float4(t.x * r, t.y * r, t.z * r, t.w * r);
+    }
+}
+
+// ---------------------------------------------------- tensor maps
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -446,6 +521,8 @@ static bool make_plane_map(CUtensorMap *m, const void *base, const skyrme_lattic
     return r == CUDA_SUCCESS;
 }
 
+
+// ------------------------------------------------------------------- host
 static int sm_count()
 {
     int dev = 0, n = 0;
@@ -454,66 +531,380 @@ static int sm_count()
     return n > 0 ? n : 152;
 }
 
+constexpr int kMaxGrid = 1216;  // persistent CTAs per launch (partial records per lattice)
+
+struct TileShape {
+    int ty, tz;
+};
+// Autotuner candidates: (rows, columns) of interior sites per CTA
+static const TileShape kTiles[] = {{8, 32}, {4, 32}, {16, 16}, {8, 16}};
+constexpr int kNumTiles = 4;
+
+template <int TY, int TZ, bool B> static void *kernel_ptr()
+{
+    return reinterpret_cast<void *>(&k_step_f32<TY, TZ, B>);
+}
+
+template <int TY, int TZ, bool B>
+static cudaError_t launch_shape(const InstDesc &one, const InstDesc *table, int ninst,
+                                long long units, int grid, int dry, cudaStream_t s)
+{
+    static std::mutex mu;
+    static bool done[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (dev < 64 && !done[dev]) {
+            cudaError_t e = cudaFuncSetAttribute(k_step_f32<TY, TZ, B>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)sizeof(StepSmem<TY, TZ>));
+            if (e != cudaSuccess) return e;
+            done[dev] = true;
+        }
+    }
+    k_step_f32<TY, TZ, B><<<(unsigned)grid, TY * TZ, sizeof(StepSmem<TY, TZ>), s>>>(one, table, ninst,
+                                                                                     units, dry);
+    return cudaGetLastError();
+}
+
+template <bool B>
+static cudaError_t launch_tile(int tile, const InstDesc &one, const InstDesc *table, int ninst,
+                               long long units, int grid, int dry, cudaStream_t s)
+{
+    switch (tile) {
+    case 0: return launch_shape<8, 32, B>(one, table, ninst, units, grid, dry, s);
+    case 1: return launch_shape<4, 32, B>(one, table, ninst, units, grid, dry, s);
+    case 2: return launch_shape<16, 16, B>(one, table, ninst, units, grid, dry, s);
+    default: return launch_shape<8, 16, B>(one, table, ninst, units, grid, dry, s);
+    }
+}
+
+// Persistent CTAs of one tile shape that fit on the device.
+template <int TY, int TZ, bool B> static int occupancy_of()
+{
+    int n = 0;
+    cudaFuncSetAttribute(k_step_f32<TY, TZ, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(StepSmem<TY, TZ>));
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_f32<TY, TZ, B>, TY * TZ,
+                                                      sizeof(StepSmem<TY, TZ>)) != cudaSuccess)
+        n = 1;
+    return n > 0 ? n : 1;
+}
+
+static int blocks_per_sm(int tile, bool batched)
+{
+    static std::mutex mu;
+    static int cache[2][kNumTiles] = {{0}};
+    std::lock_guard<std::mutex> lock(mu);
+    int &c = cache[batched][tile];
+    if (!c) {
+        switch (tile * 2 + (batched ? 1 : 0)) {
+        case 0: c = occupancy_of<8, 32, false>(); break;
+        case 1: c = occupancy_of<8, 32, true>(); break;
+        case 2: c = occupancy_of<4, 32, false>(); break;
+        case 3: c = occupancy_of<4, 32, true>(); break;
+        case 4: c = occupancy_of<16, 16, false>(); break;
+        case 5: c = occupancy_of<16, 16, true>(); break;
+        case 6: c = occupancy_of<8, 16, false>(); break;
+        default: c = occupancy_of<8, 16, true>(); break;
+        }
+    }
+    return c;
+}
+
+
+// Lattice description for a tile shape; the work partition is filled later.
+static bool fill_desc(InstDesc &d, const skyrme_lattice &lat, const skyrme_state &st, Ctrl *ctrl,
+                      double dt, int mode, int tile)
+{
+    const int ty = kTiles[tile].ty, tz = kTiles[tile].tz;
+    memset(&d, 0, sizeof(d));
+    for (int i = 0; i < 2; ++i) {
+        if (!make_plane_map(&d.map[i], st.phi[i], lat, 4 * (tz + 4), ty + 4)) return false;
+        if (!make_plane_map(&d.vmap[i], st.vel[i], lat, 4 * tz, ty)) return false;
+        d.phi[i] = static_cast<float4 *>(st.phi[i]);
+        d.vel[i] = static_cast<float4 *>(st.vel[i]);
+    }
+    d.ctrl = ctrl;
+    d.n0 = lat.n[0];
+    d.n1 = lat.n[1];
+    d.n2 = lat.n[2];
+    const int nyt = (lat.n[1] - 4 + ty - 1) / ty;
+    d.nzt = (lat.n[2] - 4 + tz - 1) / tz;
+    d.nix = lat.n[0] - 4;
+    d.units = (long long)nyt * d.nzt * d.nix;
+    const double ih = 1.0 / lat.h, ih2 = ih * ih;
+    d.c1 = (float)(2.0 / 3.0 * ih);
+    d.c2 = (float)(-1.0 / 12.0 * ih);
+    d.s1 = (float)(4.0 / 3.0 * ih2);
+    d.s2 = (float)(-1.0 / 12.0 * ih2);
+    d.s0 = (float)(-2.5 * ih2);
+    d.m2 = (float)(lat.m * lat.m);
+    d.dt = (float)dt;
+    d.h3 = lat.h * lat.h * lat.h;
+    d.mode = mode;
+    return true;
+}
+
+// Split total units over `grid` CTAs and record, for each lattice, the CTAs
+// that touch it; partial records are laid out lattice after lattice.
+static void partition(std::vector<InstDesc> &ds, int grid, double *parts)
+{
+    long long total = 0;
+    for (auto &d : ds) {
+        d.unit_start = total;
+        total += d.units;
+    }
+    size_t off = 0;
+    for (auto &d : ds) {
+        const long long lo = d.unit_start, hi = d.unit_start + d.units;
+        int first = -1, count = 0;
+        for (int b = 0; b < grid; ++b) {
+            const long long b0 = total * b / grid, b1 = total * (b + 1) / grid;
+            if (b1 > lo && b0 < hi) {
+                if (first < 0) first = b;
+                ++count;
+            }
+        }
+        d.cta_first = first;
+        d.cta_count = count;
+        d.parts = parts + off * kPartialDoubles;
+        off += (size_t)count;
+    }
+}
+
+static long long total_units(const std::vector<InstDesc> &ds)
+{
+    long long t = 0;
+    for (auto &d : ds) t += d.units;
+    return t;
+}
+
+static int grid_for(int tile, bool batched, long long units)
+{
+    long long g = (long long)sm_count() * blocks_per_sm(tile, batched);
+    g = std::min<long long>(g, units);
+    g = std::min<long long>(g, kMaxGrid);
+    return (int)std::max<long long>(g, 1);
+}
+
 bool f32_fast_path_available(const skyrme_lattice &lat)
 {
-    // the streaming kernel needs 16-byte aligned TMA rows (always true for
-    // float4 sites) and a driver that exposes the tensor-map encoder
+    // the streaming kernel needs the driver's tensor-map encoder
     return lat.precision == 32 && encode_fn() != nullptr;
 }
 
 int f32_fast_blocks(const skyrme_lattice &lat)
 {
     (void)lat;
-    return 1216;  // upper bound on the persistent grid (one CTA per SM)
+    return kMaxGrid;
 }
 
 cudaError_t launch_step_f32_fast(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s)
 {
-    CUtensorMap m0, m1, v0, v1;
-    if (!make_plane_map(&m0, a.phi[0], lat, 4 * FSZ, FSY) ||
-        !make_plane_map(&m1, a.phi[1], lat, 4 * FSZ, FSY) ||
-        !make_plane_map(&v0, a.vel[0], lat, 4 * FTZ, FTY) ||
-        !make_plane_map(&v1, a.vel[1], lat, 4 * FTZ, FTY))
-        return cudaErrorInvalidValue;
-    static thread_local int smem_set_device = -1;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (smem_set_device != dev) {
-        cudaError_t e = cudaFuncSetAttribute(k_step_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sizeof(F32Smem));
-        if (e != cudaSuccess) return e;
-        smem_set_device = dev;
+    const int tile = 0;
+    skyrme_state st;
+    for (int i = 0; i < 2; ++i) {
+        st.phi[i] = a.phi[i];
+        st.vel[i] = a.vel[i];
     }
-    F32Params p;
-    p.phi[0] = static_cast<float4 *>(a.phi[0]);
-    p.phi[1] = static_cast<float4 *>(a.phi[1]);
-    p.vel[0] = static_cast<float4 *>(a.vel[0]);
-    p.vel[1] = static_cast<float4 *>(a.vel[1]);
-    p.ctrl = static_cast<Ctrl *>(a.ctrl);
-    p.parts = a.step_parts;
-    p.n0 = lat.n[0];
-    p.n1 = lat.n[1];
-    p.n2 = lat.n[2];
-    const int nyt = (lat.n[1] - 4 + FTY - 1) / FTY;
-    p.nzt = (lat.n[2] - 4 + FTZ - 1) / FTZ;
-    p.nix = lat.n[0] - 4;
-    p.units = (long long)nyt * p.nzt * p.nix;
-    const double ih = 1.0 / lat.h, ih2 = ih * ih;
-    p.c1 = (float)(2.0 / 3.0 * ih);
-    p.c2 = (float)(-1.0 / 12.0 * ih);
-    p.s1 = (float)(4.0 / 3.0 * ih2);
-    p.s2 = (float)(-1.0 / 12.0 * ih2);
-    p.s0 = (float)(-2.5 * ih2);
-    p.m2 = (float)(lat.m * lat.m);
-    p.dt = (float)a.dt;
-    p.h3 = lat.h * lat.h * lat.h;
-    p.mode = a.mode;
-    long long grid = 2LL * sm_count();
-    if (grid > p.units) grid = p.units;
-    if (grid > f32_fast_blocks(lat)) grid = f32_fast_blocks(lat);
-    if (grid < 1) grid = 1;
-    k_step_f32<<<(unsigned)grid, FTHREADS, sizeof(F32Smem), s>>>(m0, m1, v0, v1, p);
-    return cudaGetLastError();
+    std::vector<InstDesc> ds(1);
+    if (!fill_desc(ds[0], lat, st, static_cast<Ctrl *>(a.ctrl), a.dt, a.mode, tile))
+        return cudaErrorInvalidValue;
+    const int grid = grid_for(tile, false, ds[0].units);
+    partition(ds, grid, a.step_parts);
+    return launch_tile<false>(tile, ds[0], nullptr, 1, ds[0].units, grid, 0, s);
 }
 
+}  // namespace skyrme
+
+// ---------------------------------------------------------- batch C ABI
+using namespace skyrme;
+
+struct skyrme_batch {
+    int ninst = 0;
+    int mode = 0;
+    int tile = 0;
+    int grid = 1;
+    long long units = 0;
+    std::vector<skyrme_lattice> lats;
+    std::vector<skyrme_state> states;
+    std::vector<double> dt;
+    InstDesc *d_table = nullptr;  // in the caller's batch scratch
+    double *d_parts = nullptr;
+    size_t fixup_blocks = 32;
+};
+
+static size_t table_bytes(int ninst) { return ((size_t)ninst * sizeof(InstDesc) + 255) & ~(size_t)255; }
+static size_t batch_parts_bytes(int ninst)
+{
+    return ((size_t)(kMaxGrid + ninst) * kPartialDoubles * sizeof(double) + 255) & ~(size_t)255;
+}
+
+// Encode the lattice table for tile shape `tile` and upload it.
+static skyrme_status upload_table(skyrme_batch *b, int tile)
+{
+    std::vector<InstDesc> ds(b->ninst);
+    for (int i = 0; i < b->ninst; ++i) {
+        Ctrl *ctrl = static_cast<Ctrl *>(b->states[i].scratch);
+        if (!fill_desc(ds[i], b->lats[i], b->states[i], ctrl, b->dt[i], b->mode, tile))
+            return SKYRME_EINVAL;
+    }
+    const long long units = total_units(ds);
+    const int grid = grid_for(tile, true, units);
+    partition(ds, grid, b->d_parts);
+    if (cudaMemcpy(b->d_table, ds.data(), ds.size() * sizeof(InstDesc), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+        return SKYRME_ECUDA;
+    b->tile = tile;
+    b->grid = grid;
+    b->units = units;
+    return SKYRME_OK;
+}
+
+static skyrme_status batch_launch(skyrme_batch *b, int nsteps, int dry, cudaStream_t s)
+{
+    InstDesc dummy;
+    memset(&dummy, 0, sizeof(dummy));
+    for (int k = 0; k < nsteps; ++k) {
+        if (launch_tile<true>(b->tile, dummy, b->d_table, b->ninst, b->units, b->grid, dry, s) !=
+            cudaSuccess)
+            return SKYRME_ECUDA;
+        if (!dry && b->mode == MODE_ARRESTED) {
+            k_fixup_batch<<<dim3((unsigned)b->fixup_blocks, (unsigned)b->ninst), 256, 0, s>>>(b->d_table);
+            if (cudaGetLastError() != cudaSuccess) return SKYRME_ECUDA;
+        }
+    }
+    return SKYRME_OK;
+}
+
+namespace skyrme {
+bool state_ok_for_batch(const skyrme_lattice *lat, const skyrme_state *st);
+skyrme_status make_graph(skyrme_batch *b, int nsteps, cudaStream_t s, skyrme_graph **out);
+}  // namespace skyrme
+
+extern "C" {
+
+size_t skyrme_batch_scratch_bytes(int ninst, const skyrme_lattice *lats)
+{
+    if (ninst < 1 || !lats) return 0;
+    return table_bytes(ninst) + batch_parts_bytes(ninst);
+}
+
+skyrme_status skyrme_batch_create(int ninst, const skyrme_lattice *lats, skyrme_state *states,
+                                  const double *dt, int mode, void *scratch, size_t scratch_bytes,
+                                  skyrme_batch **out)
+{
+    if (!out) return SKYRME_EINVAL;
+    *out = nullptr;
+    if (ninst < 1 || !lats || !states || !dt || !scratch) return SKYRME_EINVAL;
+    if (mode != MODE_NEWTON && mode != MODE_ARRESTED && mode != MODE_GRADIENT) return SKYRME_EINVAL;
+    if ((uintptr_t)scratch % 256) return SKYRME_EINVAL;
+    if (scratch_bytes < skyrme_batch_scratch_bytes(ninst, lats)) return SKYRME_ENOMEM;
+    for (int i = 0; i < ninst; ++i) {
+        if (lats[i].precision != 32) return SKYRME_EUNSUPPORTED;
+        if (!state_ok_for_batch(&lats[i], &states[i])) return SKYRME_EINVAL;
+        if (!(dt[i] > 0.0)) return SKYRME_EINVAL;
+    }
+    if (!f32_fast_path_available(lats[0])) return SKYRME_EUNSUPPORTED;
+    skyrme_batch *b = new skyrme_batch();
+    b->ninst = ninst;
+    b->mode = mode;
+    b->lats.assign(lats, lats + ninst);
+    b->states.assign(states, states + ninst);
+    b->dt.assign(dt, dt + ninst);
+    b->d_table = static_cast<InstDesc *>(scratch);
+    b->d_parts = reinterpret_cast<double *>(static_cast<char *>(scratch) + table_bytes(ninst));
+    skyrme_status rc = upload_table(b, 0);
+    if (rc != SKYRME_OK) {
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return SKYRME_OK;
+}
+
+skyrme_status skyrme_batch_step(skyrme_batch *b, int nsteps, void *stream)
+{
+    if (!b || nsteps < 0) return SKYRME_EINVAL;
+    return batch_launch(b, nsteps, 0, static_cast<cudaStream_t>(stream));
+}
+
+skyrme_status skyrme_batch_set_tile(skyrme_batch *b, int tile)
+{
+    if (!b || tile < 0 || tile >= kNumTiles) return SKYRME_EINVAL;
+    return upload_table(b, tile);
+}
+
+skyrme_status skyrme_batch_autotune(skyrme_batch *b, int trials, void *stream, int *best_tile,
+                                    double *best_ms)
+{
+    if (!b || trials < 1) return SKYRME_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return SKYRME_ECUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return SKYRME_ECUDA;
+    }
+    int best = -1;
+    float best_t = 0.f;
+    skyrme_status rc = SKYRME_OK;
+    for (int t = 0; t < kNumTiles && rc == SKYRME_OK; ++t) {
+        rc = upload_table(b, t);
+        if (rc != SKYRME_OK) break;
+        rc = batch_launch(b, 1, 1, s);  // warm-up (dry: the flow does not advance)
+        if (rc != SKYRME_OK) break;
+        cudaEventRecord(e0, s);
+        rc = batch_launch(b, trials, 1, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = SKYRME_ECUDA;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= (float)trials;
+        if (rc == SKYRME_OK && (best < 0 || ms < best_t)) {
+            best = t;
+            best_t = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != SKYRME_OK) return rc;
+    rc = upload_table(b, best);
+    if (rc != SKYRME_OK) return rc;
+    if (best_tile) *best_tile = best;
+    if (best_ms) *best_ms = best_t;
+    return SKYRME_OK;
+}
+
+skyrme_status skyrme_batch_tile(const skyrme_batch *b, int *tile, int *ty, int *tz, int *grid)
+{
+    if (!b) return SKYRME_EINVAL;
+    if (tile) *tile = b->tile;
+    if (ty) *ty = kTiles[b->tile].ty;
+    if (tz) *tz = kTiles[b->tile].tz;
+    if (grid) *grid = b->grid;
+    return SKYRME_OK;
+}
+
+skyrme_status skyrme_batch_graph_create(skyrme_batch *b, int nsteps, void *stream, skyrme_graph **out)
+{
+    if (!b || nsteps < 1 || !out) return SKYRME_EINVAL;
+    return make_graph(b, nsteps, static_cast<cudaStream_t>(stream), out);
+}
+
+skyrme_status skyrme_batch_destroy(skyrme_batch *b)
+{
+    delete b;
+    return SKYRME_OK;
+}
+
+}  // extern "C"
+
+namespace skyrme {
+skyrme_status batch_capture(skyrme_batch *b, int nsteps, cudaStream_t s)
+{
+    return batch_launch(b, nsteps, 0, s);
+}
 }  // namespace skyrme

@@ -290,6 +290,8 @@ __global__ void k_reset_ctrl(Ctrl *c)
         c->status = 0;
         c->done = 0;
         c->edone = 0;
+        c->hist = 0;
+        for (int i = 0; i < 16; ++i) c->pht[i] = 1;  // weakly "no arrest"
     }
 }
 
@@ -377,11 +379,14 @@ static int pointwise_blocks(size_t total)
 
 cudaError_t launch_fixup(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s)
 {
+    // mostly an early exit: keep the grid small (grid-stride when active)
     const size_t total = (size_t)(lat.n[0] - 4) * (lat.n[1] - 4) * (lat.n[2] - 4);
+    int blocks = pointwise_blocks(total);
+    if (blocks > 304) blocks = 304;
     if (lat.precision == 64)
-        k_fixup<double><<<pointwise_blocks(total), 256, 0, s>>>(make_params<double>(a, a.step_parts));
+        k_fixup<double><<<blocks, 256, 0, s>>>(make_params<double>(a, a.step_parts));
     else
-        k_fixup<float><<<pointwise_blocks(total), 256, 0, s>>>(make_params<float>(a, a.step_parts));
+        k_fixup<float><<<blocks, 256, 0, s>>>(make_params<float>(a, a.step_parts));
     return cudaGetLastError();
 }
 

@@ -64,7 +64,10 @@ struct Ctrl {
     unsigned int done;    // arrival counter of the step launch
     unsigned int edone;   // arrival counter of the energy launch
     double energy[8];     // E, E2, E4, E0, B, V, max|F|, rms|F| of skyrme_energy
-    double pad[6];
+    int hist;             // last 4 arrest decisions (bit 0 = latest)
+    int pad_i;
+    unsigned char pht[16];  // 2-bit saturating counters indexed by hist
+    double pad[3];
 };
 static_assert(sizeof(Ctrl) <= 512, "control block must fit its 512-byte slot");
 
@@ -200,41 +203,61 @@ __device__ __forceinline__ void block_reduce(double (&v)[NQ], double *red, doubl
     }
 }
 
-// Sum the per-CTA partial records (count of them = nparts) in a fixed order
-// with the threads of one block; the totals land in tot[] of thread 0.
+// Block reduction through shared memory with one warp per quantity: every
+// thread parks its NQ values in buf (NQ * blockDim doubles), then warp q sums
+// quantity q (a max for MAXQ) lane-strided and with a butterfly.  Far fewer
+// FP64 instructions than a shuffle tree in every warp, which matters on a
+// GPU whose FP64 pipe is narrow.  Needs at least NQ warps; fixed order.
+template <int NQ, int MAXQ>
+__device__ __forceinline__ void block_reduce_wide(const double (&v)[NQ], double *buf,
+                                                  double (&out)[NQ])
+{
+    const int nthr = blockDim.x * blockDim.y * blockDim.z;
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int lane = tid & 31, warp = tid >> 5;
+    __syncthreads();  // buf may alias memory the block was still reading
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) buf[q * nthr + tid] = v[q];
+    __syncthreads();
+    double r = 0.0;
+    if (warp < NQ) {
+        const double *col = buf + warp * nthr;
+        r = col[lane];
+        for (int i = lane + 32; i < nthr; i += 32) r = (warp == MAXQ) ? fmax(r, col[i]) : r + col[i];
+        r = (warp == MAXQ) ? warp_max(r) : warp_sum(r);
+    }
+    __syncthreads();
+    if (warp < NQ && lane == 0) buf[warp] = r;
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) out[q] = buf[q];
+    }
+}
+
+// Sum the per-CTA partial records (count nparts) in a fixed order: warp q
+// handles field q of every record (field 5 is a max).  The totals land in
+// tot[] of thread 0; red must hold kPartialDoubles doubles.
 __device__ __forceinline__ void reduce_partials(const double *parts, int nparts, double *red,
                                                 double (&tot)[kPartialDoubles])
 {
-    double v[kPartialDoubles];
-#pragma unroll
-    for (int q = 0; q < kPartialDoubles; ++q) v[q] = 0.0;
     const int nthr = blockDim.x * blockDim.y * blockDim.z;
     const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-    for (int i = tid; i < nparts; i += nthr) {
-        const double *p = parts + (size_t)i * kPartialDoubles;
-#pragma unroll
-        for (int q = 0; q < kPartialDoubles; ++q) {
-            const double x = __ldcg(p + q);
-            v[q] = (q == 5) ? fmax(v[q], x) : v[q] + x;
-        }
-    }
     const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
-#pragma unroll
-    for (int q = 0; q < kPartialDoubles; ++q) v[q] = (q == 5) ? warp_max(v[q]) : warp_sum(v[q]);
     __syncthreads();
-    if (lane == 0) {
-#pragma unroll
-        for (int q = 0; q < kPartialDoubles; ++q) red[q * nw + warp] = v[q];
+    for (int q = warp; q < kPartialDoubles; q += nw) {
+        double r = (q == 5) ? 0.0 : 0.0;
+        for (int i = lane; i < nparts; i += 32) {
+            const double x = __ldcg(parts + (size_t)i * kPartialDoubles + q);
+            r = (q == 5) ? fmax(r, x) : r + x;
+        }
+        r = (q == 5) ? warp_max(r) : warp_sum(r);
+        if (lane == 0) red[q] = r;
     }
     __syncthreads();
     if (tid == 0) {
 #pragma unroll
-        for (int q = 0; q < kPartialDoubles; ++q) {
-            double acc = red[q * nw];
-            for (int w = 1; w < nw; ++w)
-                acc = (q == 5) ? fmax(acc, red[q * nw + w]) : acc + red[q * nw + w];
-            tot[q] = acc;
-        }
+        for (int q = 0; q < kPartialDoubles; ++q) tot[q] = red[q];
     }
 }
 
@@ -252,7 +275,18 @@ __device__ __forceinline__ void finish_step(Ctrl *c, const double (&tot)[kPartia
     if (mode == MODE_ARRESTED) actual = (E > c->E_prev) ? 1 : 0;
     const int fix = (actual == pred) ? 0 : (actual ? -1 : +1);
     c->fix = fix;
-    c->pred = actual;
+    // two-level adaptive prediction of the next decision: the last four
+    // decisions select a 2-bit saturating counter (learns runs and the
+    // alternating arrest pattern of a nearly converged flow)
+    {
+        const int h = c->hist & 15;
+        int ctr = c->pht[h];
+        ctr = actual ? (ctr < 3 ? ctr + 1 : 3) : (ctr > 0 ? ctr - 1 : 0);
+        c->pht[h] = (unsigned char)ctr;
+        const int hn = ((h << 1) | actual) & 15;
+        c->hist = hn;
+        c->pred = c->pht[hn] >= 2 ? 1 : 0;
+    }
     c->arrests += actual;
     c->fixups += (fix != 0);
     c->E_prev = E;

@@ -6,7 +6,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
-#include "../../include/skyrme.h"
+#include "skyrme.h"
 
 namespace skyrme {
 

@@ -139,6 +139,21 @@ def test_fp64_trajectory_matches_oracle(mode):
     assert rep["arrests"] == sum(r["arrested"] for r in oreps)
 
 
+def mispredictions(seq):
+    """Mispredicted arrest decisions of the library's documented predictor:
+    the last four decisions index 16 two-bit saturating counters (initially
+    1); an arrest is predicted when the selected counter is at least 2.
+    Returns (predicted free but arrested, predicted arrested but free)."""
+    hist, pht, pred, up, down = 0, [1] * 16, 0, 0, 0
+    for a in seq:
+        if a != pred:
+            up, down = (up + 1, down) if a else (up, down + 1)
+        pht[hist] = min(pht[hist] + 1, 3) if a else max(pht[hist] - 1, 0)
+        hist = ((hist << 1) | a) & 15
+        pred = 1 if pht[hist] >= 2 else 0
+    return up, down
+
+
 def test_fp64_arrest_switching_trajectory_exercises_both_fixups():
     """The massless hedgehog on a coarse lattice switches between arrested and
     free iterations many times in its first 160 steps.  Every switch is a
@@ -148,9 +163,8 @@ def test_fp64_arrest_switching_trajectory_exercises_both_fixups():
     phi = oracle.seed_rational_map(n, h, 1, 1.0)
     ost, oreps, st, rep = run_both(phi, h, m, dt, 160, 64, chunks=4)
     seq = [r["arrested"] for r in oreps]
-    ups = sum(1 for a, b in zip([0] + seq[:-1], seq) if b and not a)
-    downs = sum(1 for a, b in zip([0] + seq[:-1], seq) if a and not b)
-    assert ups >= 3 and downs >= 3
+    ups, downs = mispredictions(seq)
+    assert ups >= 3 and downs >= 1
     assert rep["arrests"] == sum(seq)
     assert rep["fixups"] == ups + downs
     assert np.max(np.abs(st.field().cpu().numpy() - ost.phi)) < 1e-11
@@ -209,3 +223,57 @@ def test_nonfinite_input_is_reported():
     assert ei.value.status == 4
     with pytest.raises(sk.SkyrmeError):
         sk.energy(lat, st)
+
+
+def test_graph_replay_equals_flow_step():
+    """A captured graph of K iterations replayed twice reproduces 2K calls of
+    skyrme_flow_step bit for bit (the flow state lives on the device)."""
+    n, h, m, K = (28, 30, 32), 0.2, 1.0, 7
+    for prec in (32, 64):
+        lat = sk.Lattice(n, h, m, prec)
+        a = sk.State(lat, DEV)
+        b = sk.State(lat, DEV)
+        for st in (a, b):
+            sk.init_field(lat, sk.Seed.rational_map(4, 1.5), st)
+        ra = sk.flow_step(lat, 0.01, 2 * K, sk.ARRESTED, a)
+        g = sk.FlowGraph(lat, b, 0.01, K, sk.ARRESTED)
+        g.launch()
+        g.launch()
+        g.stream.synchronize()
+        rb = sk.read_report(lat, b)
+        g.close()
+        assert rb["steps"] == 2 * K and rb["E"] == ra["E"]
+        assert torch.equal(a.field(), b.field()) and torch.equal(a.velocity(), b.velocity())
+
+
+def load_golden(name):
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    rows = []
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            v = line.split()
+            rows.append((int(v[0]), [float(t) for t in v[1:7]], int(v[7])))
+    return rows
+
+
+def test_fp64_b1_hedgehog_48_full_run_matches_stored_oracle_trajectory():
+    """The 48^3 FP64 workload for its full 1000 iterations against the FP64
+    oracle's trajectory stored by tests/golden/make_golden.py."""
+    wl = workloads.b1_hedgehog_48()
+    lat = sk.Lattice(wl.n, wl.h, wl.m, 64)
+    st = sk.State(lat, DEV)
+    sk.init_field(lat, sk.Seed.from_spec(wl.seed), st)
+    done = 0
+    for k, vals, arrests in load_golden("b1_hedgehog_48_trajectory.txt"):
+        rep = sk.flow_step(lat, wl.dt, k + 1 - done, sk.ARRESTED, st)
+        done = k + 1
+        E, E2, E4, E0, B, delta = vals
+        assert rep["E"] == pytest.approx(E, rel=1e-12), k
+        assert rep["E2"] == pytest.approx(E2, rel=1e-12) and rep["E4"] == pytest.approx(E4, rel=1e-12)
+        assert rep["B"] == pytest.approx(B, rel=1e-12)
+        assert rep["delta"] == pytest.approx(delta, rel=1e-9)
+        assert rep["arrests"] == arrests, k
+    assert done == wl.steps
