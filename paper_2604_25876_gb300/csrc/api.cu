@@ -15,6 +15,7 @@ int max_constituents();
 int max_smoothing_half_width();
 bool f32_fast_path_available(const skyrme_lattice &lat);
 cudaError_t launch_step_f32_fast(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s);
+cudaError_t launch_fixup_f32_fast(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s);
 int f32_fast_blocks(const skyrme_lattice &lat);
 }  // namespace skyrme
 
@@ -243,7 +244,10 @@ static skyrme_status launch_iterations(const skyrme_lattice &lat, const FlowArgs
     for (int k = 0; k < nsteps; ++k) {
         if (fast) CK(launch_step_f32_fast(lat, a, s), "step kernel (fp32)");
         else CK(launch_step(lat, a, s), "step kernel");
-        if (a.mode == SKYRME_ARRESTED) CK(launch_fixup(lat, a, s), "fix-up kernel");
+        if (a.mode == SKYRME_ARRESTED) {
+            if (fast) CK(launch_fixup_f32_fast(lat, a, s), "fix-up kernel (fp32)");
+            else CK(launch_fixup(lat, a, s), "fix-up kernel");
+        }
     }
     return SKYRME_OK;
 }

@@ -69,7 +69,7 @@ struct InstDesc {
     float c1, c2;          // first-derivative weights / h
     float s1, s2, s0;      // second-derivative weights / h^2
     float m2, dt;
-    double h3;
+    float h3_hi, h3_lo;    // h^3 as an unevaluated float sum
     int mode;
 };
 
@@ -171,19 +171,107 @@ __device__ __forceinline__ P4 fd2(const P4 &m2, const P4 &m1, const P4 &c, const
     return fma(bc(s0), c, fma(bc(s2), add(p2, m2), mul(bc(s1), add(p1, m1))));
 }
 
+// ------------------------------------------------- double-float sums
+// The streaming kernel keeps its energy, charge and force sums as unevaluated
+// sums hi + lo of two floats (|lo| <= ulp(hi)/2), combined with the error-free
+// two-sum and FMA two-product transformations (Knuth, Dekker): about 48
+// significant bits on the FP32 pipe.  GB300's FP64 pipe issues 2 operations
+// per SM and cycle, so FP64 reductions at the end of a launch sit on the
+// critical path; these do not.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ DF quick_two_sum(float a, float b)  // |a| >= |b|
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b)
+{
+    float s, e, t, f;
+    two_sum(a.hi, b.hi, s, e);
+    two_sum(a.lo, b.lo, t, f);
+    DF r = quick_two_sum(s, __fadd_rn(e, t));
+    return quick_two_sum(r.hi, __fadd_rn(r.lo, f));
+}
+__device__ __forceinline__ DF df_add(DF a, float x)
+{
+    float s, e;
+    two_sum(a.hi, x, s, e);
+    return quick_two_sum(s, __fadd_rn(e, a.lo));
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    const float e = __fmaf_rn(a.hi, b.hi, -p);
+    return quick_two_sum(p, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e)));
+}
+__device__ __forceinline__ DF df_neg(DF a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ bool df_gt(DF a, DF b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+__device__ __forceinline__ double df_value(DF a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ DF df_shfl_xor(DF a, int o)
+{
+    return {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+
+// the five sums of a step: e2, e4, (1 - phi^0), det, |F|^2; plus max |F|^2
+constexpr int kSums = 5;
+
 struct Acc {
     float e2, e4, e0, b, f2, fmax2;
 };
 
-__device__ __forceinline__ void flush(double (&acc)[6], Acc &a)
+__device__ __forceinline__ void flush(DF (&acc)[kSums], float &amax, Acc &a)
 {
-    acc[0] += (double)a.e2;
-    acc[1] += (double)a.e4;
-    acc[2] += (double)a.e0;
-    acc[3] += (double)a.b;
-    acc[4] += (double)a.f2;
-    acc[5] = fmax(acc[5], (double)a.fmax2);
+    acc[0] = df_add(acc[0], a.e2);
+    acc[1] = df_add(acc[1], a.e4);
+    acc[2] = df_add(acc[2], a.e0);
+    acc[3] = df_add(acc[3], a.b);
+    acc[4] = df_add(acc[4], a.f2);
+    amax = fmaxf(amax, a.fmax2);
     a = {0, 0, 0, 0, 0, 0};
+}
+
+// Block sum of the per-thread double-float sums (and max of amax) in a fixed
+// shuffle order; thread 0 ends with the totals.  buf: kSums * NW DFs, amx: NW.
+template <int NW>
+__device__ __forceinline__ void block_reduce_df(DF (&v)[kSums], float amax, DF *buf, float *amx,
+                                                DF (&tot)[kSums], float &tmax)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int q = 0; q < kSums; ++q) v[q] = df_add(v[q], df_shfl_xor(v[q], o));
+        amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    }
+    __syncthreads();  // buf may still be read by an earlier reduction
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < kSums; ++q) buf[q * NW + warp] = v[q];
+        amx[warp] = amax;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < kSums; ++q) v[q] = lane < NW ? buf[q * NW + lane] : DF{0.f, 0.f};
+        amax = lane < NW ? amx[lane] : 0.f;
+#pragma unroll
+        for (int o = NW / 2; o > 0; o >>= 1) {
+#pragma unroll
+            for (int q = 0; q < kSums; ++q) v[q] = df_add(v[q], df_shfl_xor(v[q], o));
+            amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        }
+#pragma unroll
+        for (int q = 0; q < kSums; ++q) tot[q] = v[q];
+        tmax = amax;
+    }
 }
 
 // Per-plane values of one column kept in the register x-ring.
@@ -197,10 +285,99 @@ template <int TY, int TZ> struct __align__(128) StepSmem {
     float4 dy[2][TY][TZ + 4];             // d_y phi exchange for d_yz
     float4 inpl[3][4][TY * TZ];           // per-thread in-plane values of the last 3 planes
     unsigned long long bar[NSLOT];
-    double red[8 * 16];
+    DF dfred[kSums * (TY * TZ / 32)];
+    float mxred[TY * TZ / 32];
     int flag;
     int last;
 };
+
+// End of a step for one lattice, run by every thread of the last CTA to
+// leave it.  The CTA records {e2, e4, 1 - phi^0, det, |F|^2} (as hi, lo float
+// pairs) and max |F|^2 are summed in a fixed order; thread 0 then forms the
+// energies of Eq. (2.4), the charge of Eq. (2.6) and the virial, applies the
+// arrest rule of Section 4 (E_n > E_{n-1}: the velocity is zeroed), scores the
+// prediction the launch ran with, and updates the two-level predictor: the
+// last four decisions select a 2-bit saturating counter.
+template <int NW>
+__device__ __forceinline__ void finish_lattice(const InstDesc &D, Ctrl *c, int cur, int mode,
+                                               int pred, int dry, DF *buf, float *amx)
+{
+    const int tid = threadIdx.x;
+    // thread 0 fetches the control fields it needs while the block sums the records
+    float ep_hi = 0.f, ep_lo = 0.f;
+    int hist = 0;
+    uint4 pht4 = make_uint4(0u, 0u, 0u, 0u);
+    long long steps = 0, arrests = 0, fixups = 0;
+    if (tid == 0 && !dry) {
+        ep_hi = __ldcg(&c->eprev_hi);
+        ep_lo = __ldcg(&c->eprev_lo);
+        hist = __ldcg(&c->hist);
+        pht4 = __ldcg(reinterpret_cast<const uint4 *>(c->pht));
+        steps = __ldcg(&c->steps);
+        arrests = __ldcg(&c->arrests);
+        fixups = __ldcg(&c->fixups);
+    }
+    DF v[kSums] = {};
+    float amax = 0.f;
+    for (int i = tid; i < D.cta_count; i += NW * 32) {
+        const float4 *r = reinterpret_cast<const float4 *>(D.parts + (size_t)i * kPartialDoubles);
+        const float4 a = __ldcg(r), b = __ldcg(r + 1), e = __ldcg(r + 2);
+        v[0] = df_add(v[0], DF{a.x, a.y});
+        v[1] = df_add(v[1], DF{a.z, a.w});
+        v[2] = df_add(v[2], DF{b.x, b.y});
+        v[3] = df_add(v[3], DF{b.z, b.w});
+        v[4] = df_add(v[4], DF{e.x, e.y});
+        amax = fmaxf(amax, e.z);
+    }
+    DF t[kSums];
+    float tmax = 0.f;
+    block_reduce_df<NW>(v, amax, buf, amx, t, tmax);
+    if (tid != 0) return;
+    if (dry) {
+        c->done = 0;
+        return;
+    }
+    constexpr double kB = -0.050660591821168885;  // b = -det / (2 pi^2)
+    const DF bfac = {(float)kB, (float)(kB - (double)(float)kB)};
+    const DF h3 = {D.h3_hi, D.h3_lo};
+    const DF E2 = df_mul(h3, t[0]), E4 = df_mul(h3, t[1]);
+    const DF E0 = df_mul(h3, df_mul(DF{2.f * D.m2, 0.f}, t[2]));  // e0 = 2 m^2 (1 - phi^0)
+    const DF E = df_add(df_add(E2, E4), E0);
+    const DF B = df_mul(h3, df_mul(bfac, t[3]));
+    const DF V = df_add(df_add(df_neg(E2), E4), df_mul(DF{-3.f, 0.f}, E0));
+    const int actual = (mode == MODE_ARRESTED && df_gt(E, DF{ep_hi, ep_lo})) ? 1 : 0;
+    const int fix = (actual == pred) ? 0 : (actual ? -1 : +1);
+    unsigned char pht[16];
+    memcpy(pht, &pht4, sizeof(pht));
+    const int h = hist & 15;
+    int ctr = pht[h];
+    ctr = actual ? (ctr < 3 ? ctr + 1 : 3) : (ctr > 0 ? ctr - 1 : 0);
+    pht[h] = (unsigned char)ctr;
+    const int hn = ((h << 1) | actual) & 15;
+    c->pht[h] = (unsigned char)ctr;
+    c->hist = hn;
+    c->pred = pht[hn] >= 2 ? 1 : 0;
+    c->fix = fix;
+    c->arrests = arrests + actual;
+    c->fixups = fixups + (fix != 0);
+    const double Ed = df_value(E);
+    c->E_prev = Ed;
+    c->eprev_hi = E.hi;
+    c->eprev_lo = E.lo;
+    c->steps = steps + 1;
+    c->cur = cur ^ 1;
+    const float nsites = (float)(D.n0 - 4) * (float)(D.n1 - 4) * (float)(D.n2 - 4);
+    c->last[0] = Ed;
+    c->last[1] = df_value(E2);
+    c->last[2] = df_value(E4);
+    c->last[3] = df_value(E0);
+    c->last[4] = df_value(B);
+    c->last[5] = df_value(V);
+    c->last[6] = (double)sqrtf(tmax);
+    c->last[7] = (double)sqrtf(t[4].hi / nsites);
+    if (!(isfinite(E.hi) && isfinite(B.hi) && isfinite(t[4].hi))) c->status = DEV_NONFINITE;
+    c->done = 0;
+}
 
 // The step for every lattice of the launch.  BATCHED: lattices come from
 // `table` (ninst entries, ordered by unit_start); otherwise from `one`.
@@ -258,7 +435,8 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
         const float dt = D.dt, dt2 = 2.0f * D.dt;
         const int nix = D.nix, nzt = D.nzt, n1 = D.n1, n2 = D.n2;
         const size_t plane_stride = (size_t)n1 * n2;
-        double acc_d[6] = {0, 0, 0, 0, 0, 0};
+        DF acc[kSums] = {};
+        float amax = 0.f;
         Acc a32 = {0, 0, 0, 0, 0, 0};
 
         while (us < seg_hi && !failed) {
@@ -305,10 +483,13 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
                     const P4 dzz = fd2(zm2, zm1, c, zp1, zp2, s1, s2, s0);
                     float4(*DY)[TZ + 4] = sm.dy[g & 1];
                     DY[ty][tz + 2] = st4(dy);
-                    if (tz < 4) {  // z-halo columns of d_y phi for this row
-                        const int hc = tz < 2 ? tz : TZ + tz;
-                        DY[ty][hc] = st4(fd1(ld4(P[ty][hc]), ld4(P[ty + 1][hc]), ld4(P[ty + 3][hc]),
-                                             ld4(P[ty + 4][hc]), c1, c2));
+                    if (tid >= THREADS - 32) {  // the last warp fills every z-halo column of d_y phi
+                        for (int j = tid - (THREADS - 32); j < 4 * TY; j += 32) {
+                            const int hr = j >> 2, ci = j & 3;
+                            const int hc = ci < 2 ? ci : TZ + ci;
+                            DY[hr][hc] = st4(fd1(ld4(P[hr][hc]), ld4(P[hr + 1][hc]), ld4(P[hr + 3][hc]),
+                                                 ld4(P[hr + 4][hc]), c1, c2));
+                        }
                     }
                     ring[k].phi = c;
                     ring[k].dy = dy;
@@ -408,44 +589,36 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
                     wrec[3 * THREADS] = make_float4(ayz, 0.f, 0.f, 0.f);
                     ++g;
                 }
-                // FP32 partial sums cover at most 20 planes before entering FP64
-                if ((++nouter & 3) == 0) flush(acc_d, a32);
+                // FP32 partial sums cover at most 40 planes before entering the double-float sums
+                if ((++nouter & 7) == 0) flush(acc, amax, a32);
             }
-            flush(acc_d, a32);
+            flush(acc, amax, a32);
         }
 #undef c1
 #undef c2
 #undef s1
 #undef s2
 #undef s0
+#undef m2
         if (failed) break;
 
         // ---- this CTA is done with lattice D: block reduction, per-lattice finish
-        acc_d[2] *= 2.0 * (double)m2;        // e0 = 2 m^2 (1 - phi^0)
-#undef m2
-        acc_d[3] *= -0.050660591821168885;  // b = -det / (2 pi^2)
-        double tot6[6];
-        // the in-plane ring is free between lattices: it hosts the block reduction
-        block_reduce_wide<6, 5>(acc_d, reinterpret_cast<double *>(&sm.inpl[0][0][0]), tot6);
+        DF tot[kSums];
+        float tmax = 0.f;
+        block_reduce_df<THREADS / 32>(acc, amax, sm.dfred, sm.mxred, tot, tmax);
         if (tid == 0) {
-            double *recp = D.parts + (size_t)(blockIdx.x - D.cta_first) * kPartialDoubles;
-            for (int q = 0; q < 6; ++q) recp[q] = tot6[q];
-            recp[6] = recp[7] = 0.0;
+            float4 *recp = reinterpret_cast<float4 *>(D.parts + (size_t)(blockIdx.x - D.cta_first) *
+                                                                    kPartialDoubles);
+            recp[0] = make_float4(tot[0].hi, tot[0].lo, tot[1].hi, tot[1].lo);
+            recp[1] = make_float4(tot[2].hi, tot[2].lo, tot[3].hi, tot[3].lo);
+            recp[2] = make_float4(tot[4].hi, tot[4].lo, tmax, 0.f);
             __threadfence();
             sm.last = (atomicAdd(&ctrl->done, 1u) == (unsigned)(D.cta_count - 1));
         }
         __syncthreads();
         if (sm.last) {
             __threadfence();
-            double tot[kPartialDoubles];
-            reduce_partials(D.parts, D.cta_count, sm.red, tot);
-            if (tid == 0) {
-                tot[6] = (double)(D.n0 - 4) * (double)(n1 - 4) * (double)(n2 - 4);
-                if (dry)
-                    ctrl->done = 0;
-                else
-                    finish_step(ctrl, tot, D.h3, mode, pred);
-            }
+            finish_lattice<THREADS / 32>(D, ctrl, cur, mode, pred, dry, sm.dfred, sm.mxred);
         }
         __syncthreads();
     }
@@ -464,28 +637,94 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
     }
 }
 
-// Pointwise correction of a mispredicted arrest in any lattice of a batch:
-// blockIdx.y selects the lattice, whose CTAs leave at once when its flag is 0.
-__global__ void k_fixup_batch(const InstDesc *__restrict__ table)
+// Pointwise correction of a mispredicted arrest decision (the finished step
+// stored fix = -1: the velocity should have been zeroed, +1: kept): the site
+// update is redone from the previous buffers, v = v_new + fix v_old,
+// phi = normalise(phi_old + dt v).  Warps of the grid share the z-rows of
+// interior sites; each lane stages two sites' loads before its stores.
+__device__ __forceinline__ void fixup_rows(float4 *const (&phi)[2], float4 *const (&vel)[2],
+                                           int cur, int n0, int n1, int n2, float dt, int fix,
+                                           int wg, int ws)
 {
-    const InstDesc *D = table + blockIdx.y;
-    const int fix = __ldcg(&D->ctrl->fix);
+    const int nb = cur, ob = cur ^ 1;  // cur was already flipped by the finished step
+    const float4 *__restrict__ vnp = vel[nb];
+    const float4 *__restrict__ vop = vel[ob];
+    const float4 *__restrict__ fop = phi[ob];
+    float4 *__restrict__ vst = vel[nb];
+    float4 *__restrict__ fst = phi[nb];
+    const int iy = n1 - 4, iz = n2 - 4, rows = (n0 - 4) * iy;
+    const float sgn = (float)fix;
+    const int lane = threadIdx.x & 31;
+    for (int row = wg; row < rows; row += ws) {
+        const int xr = row / iy;
+        const size_t base = ((size_t)(2 + xr) * n1 + (2 + row - xr * iy)) * n2 + 2;
+        for (int z0 = 0; z0 < iz; z0 += 64) {
+            float4 vn[2], vo[2], fo[2];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int z = z0 + 32 * k + lane;
+                if (z < iz) {
+                    vn[k] = vnp[base + z];
+                    vo[k] = __ldcs(vop + base + z);
+                    fo[k] = __ldcs(fop + base + z);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int z = z0 + 32 * k + lane;
+                if (z < iz) {
+                    const float4 v = make_float4(vn[k].x + sgn * vo[k].x, vn[k].y + sgn * vo[k].y,
+                                                 vn[k].z + sgn * vo[k].z, vn[k].w + sgn * vo[k].w);
+                    const float4 t = make_float4(fo[k].x + dt * v.x, fo[k].y + dt * v.y,
+                                                 fo[k].z + dt * v.z, fo[k].w + dt * v.w);
+                    const float r = rsqrtf(t.x * t.x + t.y * t.y + t.z * t.z + t.w * t.w);
+                    vst[base + z] = v;
+                    fst[base + z] = make_float4(t.x * r, t.y * r, t.z * r, t.w * r);
+                }
+            }
+        }
+    }
+}
+
+struct FixDesc {
+    float4 *phi[2];
+    float4 *vel[2];
+    Ctrl *ctrl;
+    int n0, n1, n2;
+    float dt;
+};
+
+// one lattice; mostly an early exit
+__global__ void __launch_bounds__(512, 2) k_fixup_one(const __grid_constant__ FixDesc d)
+{
+    const int fix = __ldcg(&d.ctrl->fix);
     if (fix == 0) return;
-    const int nb = __ldcg(&D->ctrl->cur), ob = nb ^ 1;
-    const int ix = D->n0 - 4, iy = D->n1 - 4, iz = D->n2 - 4;
-    const size_t total = (size_t)ix * iy * iz;
-    const float sgn = (float)fix, dt = D->dt;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const int z = 2 + (int)(i % iz), y = 2 + (int)((i / iz) % iy), x = 2 + (int)(i / ((size_t)iz * iy));
-        const size_t s = ((size_t)x * D->n1 + y) * D->n2 + z;
-        const float4 vn = D->vel[nb][s], vo = D->vel[ob][s], fo = D->phi[ob][s];
-        const float4 v = make_float4(vn.x + sgn * vo.x, vn.y + sgn * vo.y, vn.z + sgn * vo.z,
-                                     vn.w + sgn * vo.w);
-        const float4 t = make_float4(fo.x + dt * v.x, fo.y + dt * v.y, fo.z + dt * v.z, fo.w + dt * v.w);
-        const float r = rsqrtf(t.x * t.x + t.y * t.y + t.z * t.z + t.w * t.w);
-        D->vel[nb][s] = v;
-        D->phi[nb][s] = make_float4(t.x * r, t.y * r, t.z * r, t.w * r);
+    const int warps = blockDim.x >> 5;
+    fixup_rows(d.phi, d.vel, __ldcg(&d.ctrl->cur), d.n0, d.n1, d.n2, d.dt, fix,
+               blockIdx.x * warps + (threadIdx.x >> 5), gridDim.x * warps);
+}
+
+// every lattice of a batch: each warp reads 32 lattices' flags at once and
+// the whole grid then corrects, one after another, the lattices that need it
+__global__ void __launch_bounds__(512, 2) k_fixup_batch(const InstDesc *__restrict__ table, int ninst)
+{
+    const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+    const int wg = blockIdx.x * warps + (threadIdx.x >> 5), ws = gridDim.x * warps;
+    for (int i0 = 0; i0 < ninst; i0 += 32) {
+        int fix = 0, cur = 0;
+        if (i0 + lane < ninst) {
+            const Ctrl *c = table[i0 + lane].ctrl;
+            fix = __ldcg(&c->fix);
+            cur = __ldcg(&c->cur);
+        }
+        unsigned need = __ballot_sync(0xffffffffu, fix != 0);
+        while (need) {
+            const int j = __ffs(need) - 1;
+            need &= need - 1;
+            const int f = __shfl_sync(0xffffffffu, fix, j), cj = __shfl_sync(0xffffffffu, cur, j);
+            const InstDesc &D = table[i0 + j];
+            fixup_rows(D.phi, D.vel, cj, D.n0, D.n1, D.n2, D.dt, f, wg, ws);
+        }
     }
 }
 
@@ -642,7 +881,9 @@ static bool fill_desc(InstDesc &d, const skyrme_lattice &lat, const skyrme_state
     d.s0 = (float)(-2.5 * ih2);
     d.m2 = (float)(lat.m * lat.m);
     d.dt = (float)dt;
-    d.h3 = lat.h * lat.h * lat.h;
+    const double h3 = lat.h * lat.h * lat.h;
+    d.h3_hi = (float)h3;
+    d.h3_lo = (float)(h3 - (double)d.h3_hi);
     d.mode = mode;
     return true;
 }
@@ -701,6 +942,24 @@ int f32_fast_blocks(const skyrme_lattice &lat)
     return kMaxGrid;
 }
 
+cudaError_t launch_fixup_f32_fast(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s)
+{
+    FixDesc d;
+    for (int i = 0; i < 2; ++i) {
+        d.phi[i] = static_cast<float4 *>(a.phi[i]);
+        d.vel[i] = static_cast<float4 *>(a.vel[i]);
+    }
+    d.ctrl = static_cast<Ctrl *>(a.ctrl);
+    d.n0 = lat.n[0];
+    d.n1 = lat.n[1];
+    d.n2 = lat.n[2];
+    d.dt = (float)a.dt;
+    const long long rows = (long long)(lat.n[0] - 4) * (lat.n[1] - 4);
+    const int blocks = (int)std::max(1LL, std::min((long long)sm_count() * 2, (rows + 15) / 16));
+    k_fixup_one<<<blocks, 512, 0, s>>>(d);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_step_f32_fast(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s)
 {
     const int tile = 0;
@@ -733,7 +992,7 @@ struct skyrme_batch {
     std::vector<double> dt;
     InstDesc *d_table = nullptr;  // in the caller's batch scratch
     double *d_parts = nullptr;
-    size_t fixup_blocks = 32;
+    int fixup_blocks = 1;
 };
 
 static size_t table_bytes(int ninst) { return ((size_t)ninst * sizeof(InstDesc) + 255) & ~(size_t)255; }
@@ -772,7 +1031,7 @@ static skyrme_status batch_launch(skyrme_batch *b, int nsteps, int dry, cudaStre
             cudaSuccess)
             return SKYRME_ECUDA;
         if (!dry && b->mode == MODE_ARRESTED) {
-            k_fixup_batch<<<dim3((unsigned)b->fixup_blocks, (unsigned)b->ninst), 256, 0, s>>>(b->d_table);
+            k_fixup_batch<<<(unsigned)b->fixup_blocks, 512, 0, s>>>(b->d_table, b->ninst);
             if (cudaGetLastError() != cudaSuccess) return SKYRME_ECUDA;
         }
     }
@@ -811,6 +1070,7 @@ skyrme_status skyrme_batch_create(int ninst, const skyrme_lattice *lats, skyrme_
     skyrme_batch *b = new skyrme_batch();
     b->ninst = ninst;
     b->mode = mode;
+    b->fixup_blocks = sm_count() * 2;
     b->lats.assign(lats, lats + ninst);
     b->states.assign(states, states + ninst);
     b->dt.assign(dt, dt + ninst);

@@ -17,6 +17,8 @@
 // phi_{n+1} = normalise(phi_n + dt v_{n+1}) from the untouched old buffers.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "skyrme_device.cuh"
 #include "skyrme_internal.h"
 
@@ -183,7 +185,11 @@ __global__ void __launch_bounds__(GTHREADS) k_tile(FlowParams<T> p, vec4_t<T> *f
     vec4_t<T> *tile = reinterpret_cast<vec4_t<T> *>(smem_raw);
     const int cur = __ldcg(&p.ctrl->cur);
     const int pred = (KIND == 0 && p.mode == MODE_ARRESTED) ? __ldcg(&p.ctrl->pred) : 0;
-    const vec4_t<T> *phi = p.phi[cur];
+    // buffers selected by value (a run-time index into the parameter copies it to the stack)
+    const vec4_t<T> *phi = cur ? p.phi[1] : p.phi[0];
+    const vec4_t<T> *vin = cur ? p.vel[1] : p.vel[0];
+    vec4_t<T> *phi_out = cur ? p.phi[0] : p.phi[1];
+    vec4_t<T> *vel_out = cur ? p.vel[0] : p.vel[1];
     const int x0 = 2 + blockIdx.z * GTX, y0 = 2 + blockIdx.y * GTY, z0 = 2 + blockIdx.x * GTZ;
     load_tile<T>(tile, phi, x0, y0, z0, p.n0, p.n1, p.n2);
     __syncthreads();
@@ -205,7 +211,7 @@ __global__ void __launch_bounds__(GTHREADS) k_tile(FlowParams<T> p, vec4_t<T> *f
             } else {
                 T v[4] = {T(0), T(0), T(0), T(0)};
                 if (!pred) {
-                    const vec4_t<T> vv = load4<T>(p.vel[cur] + s);
+                    const vec4_t<T> vv = load4<T>(vin + s);
                     v[0] = vv.x; v[1] = vv.y; v[2] = vv.z; v[3] = vv.w;
                 }
 #pragma unroll
@@ -213,9 +219,9 @@ __global__ void __launch_bounds__(GTHREADS) k_tile(FlowParams<T> p, vec4_t<T> *f
                     v[A] = v[A] + p.dt * F[A];
                     t[A] = ph[A] + p.dt * v[A];
                 }
-                store4<T>(p.vel[cur ^ 1] + s, make4<T>(v[0], v[1], v[2], v[3]));
+                store4<T>(vel_out + s, make4<T>(v[0], v[1], v[2], v[3]));
             }
-            normalise_store<T>(p.phi[cur ^ 1] + s, t);
+            normalise_store<T>(phi_out + s, t);
         } else if (KIND == 2) {
             if (fout) store4<T>(fout + s, make4<T>(F[0], F[1], F[2], F[3]));
             if (dout) store4<T>(dout + s, make4<T>(dens[0], dens[1], dens[2], dens[3]));
@@ -231,29 +237,55 @@ __global__ void __launch_bounds__(GTHREADS) k_tile(FlowParams<T> p, vec4_t<T> *f
     reduce_and_finish<T>(p, acc, KIND == 1, pred);
 }
 
-// Pointwise correction of a mispredicted arrest decision.
-template <typename T> __global__ void k_fixup(FlowParams<T> p)
+// Pointwise correction of a mispredicted arrest decision: the step ran with
+// the predicted rule, the finished step stored fix = -1 (velocity should have
+// been zeroed) or +1 (it should have been kept), and the site update is redone
+// from the previous buffers: v = v_new + fix v_old, phi = normalise(phi_old + dt v).
+// One warp per z-row of interior sites; each lane stages the loads of
+// kFixUnroll sites before its stores so that many loads are in flight.
+template <typename T> __global__ void __launch_bounds__(512, 2) k_fixup(FlowParams<T> p)
 {
+    constexpr int kFixUnroll = sizeof(T) == 4 ? 2 : 1;
     const int fix = __ldcg(&p.ctrl->fix);
     if (fix == 0) return;
     const int nb = __ldcg(&p.ctrl->cur);  // new buffers (already flipped)
     const int ob = nb ^ 1;
-    const int ix = p.n0 - 4, iy = p.n1 - 4, iz = p.n2 - 4;
-    const size_t total = (size_t)ix * iy * iz;
+    const int iy = p.n1 - 4, iz = p.n2 - 4, rows = (p.n0 - 4) * iy;
     const T sgn = T(fix);
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const int z = 2 + (int)(i % iz);
-        const int y = 2 + (int)((i / iz) % iy);
-        const int x = 2 + (int)(i / ((size_t)iz * iy));
-        const size_t s = site_index(x, y, z, p.n1, p.n2);
-        const vec4_t<T> vn = load4<T>(p.vel[nb] + s);
-        const vec4_t<T> vo = load4<T>(p.vel[ob] + s);
-        const vec4_t<T> fo = load4<T>(p.phi[ob] + s);
-        T v[4] = {vn.x + sgn * vo.x, vn.y + sgn * vo.y, vn.z + sgn * vo.z, vn.w + sgn * vo.w};
-        T t[4] = {fo.x + p.dt * v[0], fo.y + p.dt * v[1], fo.z + p.dt * v[2], fo.w + p.dt * v[3]};
-        store4<T>(p.vel[nb] + s, make4<T>(v[0], v[1], v[2], v[3]));
-        normalise_store<T>(p.phi[nb] + s, t);
+    const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+    // buffer selection by value: a run-time index into the parameter would copy it to the stack
+    vec4_t<T> *vnew = ob ? p.vel[0] : p.vel[1];
+    vec4_t<T> *pnew = ob ? p.phi[0] : p.phi[1];
+    const vec4_t<T> *vold = ob ? p.vel[1] : p.vel[0];
+    const vec4_t<T> *pold = ob ? p.phi[1] : p.phi[0];
+    for (int row = blockIdx.x * warps + (threadIdx.x >> 5); row < rows; row += gridDim.x * warps) {
+        const int xr = row / iy;
+        const size_t base = site_index(2 + xr, 2 + (row - xr * iy), 2, p.n1, p.n2);
+        for (int z0 = 0; z0 < iz; z0 += 32 * kFixUnroll) {
+            vec4_t<T> vn[kFixUnroll], vo[kFixUnroll], fo[kFixUnroll];
+#pragma unroll
+            for (int k = 0; k < kFixUnroll; ++k) {
+                const int z = z0 + 32 * k + lane;
+                if (z < iz) {
+                    vn[k] = load4<T>(vnew + base + z);
+                    vo[k] = load4<T>(vold + base + z);
+                    fo[k] = load4<T>(pold + base + z);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < kFixUnroll; ++k) {
+                const int z = z0 + 32 * k + lane;
+                if (z < iz) {
+                    const T v0 = vn[k].x + sgn * vo[k].x, v1 = vn[k].y + sgn * vo[k].y;
+                    const T v2 = vn[k].z + sgn * vo[k].z, v3 = vn[k].w + sgn * vo[k].w;
+                    const T t0 = fo[k].x + p.dt * v0, t1 = fo[k].y + p.dt * v1;
+                    const T t2 = fo[k].z + p.dt * v2, t3 = fo[k].w + p.dt * v3;
+                    store4<T>(vnew + base + z, make4<T>(v0, v1, v2, v3));
+                    const T r = T(1) / sqrt(t0 * t0 + t1 * t1 + t2 * t2 + t3 * t3);
+                    store4<T>(pnew + base + z, make4<T>(t0 * r, t1 * r, t2 * r, t3 * r));
+                }
+            }
+        }
     }
 }
 
@@ -280,6 +312,8 @@ __global__ void k_reset_ctrl(Ctrl *c)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         c->E_prev = __longlong_as_double(0x7ff0000000000000LL);  // +inf
+        c->eprev_hi = __int_as_float(0x7f800000);
+        c->eprev_lo = 0.f;
         for (int i = 0; i < 8; ++i) c->last[i] = 0.0, c->energy[i] = 0.0;
         c->steps = 0;
         c->arrests = 0;
@@ -379,14 +413,13 @@ static int pointwise_blocks(size_t total)
 
 cudaError_t launch_fixup(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s)
 {
-    // mostly an early exit: keep the grid small (grid-stride when active)
-    const size_t total = (size_t)(lat.n[0] - 4) * (lat.n[1] - 4) * (lat.n[2] - 4);
-    int blocks = pointwise_blocks(total);
-    if (blocks > 304) blocks = 304;
+    // mostly an early exit: one wave of 512-thread blocks, 16 rows each at most per pass
+    const long long rows = (long long)(lat.n[0] - 4) * (lat.n[1] - 4);
+    const int blocks = (int)std::max(1LL, std::min(304LL, (rows + 15) / 16));
     if (lat.precision == 64)
-        k_fixup<double><<<blocks, 256, 0, s>>>(make_params<double>(a, a.step_parts));
+        k_fixup<double><<<blocks, 512, 0, s>>>(make_params<double>(a, a.step_parts));
     else
-        k_fixup<float><<<blocks, 256, 0, s>>>(make_params<float>(a, a.step_parts));
+        k_fixup<float><<<blocks, 512, 0, s>>>(make_params<float>(a, a.step_parts));
     return cudaGetLastError();
 }
 
