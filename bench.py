@@ -40,7 +40,6 @@ BYTES_PER_SITE_F32 = 64   # read phi, v; write phi', v' (16 B each)
 BYTES_PER_SITE_F64 = 128
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0     # GB/s, used only when the measured peaks file is absent
-FP64_NOMINAL_TFLOPS = 1.25
 FLOPS_PER_SITE = 590      # algorithmic FP operations per site-update (FMA = 2)
 GRAPH_CHUNK = 250         # iterations per captured CUDA graph
 
@@ -52,6 +51,14 @@ def peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM, "fallback"
+
+
+def alu_peaks(sk):
+    """Measured FMA throughput of this GPU (TFLOP/s): packed FP32 pairs, FP64."""
+    return {"fp32_tflops": round(sk.measure_fma_peak(sk.PEAK_FP32), 2),
+            "fp64_tflops": round(sk.measure_fma_peak(sk.PEAK_FP64), 4),
+            "method": "skyrme_measure_fma_peak: 8 independent FMA chains per thread, "
+                      "8 CTAs of 256 threads per SM, best of 3 timed launches"}
 
 
 def dist_env():
@@ -253,25 +260,33 @@ def run_ours(args, ws, rank, local):
     # roofline of the dominant kernel: algorithmic bytes per launch over the
     # mean duration of one iteration (step launch + fix-up check)
     hbm, peak_kind = peaks()
+    alu = alu_peaks(sk)
     mean_iter = statistics.fmean(iter_ms)
-    if prec == 32:
-        achieved = BYTES_PER_SITE_F32 * sites / (mean_iter * 1e-3) / 1e9
-        traffic = recorded_traffic(f"step_f32_{wl.name}", sites)
+    # the roofline is the slower of the HBM and ALU bounds (site-updates/s)
+    bytes_site = BYTES_PER_SITE_F32 * (1 if prec == 32 else 2)
+    alu_tflops = alu["fp32_tflops"] if prec == 32 else alu["fp64_tflops"]
+    hbm_bound = hbm * 1e9 / bytes_site / 1e9
+    alu_bound = alu_tflops * 1e12 / FLOPS_PER_SITE / 1e9
+    bounds = {"hbm_bound_gsites": round(hbm_bound, 2), "alu_bound_gsites": round(alu_bound, 3),
+              "alu_peaks": alu, "algorithmic_flops_per_site": FLOPS_PER_SITE,
+              "algorithmic_bytes_per_site": bytes_site}
+    if hbm_bound <= alu_bound:
+        achieved = bytes_site * sites / (mean_iter * 1e-3) / 1e9
         roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                    "frac": round(achieved / hbm, 4), "traffic": traffic,
+                    "frac": round(achieved / hbm, 4),
+                    "traffic": recorded_traffic(f"step_f{prec}_{wl.name}", sites),
                     "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
                     if peak_kind == "measured" else "fallback 6.8 TB/s",
-                    "algorithmic_bytes_per_site": BYTES_PER_SITE_F32,
                     "duration": "mean per iteration (step kernel + fix-up check) from CUDA "
-                                "events around each graph replay"}
+                                "events around each graph replay", **bounds}
     else:
         tfl = FLOPS_PER_SITE * sites / (mean_iter * 1e-3) / 1e12
-        roofline = {"bound": "alu", "achieved": round(tfl, 4), "peak": FP64_NOMINAL_TFLOPS,
-                    "unit": "TFLOP/s", "frac": round(tfl / FP64_NOMINAL_TFLOPS, 4),
-                    "traffic": recorded_traffic(f"step_f64_{wl.name}", sites),
-                    "peak_source": "nominal GB300 FP64 rate (profiling recipe table)",
-                    "algorithmic_flops_per_site": FLOPS_PER_SITE,
-                    "duration": "mean per iteration from CUDA events around each graph replay"}
+        roofline = {"bound": "alu", "achieved": round(tfl, 4), "peak": alu_tflops,
+                    "unit": "TFLOP/s", "frac": round(tfl / alu_tflops, 4),
+                    "traffic": recorded_traffic(f"step_f{prec}_{wl.name}", sites),
+                    "peak_source": "measured FP%d FMA throughput (skyrme_measure_fma_peak)" % prec,
+                    "duration": "mean per iteration (step kernel + fix-up check) from CUDA "
+                                "events around each graph replay", **bounds}
 
     out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": K,
            "warmup": W, "ms_per_step": round(total_ms / K, 5), "higher_is_better": True,
@@ -288,7 +303,7 @@ def run_ours(args, ws, rank, local):
     if rank == 0 and not args.no_extras:
         out["e2e"] = run_e2e(sk, torch, dev, wl, K)
         if prec == 32:
-            out["fp64_gpu"] = run_fp64_compare(sk, torch, dev, wl, K + W, rep)
+            out["fp64_gpu"] = run_fp64_compare(sk, torch, dev, wl, K + W, rep, alu["fp64_tflops"])
         out["cpu_baseline"] = run_cpu_baseline(wl, args.cpu_seconds)
     return out
 
@@ -377,7 +392,7 @@ def run_e2e(sk, torch, dev, wl, K):
             "what": f"one job of {K} iterations: seed upload, flow, report and field download"}
 
 
-def run_fp64_compare(sk, torch, dev, wl, nsteps, rep32):
+def run_fp64_compare(sk, torch, dev, wl, nsteps, rep32, fp64_tflops):
     """FP64 GPU flow of the same workload for the same iterations (validated
     against the FP64 oracle by the parity tests): its throughput, its ALU
     roofline and the FP32 energy error relative to it."""
@@ -397,9 +412,9 @@ def run_fp64_compare(sk, torch, dev, wl, nsteps, rep32):
     tfl = gs * FLOPS_PER_SITE / 1e3
     return {"value": round(gs, 4), "unit": UNIT, "steps": nsteps,
             "roofline": {"bound": "alu", "achieved": round(tfl, 4),
-                         "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                         "frac": round(tfl / FP64_NOMINAL_TFLOPS, 4),
-                         "peak_source": "nominal GB300 FP64 rate",
+                         "peak": fp64_tflops, "unit": "TFLOP/s",
+                         "frac": round(tfl / fp64_tflops, 4),
+                         "peak_source": "measured FP64 FMA throughput (skyrme_measure_fma_peak)",
                          "algorithmic_flops_per_site": FLOPS_PER_SITE},
             "E_fp64": rep["E"],
             "fp32_energy_rel_err": abs(rep32["E"] - rep["E"]) / abs(rep["E"])

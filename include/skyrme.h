@@ -225,6 +225,17 @@ skyrme_status skyrme_forces(const skyrme_lattice *lat, skyrme_state *st, void *f
 skyrme_status skyrme_energy_static(const skyrme_lattice *lat, const void *phi, double out6[6],
                                    void *stream);
 
+/* ---- measurement diagnostic ----
+ * skyrme_measure_fma_peak: the device's fused multiply-add throughput in
+ * TFLOP/s (an FMA counts as 2 operations), measured by timing long chains of
+ * independent FMAs on every SM: kind SKYRME_PEAK_FP32 uses the packed FP32
+ * pair instruction the FP32 step kernel uses, SKYRME_PEAK_FP64 the FP64 FMA.
+ * These are the ALU roofline denominators of the step kernels; the paper has
+ * no counterpart.  Launches a few kernels on `stream` (about 1 ms) and
+ * synchronises it.  SKYRME_EINVAL for another kind or a null pointer. */
+typedef enum { SKYRME_PEAK_FP32 = 0, SKYRME_PEAK_FP64 = 1 } skyrme_peak_kind;
+skyrme_status skyrme_measure_fma_peak(int kind, double *tflops, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -84,6 +84,7 @@ _SIGNATURES = {
                                      _P]),
     "skyrme_energy_static": (ctypes.c_int, [ctypes.POINTER(c_lattice), _P,
                                             ctypes.POINTER(ctypes.c_double), _P]),
+    "skyrme_measure_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P]),
     "skyrme_batch_scratch_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.POINTER(c_lattice)]),
     "skyrme_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(c_lattice),
                                            ctypes.POINTER(c_state), ctypes.POINTER(ctypes.c_double),
@@ -336,6 +337,18 @@ def forces(lat: Lattice, st: State, want_dens: bool = True, stream=None):
                                 ctypes.c_void_p(D.data_ptr()) if D is not None else None,
                                 _stream_ptr(stream, st.device)), "skyrme_forces")
     return F, D
+
+
+PEAK_FP32, PEAK_FP64 = 0, 1
+
+
+def measure_fma_peak(kind: int, stream=None) -> float:
+    """Measured FMA throughput (TFLOP/s) of the current device: packed FP32
+    pairs (PEAK_FP32) or FP64 (PEAK_FP64).  Synchronises the stream."""
+    out = ctypes.c_double(0.0)
+    _check(load().skyrme_measure_fma_peak(int(kind), ctypes.byref(out), _stream_ptr(stream)),
+           "skyrme_measure_fma_peak")
+    return out.value
 
 
 class FlowGraph:

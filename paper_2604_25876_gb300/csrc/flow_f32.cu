@@ -4,9 +4,9 @@
 // Same iteration as the tile kernel (Section 3: 4th-order first, second and
 // mixed derivatives, Euler-Lagrange gradient, tangent projection of
 // Eq. "Newton_flow", v += dt F, phi = normalise(phi + dt v); Section 2.1
-// densities summed in FP64), organised for GB300:
+// densities), organised for GB300:
 //
-//  * persistent CTAs (as many as fit, normally two or four per SM) split the
+//  * persistent CTAs (as many as fit, normally two per SM) split the
 //    (column, x-plane) work of every lattice in the batch evenly.  A column
 //    is a TY x TZ block of interior (y, z) sites; a CTA marches along x
 //    through contiguous runs of planes, crossing from one lattice into the
@@ -16,21 +16,25 @@
 //  * each x-plane of the column tile, with its 2-site halo, is streamed into
 //    a 4-slot shared-memory ring by TMA (cp.async.bulk.tensor.3d) with an
 //    mbarrier per slot; every wait is bounded and reports SKYRME_ETIMEOUT
-//    instead of hanging.
+//    instead of hanging.  Warps consume the planes independently: the last
+//    warp to be done with a slot (a shared-memory counter) streams the next
+//    plane into it, so the only CTA-wide barriers are at the ends of runs.
 //  * in-plane derivatives (d_y, d_z, d_yy, d_zz) come from the staged plane;
-//    d_yz = d_z(d_y phi) uses a shared-memory exchange of d_y phi (with the
-//    4 z-halo columns computed by 4 lanes per row); d_x, d_xx, d_xy = d_x(d_y
-//    phi), d_xz = d_x(d_z phi) come from a 5-plane register ring of (phi, d_y
-//    phi, d_z phi) that the x-loop cycles through (unrolled by 5 so no
-//    register is ever moved).  The in-plane contractions a plane contributes
-//    to its own centre two planes later wait in a per-thread shared-memory
-//    ring, and the velocity of each centre plane arrives by TMA together with
-//    the field plane two planes ahead: 128 registers per thread.
+//    d_yz = d_z(d_y phi) uses a per-warp shared-memory exchange of d_y phi
+//    (each warp computes the 4 z-halo columns of its own rows); d_x, d_xx,
+//    d_xy = d_x(d_y phi), d_xz = d_x(d_z phi) come from a 5-plane register
+//    ring of (phi, d_y phi, d_z phi) that the x-loop cycles through (unrolled
+//    by 5 so no register is ever moved).  The in-plane contractions a plane
+//    contributes to its own centre two planes later wait in a per-thread
+//    shared-memory ring, and the velocity of each centre plane arrives by TMA
+//    together with the field plane two planes ahead.
 //  * 4-vector arithmetic uses the packed FP32 pair instructions of sm_100+
-//    (__ffma2_rn / __fadd2_rn / __fmul2_rn): two components per instruction.
-//  * per-site densities are summed in FP32 over at most 20 consecutive planes
-//    and then accumulated in FP64; block and per-lattice reductions are FP64
-//    in a fixed order.
+//    (__ffma2_rn / __fadd2_rn / __fmul2_rn): two components per instruction;
+//    stencil weights are stored as (w, w) pairs.
+//  * per-site densities are summed in FP32 over at most 40 consecutive
+//    planes, then in double-float (hi, lo) pairs kept in shared memory; block
+//    and per-lattice reductions are double-float in a fixed order, and the
+//    arrest comparison is made in FP64 on the rounded totals.
 //  * the tile shape (TY, TZ) is a template parameter; the batch autotuner
 //    times the candidates on the actual lattices and keeps the fastest.
 #include <cuda.h>
@@ -66,9 +70,12 @@ struct InstDesc {
     int n0, n1, n2;
     int nzt, nix;          // column tiles along z, interior planes along x
     int cta_first, cta_count;
-    float c1, c2;          // first-derivative weights / h
-    float s1, s2, s0;      // second-derivative weights / h^2
-    float m2, dt;
+    // stencil weights and time steps as (w, w) pairs: the packed FP32
+    // instructions take them as one 64-bit operand
+    float2 c1, c2;         // first-derivative weights / h
+    float2 s1, s2, s0;     // second-derivative weights / h^2
+    float2 dt, dt2;        // dt and 2 dt
+    float m2;
     float h3_hi, h3_lo;    // h^3 as an unevaluated float sum
     int mode;
 };
@@ -159,16 +166,16 @@ __device__ __forceinline__ float dot(const P4 &u, const P4 &v)
     return hsum(__ffma2_rn(u.b, v.b, __fmul2_rn(u.a, v.a)));
 }
 // first derivative c1 (p1 - m1) + c2 (p2 - m2)
-__device__ __forceinline__ P4 fd1(const P4 &m2, const P4 &m1, const P4 &p1, const P4 &p2, float c1,
-                                  float c2)
+__device__ __forceinline__ P4 fd1(const P4 &m2, const P4 &m1, const P4 &p1, const P4 &p2, float2 c1,
+                                  float2 c2)
 {
-    return fma(bc(c2), sub(p2, m2), mul(bc(c1), sub(p1, m1)));
+    return fma(c2, sub(p2, m2), mul(c1, sub(p1, m1)));
 }
 // second derivative s1 (p1 + m1) + s2 (p2 + m2) + s0 c
 __device__ __forceinline__ P4 fd2(const P4 &m2, const P4 &m1, const P4 &c, const P4 &p1,
-                                  const P4 &p2, float s1, float s2, float s0)
+                                  const P4 &p2, float2 s1, float2 s2, float2 s0)
 {
-    return fma(bc(s0), c, fma(bc(s2), add(p2, m2), mul(bc(s1), add(p1, m1))));
+    return fma(s0, c, fma(s2, add(p2, m2), mul(s1, add(p1, m1))));
 }
 
 // ------------------------------------------------- double-float sums
@@ -213,7 +220,6 @@ __device__ __forceinline__ DF df_mul(DF a, DF b)
     return quick_two_sum(p, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e)));
 }
 __device__ __forceinline__ DF df_neg(DF a) { return {-a.hi, -a.lo}; }
-__device__ __forceinline__ bool df_gt(DF a, DF b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
 __device__ __forceinline__ double df_value(DF a) { return (double)a.hi + (double)a.lo; }
 __device__ __forceinline__ DF df_shfl_xor(DF a, int o)
 {
@@ -227,37 +233,53 @@ struct Acc {
     float e2, e4, e0, b, f2, fmax2;
 };
 
-__device__ __forceinline__ void flush(DF (&acc)[kSums], float &amax, Acc &a)
+// Fold a thread's FP32 partial sums into its double-float sums, which live
+// in shared memory (acc: kSums arrays of stride nthreads, at this thread's slot).
+__device__ __forceinline__ void flush(DF *acc, float *amax, int nthreads, Acc &a)
 {
     acc[0] = df_add(acc[0], a.e2);
-    acc[1] = df_add(acc[1], a.e4);
-    acc[2] = df_add(acc[2], a.e0);
-    acc[3] = df_add(acc[3], a.b);
-    acc[4] = df_add(acc[4], a.f2);
-    amax = fmaxf(amax, a.fmax2);
+    acc[nthreads] = df_add(acc[nthreads], a.e4);
+    acc[2 * nthreads] = df_add(acc[2 * nthreads], a.e0);
+    acc[3 * nthreads] = df_add(acc[3 * nthreads], a.b);
+    acc[4 * nthreads] = df_add(acc[4 * nthreads], a.f2);
+    *amax = fmaxf(*amax, a.fmax2);
     a = {0, 0, 0, 0, 0, 0};
+}
+
+__device__ __forceinline__ void zero_sums(DF *acc, float *amax, int nthreads)
+{
+#pragma unroll
+    for (int q = 0; q < kSums; ++q) acc[q * nthreads] = DF{0.f, 0.f};
+    *amax = 0.f;
+}
+__device__ __forceinline__ void load_sums(const DF *acc, const float *amax, int nthreads,
+                                          DF (&v)[kSums], float &m)
+{
+#pragma unroll
+    for (int q = 0; q < kSums; ++q) v[q] = acc[q * nthreads];
+    m = *amax;
 }
 
 // Block sum of the per-thread double-float sums (and max of amax) in a fixed
 // shuffle order; thread 0 ends with the totals.  buf: kSums * NW DFs, amx: NW.
-template <int NW>
+template <int NW, typename Sync>
 __device__ __forceinline__ void block_reduce_df(DF (&v)[kSums], float amax, DF *buf, float *amx,
-                                                DF (&tot)[kSums], float &tmax)
+                                                DF (&tot)[kSums], float &tmax, int tid, Sync sync)
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
         for (int q = 0; q < kSums; ++q) v[q] = df_add(v[q], df_shfl_xor(v[q], o));
         amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
     }
-    __syncthreads();  // buf may still be read by an earlier reduction
+    sync();  // buf may still be read by an earlier reduction
     if (lane == 0) {
 #pragma unroll
         for (int q = 0; q < kSums; ++q) buf[q * NW + warp] = v[q];
         amx[warp] = amax;
     }
-    __syncthreads();
+    sync();
     if (warp == 0) {
 #pragma unroll
         for (int q = 0; q < kSums; ++q) v[q] = lane < NW ? buf[q * NW + lane] : DF{0.f, 0.f};
@@ -283,7 +305,11 @@ template <int TY, int TZ> struct __align__(128) StepSmem {
     float4 plane[NSLOT][TY + 4][TZ + 4];  // haloed field planes (TMA)
     float4 vpl[NSLOT][TY][TZ];            // velocity planes of the centre sites (TMA)
     float4 dy[2][TY][TZ + 4];             // d_y phi exchange for d_yz
-    float4 inpl[3][4][TY * TZ];           // per-thread in-plane values of the last 3 planes
+    int rel[NSLOT];                       // warps done with the plane in each slot
+    float4 inpl[3][3][TY * TZ];           // per-thread in-plane values of the last 3 planes
+    float inyz[3][TY * TZ];               // ... and their a_yz
+    DF accs[kSums][TY * TZ];              // per-thread double-float sums (kept out of registers)
+    float amaxs[TY * TZ];                 // per-thread max |F|^2
     unsigned long long bar[NSLOT];
     DF dfred[kSums * (TY * TZ / 32)];
     float mxred[TY * TZ / 32];
@@ -291,26 +317,174 @@ template <int TY, int TZ> struct __align__(128) StepSmem {
     int last;
 };
 
+struct CtaSync {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+
+// ------------------------------------------------- the plane pipeline
+// Arrival of a haloed plane P: in-plane first and second y/z derivatives of
+// the tile's centre column, d_y phi (each warp fills the z-halo of its own
+// rows) into DY for the mixed d_yz of this plane.
+template <int TY, int TZ>
+__device__ __forceinline__ void arrive_plane(const float4 (*P)[TZ + 4], float4 (*DY)[TZ + 4],
+                                             const InstDesc &D, int tid, int ty, int tz,
+                                             PlaneVals &rv, P4 &dyy, P4 &dzz)
+{
+    const float2 c1 = D.c1, c2 = D.c2, s1 = D.s1, s2 = D.s2, s0 = D.s0;
+    const P4 c = ld4(P[ty + 2][tz + 2]);
+    const P4 ym2 = ld4(P[ty][tz + 2]), ym1 = ld4(P[ty + 1][tz + 2]);
+    const P4 yp1 = ld4(P[ty + 3][tz + 2]), yp2 = ld4(P[ty + 4][tz + 2]);
+    const P4 zm2 = ld4(P[ty + 2][tz]), zm1 = ld4(P[ty + 2][tz + 1]);
+    const P4 zp1 = ld4(P[ty + 2][tz + 3]), zp2 = ld4(P[ty + 2][tz + 4]);
+    const P4 dy = fd1(ym2, ym1, yp1, yp2, c1, c2);
+    const P4 dz = fd1(zm2, zm1, zp1, zp2, c1, c2);
+    dyy = fd2(ym2, ym1, c, yp1, yp2, s1, s2, s0);
+    dzz = fd2(zm2, zm1, c, zp1, zp2, s1, s2, s0);
+    DY[ty][tz + 2] = st4(dy);
+    {  // each warp fills the z-halo columns of d_y phi of its own rows
+        constexpr int ROWS = 32 / TZ;
+        const int lane = tid & 31;
+        if (lane < 4 * ROWS) {
+            const int hr = (tid >> 5) * ROWS + (lane >> 2), ci = lane & 3;
+            const int hc = ci < 2 ? ci : TZ + ci;
+            DY[hr][hc] = st4(fd1(ld4(P[hr][hc]), ld4(P[hr + 1][hc]), ld4(P[hr + 3][hc]),
+                                 ld4(P[hr + 4][hc]), c1, c2));
+        }
+    }
+    rv.phi = c;
+    rv.dy = dy;
+    rv.dz = dz;
+}
+
+// In-plane values of a plane for its own centre two planes later: d_yz, the
+// y/z parts of a_ij, of the Laplacian, of d_ij phi a_ij and of g_y, g_z.
+template <int TY, int TZ>
+__device__ __forceinline__ void plane_record(const float4 (*DY)[TZ + 4], const InstDesc &D, int ty,
+                                             int tz, const PlaneVals &rv, const P4 &dyy,
+                                             const P4 &dzz, float4 *wrec, float *wyz)
+{
+    constexpr int THREADS = TY * TZ;
+    const P4 dy = rv.dy, dz = rv.dz;
+    const P4 dyz = fd1(ld4(DY[ty][tz]), ld4(DY[ty][tz + 1]), ld4(DY[ty][tz + 3]), ld4(DY[ty][tz + 4]),
+                       D.c1, D.c2);
+    const float ayy = dot(dy, dy), azz = dot(dz, dz), ayz = dot(dy, dz);
+    const P4 lin = add(dyy, dzz);
+    const P4 qin = fma(bc(2.f * ayz), dyz, fma(bc(azz), dzz, mul(bc(ayy), dyy)));
+    const float gyv = hsum(dot2(dyz, dz, __ffma2_rn(dyy.b, dy.b, __fmul2_rn(dyy.a, dy.a))));
+    const float gzv = hsum(dot2(dzz, dz, __ffma2_rn(dyz.b, dy.b, __fmul2_rn(dyz.a, dy.a))));
+    wrec[0] = st4(lin);
+    wrec[THREADS] = st4(qin);
+    wrec[2 * THREADS] = make_float4(gyv, gzv, ayy, azz);
+    *wyz = ayz;
+}
+
+// One centre site: x-derivatives from the register ring (M2, M1, C, Q1, Q2 in
+// streaming order; xc1, xc2 are the first-derivative weights along x), the
+// Euler-Lagrange force of Eq. (3.3) projected on the tangent space, the
+// symplectic update with renormalisation, and the energy, charge and force
+// densities into a32 (valid sites only).
+template <int TY, int TZ>
+__device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &M2,
+                                            const PlaneVals &M1, const PlaneVals &C,
+                                            const PlaneVals &Q1, const PlaneVals &Q2, float2 xc1,
+                                            float2 xc2, const float4 *rec, const float *recyz,
+                                            const float4 *vp,
+                                            bool use_v, bool valid, float4 *phiout, float4 *vout,
+                                            size_t si, Acc &a32)
+{
+    constexpr int THREADS = TY * TZ;
+    const float2 s1 = D.s1, s2 = D.s2, s0 = D.s0;
+    const int mode = D.mode;
+    const float2 dt = D.dt, dt2 = D.dt2;
+    const P4 lin = ld4(rec[0]), qin = ld4(rec[THREADS]);
+    const float4 r2 = rec[2 * THREADS];
+    const float Cgy = r2.x, Cgz = r2.y, Cayy = r2.z, Cazz = r2.w;
+    const float Cayz = *recyz;
+    const P4 ph = C.phi;
+    const P4 dx = fd1(M2.phi, M1.phi, Q1.phi, Q2.phi, xc1, xc2);
+    const P4 dxx = fd2(M2.phi, M1.phi, ph, Q1.phi, Q2.phi, s1, s2, s0);
+    const P4 dxy = fd1(M2.dy, M1.dy, Q1.dy, Q2.dy, xc1, xc2);
+    const P4 dxz = fd1(M2.dz, M1.dz, Q1.dz, Q2.dz, xc1, xc2);
+    const P4 dyc = C.dy, dzc = C.dz;
+    const float axx = dot(dx, dx), axy = dot(dx, dyc), axz = dot(dx, dzc);
+    const float tra = axx + Cayy + Cazz;
+    const P4 L = add(dxx, lin);
+    // g_i = sum_j d_ij phi.d_j phi; c_i = g_i - Laplacian.d_i phi
+    const float gx = hsum(dot2(dxz, dzc, dot2(dxy, dyc, __ffma2_rn(dxx.b, dx.b, __fmul2_rn(dxx.a, dx.a)))));
+    const float gy = dot(dxy, dx) + Cgy;
+    const float gz = dot(dxz, dx) + Cgz;
+    const float ccx = gx - dot(L, dx), ccy = gy - dot(L, dyc), ccz = gz - dot(L, dzc);
+    // d_ij phi a_ij summed over i, j
+    const P4 Ha = fma(bc(2.f * axz), dxz, fma(bc(2.f * axy), dxy, fma(bc(axx), dxx, qin)));
+    // brace of the Euler-Lagrange equation; G = -2 (brace + m^2 e_0)
+    P4 br = fma(bc(ccz), dzc, fma(bc(ccy), dyc, fma(bc(ccx), dx, fma(bc(1.f + tra), L, mul(bc(-1.f), Ha)))));
+    br.a.x += D.m2;
+    // F = -G + (G.phi) phi = 2 (br - (br.phi) phi)
+    const float bp = dot(br, ph);
+    const P4 Fh = fma(bc(-bp), ph, br);
+    const float f2 = 4.f * dot(Fh, Fh);
+    P4 t, vnew;
+    if (mode == MODE_GRADIENT) {
+        t = fma(dt2, Fh, ph);
+    } else {
+        const P4 vo = use_v ? ld4(*vp) : P4{bc(0.f), bc(0.f)};
+        vnew = fma(dt2, Fh, vo);
+        t = fma(dt, vnew, ph);
+    }
+    const float r = rsqrtf(dot(t, t));
+    const P4 pn = mul(bc(r), t);
+    const float sq = axx * axx + Cayy * Cayy + Cazz * Cazz + 2.f * (axy * axy + axz * axz + Cayz * Cayz);
+    const float e4 = 0.5f * (tra * tra - sq);
+    // det[phi, d_x phi, d_y phi, d_z phi] by 2x2 minors of rows (phi, d_x), (d_y, d_z)
+    const float q_s0 = ph.a.x * dx.a.y - dx.a.x * ph.a.y;
+    const float2 s12 = __ffma2_rn(bc(-dx.a.x), ph.b, __fmul2_rn(bc(ph.a.x), dx.b));
+    const float2 s34 = __ffma2_rn(bc(-dx.a.y), ph.b, __fmul2_rn(bc(ph.a.y), dx.b));
+    const float q_s5 = ph.b.x * dx.b.y - dx.b.x * ph.b.y;
+    const float q0 = dyc.a.x * dzc.a.y - dzc.a.x * dyc.a.y;
+    const float2 q12 = __ffma2_rn(bc(-dzc.a.x), dyc.b, __fmul2_rn(bc(dyc.a.x), dzc.b));
+    const float2 q34 = __ffma2_rn(bc(-dzc.a.y), dyc.b, __fmul2_rn(bc(dyc.a.y), dzc.b));
+    const float q5 = dyc.b.x * dzc.b.y - dzc.b.x * dyc.b.y;
+    const float det = q_s0 * q5 - s12.x * q34.y + s12.y * q34.x + s34.x * q12.y - s34.y * q12.x + q_s5 * q0;
+    if (valid) {
+        __stcs(phiout + si, st4(pn));
+        if (mode != MODE_GRADIENT) __stcs(vout + si, st4(vnew));
+        a32.e2 += tra;
+        a32.e4 += e4;
+        a32.e0 += 1.f - ph.a.x;
+        a32.b += det;
+        a32.f2 += f2;
+        a32.fmax2 = fmaxf(a32.fmax2, f2);
+    }
+}
+
+__device__ __forceinline__ void write_record(const InstDesc &D, int slot, const DF (&tot)[kSums], float tmax)
+{
+    float4 *recp = reinterpret_cast<float4 *>(D.parts + (size_t)slot * kPartialDoubles);
+    recp[0] = make_float4(tot[0].hi, tot[0].lo, tot[1].hi, tot[1].lo);
+    recp[1] = make_float4(tot[2].hi, tot[2].lo, tot[3].hi, tot[3].lo);
+    recp[2] = make_float4(tot[4].hi, tot[4].lo, tmax, 0.f);
+}
+
 // End of a step for one lattice, run by every thread of the last CTA to
 // leave it.  The CTA records {e2, e4, 1 - phi^0, det, |F|^2} (as hi, lo float
 // pairs) and max |F|^2 are summed in a fixed order; thread 0 then forms the
-// energies of Eq. (2.4), the charge of Eq. (2.6) and the virial, applies the
-// arrest rule of Section 4 (E_n > E_{n-1}: the velocity is zeroed), scores the
-// prediction the launch ran with, and updates the two-level predictor: the
-// last four decisions select a 2-bit saturating counter.
-template <int NW>
+// energies of Eq. (2.4), the charge of Eq. (2.6) and the virial, rounds them
+// to FP64, applies the arrest rule of Section 4 in FP64 (E_n > E_{n-1}: the
+// velocity is zeroed), scores the prediction the launch ran with, and updates
+// the two-level predictor: the last four decisions select a 2-bit saturating
+// counter.
+template <int NW, typename Sync>
 __device__ __forceinline__ void finish_lattice(const InstDesc &D, Ctrl *c, int cur, int mode,
-                                               int pred, int dry, DF *buf, float *amx)
+                                               int pred, int dry, DF *buf, float *amx, int tid,
+                                               Sync sync)
 {
-    const int tid = threadIdx.x;
     // thread 0 fetches the control fields it needs while the block sums the records
-    float ep_hi = 0.f, ep_lo = 0.f;
+    double E_prev = 0.0;
     int hist = 0;
     uint4 pht4 = make_uint4(0u, 0u, 0u, 0u);
     long long steps = 0, arrests = 0, fixups = 0;
     if (tid == 0 && !dry) {
-        ep_hi = __ldcg(&c->eprev_hi);
-        ep_lo = __ldcg(&c->eprev_lo);
+        E_prev = __ldcg(&c->E_prev);
         hist = __ldcg(&c->hist);
         pht4 = __ldcg(reinterpret_cast<const uint4 *>(c->pht));
         steps = __ldcg(&c->steps);
@@ -331,7 +505,7 @@ __device__ __forceinline__ void finish_lattice(const InstDesc &D, Ctrl *c, int c
     }
     DF t[kSums];
     float tmax = 0.f;
-    block_reduce_df<NW>(v, amax, buf, amx, t, tmax);
+    block_reduce_df<NW>(v, amax, buf, amx, t, tmax, tid, sync);
     if (tid != 0) return;
     if (dry) {
         c->done = 0;
@@ -345,7 +519,8 @@ __device__ __forceinline__ void finish_lattice(const InstDesc &D, Ctrl *c, int c
     const DF E = df_add(df_add(E2, E4), E0);
     const DF B = df_mul(h3, df_mul(bfac, t[3]));
     const DF V = df_add(df_add(df_neg(E2), E4), df_mul(DF{-3.f, 0.f}, E0));
-    const int actual = (mode == MODE_ARRESTED && df_gt(E, DF{ep_hi, ep_lo})) ? 1 : 0;
+    const double Ed = df_value(E);
+    const int actual = (mode == MODE_ARRESTED && Ed > E_prev) ? 1 : 0;
     const int fix = (actual == pred) ? 0 : (actual ? -1 : +1);
     unsigned char pht[16];
     memcpy(pht, &pht4, sizeof(pht));
@@ -360,10 +535,7 @@ __device__ __forceinline__ void finish_lattice(const InstDesc &D, Ctrl *c, int c
     c->fix = fix;
     c->arrests = arrests + actual;
     c->fixups = fixups + (fix != 0);
-    const double Ed = df_value(E);
     c->E_prev = Ed;
-    c->eprev_hi = E.hi;
-    c->eprev_lo = E.lo;
     c->steps = steps + 1;
     c->cur = cur ^ 1;
     const float nsites = (float)(D.n0 - 4) * (float)(D.n1 - 4) * (float)(D.n2 - 4);
@@ -375,14 +547,14 @@ __device__ __forceinline__ void finish_lattice(const InstDesc &D, Ctrl *c, int c
     c->last[5] = df_value(V);
     c->last[6] = (double)sqrtf(tmax);
     c->last[7] = (double)sqrtf(t[4].hi / nsites);
-    if (!(isfinite(E.hi) && isfinite(B.hi) && isfinite(t[4].hi))) c->status = DEV_NONFINITE;
+    if (!(isfinite(Ed) && isfinite(B.hi) && isfinite(t[4].hi))) c->status = DEV_NONFINITE;
     c->done = 0;
 }
 
-// The step for every lattice of the launch.  BATCHED: lattices come from
-// `table` (ninst entries, ordered by unit_start); otherwise from `one`.
-// dry != 0 (autotuning): outputs land in the inactive buffers and the
-// control blocks are left as they were.
+// The step for every lattice of the launch, two CTAs per SM.  BATCHED:
+// lattices come from `table` (ninst entries, ordered by unit_start); otherwise
+// from `one`.  dry != 0 (autotuning): outputs land in the inactive buffers and
+// the control blocks are left as they were.
 template <int TY, int TZ, bool BATCHED>
 __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
     k_step_f32(const __grid_constant__ InstDesc one, const InstDesc *__restrict__ table, int ninst,
@@ -398,7 +570,10 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
     const int ty = tid / TZ, tz = tid % TZ;
 
     if (tid == 0) {
-        for (int s = 0; s < NSLOT; ++s) mbar_init(&sm.bar[s], 1);
+        for (int s = 0; s < NSLOT; ++s) {
+            mbar_init(&sm.bar[s], 1);
+            sm.rel[s] = 0;
+        }
         mbar_fence_init();
         sm.flag = 0;
     }
@@ -409,7 +584,8 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
     int inst = 0;
     if (BATCHED)
         while (inst + 1 < ninst && table[inst + 1].unit_start <= u0) ++inst;
-    uint32_t g = 0;  // planes consumed by this CTA (ring sequence number)
+    uint32_t g = 0;   // planes consumed by this CTA (ring sequence number)
+    uint32_t g3 = 0;  // g % 3, the in-plane record slot of plane g
     bool failed = false;
 
     for (long long us = u0; us < u1 && !failed; ++inst) {
@@ -426,17 +602,11 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
         float4 *__restrict__ vout = D.vel[cur ^ 1];
         const int mode = D.mode;
         const bool use_v = (mode != MODE_GRADIENT) && !pred;
-#define c1 D.c1
-#define c2 D.c2
-#define s1 D.s1
-#define s2 D.s2
-#define s0 D.s0
-#define m2 D.m2
-        const float dt = D.dt, dt2 = 2.0f * D.dt;
         const int nix = D.nix, nzt = D.nzt, n1 = D.n1, n2 = D.n2;
         const size_t plane_stride = (size_t)n1 * n2;
-        DF acc[kSums] = {};
-        float amax = 0.f;
+        DF *acc = &sm.accs[0][tid];
+        float *amax = &sm.amaxs[tid];
+        zero_sums(acc, amax, THREADS);
         Acc a32 = {0, 0, 0, 0, 0, 0};
 
         while (us < seg_hi && !failed) {
@@ -470,155 +640,66 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
                     const int s = g % NSLOT;
                     const uint32_t par = (g / NSLOT) & 1u;
                     if (!mbar_wait(&sm.bar[s], par)) sm.flag = 1;
-                    // ---- arrival of plane pp: in-plane first and second derivatives
-                    const float4(*P)[TZ + 4] = sm.plane[s];
-                    const P4 c = ld4(P[ty + 2][tz + 2]);
-                    const P4 ym2 = ld4(P[ty][tz + 2]), ym1 = ld4(P[ty + 1][tz + 2]);
-                    const P4 yp1 = ld4(P[ty + 3][tz + 2]), yp2 = ld4(P[ty + 4][tz + 2]);
-                    const P4 zm2 = ld4(P[ty + 2][tz]), zm1 = ld4(P[ty + 2][tz + 1]);
-                    const P4 zp1 = ld4(P[ty + 2][tz + 3]), zp2 = ld4(P[ty + 2][tz + 4]);
-                    const P4 dy = fd1(ym2, ym1, yp1, yp2, c1, c2);
-                    const P4 dz = fd1(zm2, zm1, zp1, zp2, c1, c2);
-                    const P4 dyy = fd2(ym2, ym1, c, yp1, yp2, s1, s2, s0);
-                    const P4 dzz = fd2(zm2, zm1, c, zp1, zp2, s1, s2, s0);
                     float4(*DY)[TZ + 4] = sm.dy[g & 1];
-                    DY[ty][tz + 2] = st4(dy);
-                    if (tid >= THREADS - 32) {  // the last warp fills every z-halo column of d_y phi
-                        for (int j = tid - (THREADS - 32); j < 4 * TY; j += 32) {
-                            const int hr = j >> 2, ci = j & 3;
-                            const int hc = ci < 2 ? ci : TZ + ci;
-                            DY[hr][hc] = st4(fd1(ld4(P[hr][hc]), ld4(P[hr + 1][hc]), ld4(P[hr + 3][hc]),
-                                                 ld4(P[hr + 4][hc]), c1, c2));
-                        }
-                    }
-                    ring[k].phi = c;
-                    ring[k].dy = dy;
-                    ring[k].dz = dz;
-
-                    // ---- centre x = pp - 2: x-derivatives, physics, update
+                    P4 dyy, dzz;
+                    arrive_plane<TY, TZ>(sm.plane[s], DY, D, tid, ty, tz, ring[k], dyy, dzz);
+                    // ---- centre x = pp - 2, whose in-plane record is that of plane g - 2
+                    const uint32_t g3n = g3 == 2 ? 0 : g3 + 1;  // (g + 1) % 3 == (g - 2) % 3
                     const int x = pp - 2;
-                    if (x >= xs) {
-                        const PlaneVals &M2 = ring[(k + 1) % 5], &M1 = ring[(k + 2) % 5];
-                        const PlaneVals &C = ring[(k + 3) % 5], &Q1 = ring[(k + 4) % 5];
-                        const PlaneVals &Q2 = ring[k];
-                        const float4 *rec = &sm.inpl[(g + 1) % 3][0][tid];  // plane x = pp - 2
-                        const P4 lin = ld4(rec[0]), qin = ld4(rec[THREADS]);
-                        const float4 r2 = rec[2 * THREADS];
-                        const float Cgy = r2.x, Cgz = r2.y, Cayy = r2.z, Cazz = r2.w;
-                        const float Cayz = rec[3 * THREADS].x;
-                        const P4 ph = C.phi;
-                        const P4 dx = fd1(M2.phi, M1.phi, Q1.phi, Q2.phi, c1, c2);
-                        const P4 dxx = fd2(M2.phi, M1.phi, ph, Q1.phi, Q2.phi, s1, s2, s0);
-                        const P4 dxy = fd1(M2.dy, M1.dy, Q1.dy, Q2.dy, c1, c2);
-                        const P4 dxz = fd1(M2.dz, M1.dz, Q1.dz, Q2.dz, c1, c2);
-                        const P4 dyc = C.dy, dzc = C.dz;
-                        const float axx = dot(dx, dx), axy = dot(dx, dyc), axz = dot(dx, dzc);
-                        const float tra = axx + Cayy + Cazz;
-                        const P4 L = add(dxx, lin);
-                        // g_i = sum_j d_ij phi.d_j phi; c_i = g_i - Laplacian.d_i phi
-                        const float gx = hsum(dot2(dxz, dzc, dot2(dxy, dyc,
-                                                       __ffma2_rn(dxx.b, dx.b, __fmul2_rn(dxx.a, dx.a)))));
-                        const float gy = dot(dxy, dx) + Cgy;
-                        const float gz = dot(dxz, dx) + Cgz;
-                        const float ccx = gx - dot(L, dx), ccy = gy - dot(L, dyc), ccz = gz - dot(L, dzc);
-                        // d_ij phi a_ij summed over i, j
-                        const P4 Ha = fma(bc(2.f * axz), dxz, fma(bc(2.f * axy), dxy, fma(bc(axx), dxx, qin)));
-                        // brace of the Euler-Lagrange equation; G = -2 (brace + m^2 e_0)
-                        P4 br = fma(bc(ccz), dzc, fma(bc(ccy), dyc, fma(bc(ccx), dx,
-                                    fma(bc(1.f + tra), L, mul(bc(-1.f), Ha)))));
-                        br.a.x += m2;
-                        // F = -G + (G.phi) phi = 2 (br - (br.phi) phi)
-                        const float bp = dot(br, ph);
-                        const P4 Fh = fma(bc(-bp), ph, br);
-                        const float f2 = 4.f * dot(Fh, Fh);
-                        P4 t, vnew;
-                        if (mode == MODE_GRADIENT) {
-                            t = fma(bc(dt2), Fh, ph);
-                        } else {
-                            const P4 vo = use_v ? ld4(sm.vpl[s][ty][tz]) : P4{bc(0.f), bc(0.f)};
-                            vnew = fma(bc(dt2), Fh, vo);
-                            t = fma(bc(dt), vnew, ph);
-                        }
-                        const float r = rsqrtf(dot(t, t));
-                        const P4 pn = mul(bc(r), t);
-                        const float sq = axx * axx + Cayy * Cayy + Cazz * Cazz +
-                                         2.f * (axy * axy + axz * axz + Cayz * Cayz);
-                        const float e4 = 0.5f * (tra * tra - sq);
-                        // det[phi, d_x phi, d_y phi, d_z phi] by 2x2 minors of rows (phi, d_x), (d_y, d_z)
-                        const float q_s0 = ph.a.x * dx.a.y - dx.a.x * ph.a.y;
-                        const float2 s12 = __ffma2_rn(bc(-dx.a.x), ph.b, __fmul2_rn(bc(ph.a.x), dx.b));
-                        const float2 s34 = __ffma2_rn(bc(-dx.a.y), ph.b, __fmul2_rn(bc(ph.a.y), dx.b));
-                        const float q_s5 = ph.b.x * dx.b.y - dx.b.x * ph.b.y;
-                        const float q0 = dyc.a.x * dzc.a.y - dzc.a.x * dyc.a.y;
-                        const float2 q12 = __ffma2_rn(bc(-dzc.a.x), dyc.b, __fmul2_rn(bc(dyc.a.x), dzc.b));
-                        const float2 q34 = __ffma2_rn(bc(-dzc.a.y), dyc.b, __fmul2_rn(bc(dyc.a.y), dzc.b));
-                        const float q5 = dyc.b.x * dzc.b.y - dzc.b.x * dyc.b.y;
-                        const float det = q_s0 * q5 - s12.x * q34.y + s12.y * q34.x + s34.x * q12.y -
-                                          s34.y * q12.x + q_s5 * q0;
-                        if (valid) {
-                            const size_t si = (size_t)x * plane_stride + col_off;
-                            __stcs(phiout + si, st4(pn));
-                            if (mode != MODE_GRADIENT) __stcs(vout + si, st4(vnew));
-                            a32.e2 += tra;
-                            a32.e4 += e4;
-                            a32.e0 += 1.f - ph.a.x;
-                            a32.b += det;
-                            a32.f2 += f2;
-                            a32.fmax2 = fmaxf(a32.fmax2, f2);
+                    if (x >= xs)
+                        centre_site<TY, TZ>(D, ring[(k + 1) % 5], ring[(k + 2) % 5], ring[(k + 3) % 5],
+                                            ring[(k + 4) % 5], ring[k], D.c1, D.c2,
+                                            &sm.inpl[g3n][0][tid], &sm.inyz[g3n][tid],
+                                            &sm.vpl[s][ty][tz], use_v,
+                                            valid, phiout, vout, (size_t)x * plane_stride + col_off, a32);
+                    // this warp is done with slot s; the last warp to leave it streams
+                    // plane pp + NSLOT (and its velocity) into it
+                    __syncwarp();
+                    if ((tid & 31) == 0) {
+                        __threadfence_block();
+                        if (atomicAdd(&sm.rel[s], 1) == THREADS / 32 - 1) {
+                            sm.rel[s] = 0;
+                            __threadfence_block();
+                            if (pp + NSLOT <= pl) {
+                                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                                issue(pp + NSLOT, s);
+                            }
                         }
                     }
-                    __syncthreads();
-                    if (sm.flag) {
+                    if (*(volatile int *)&sm.flag) {
                         failed = true;
                         break;
                     }
-                    // slot s is free again: stream plane pp + NSLOT (and its velocity) into it
-                    if (tid == 0 && pp + NSLOT <= pl) issue(pp + NSLOT, s);
-                    // ---- in-plane values of plane pp for its own centre, two planes on
-                    const P4 dyz = fd1(ld4(DY[ty][tz]), ld4(DY[ty][tz + 1]), ld4(DY[ty][tz + 3]),
-                                       ld4(DY[ty][tz + 4]), c1, c2);
-                    const float ayy = dot(dy, dy), azz = dot(dz, dz), ayz = dot(dy, dz);
-                    const P4 lin = add(dyy, dzz);
-                    const P4 qin = fma(bc(2.f * ayz), dyz, fma(bc(azz), dzz, mul(bc(ayy), dyy)));
-                    const float gyv = hsum(dot2(dyz, dz, __ffma2_rn(dyy.b, dy.b, __fmul2_rn(dyy.a, dy.a))));
-                    const float gzv = hsum(dot2(dzz, dz, __ffma2_rn(dyz.b, dy.b, __fmul2_rn(dyz.a, dy.a))));
-                    float4 *wrec = &sm.inpl[g % 3][0][tid];
-                    wrec[0] = st4(lin);
-                    wrec[THREADS] = st4(qin);
-                    wrec[2 * THREADS] = make_float4(gyv, gzv, ayy, azz);
-                    wrec[3 * THREADS] = make_float4(ayz, 0.f, 0.f, 0.f);
+                    plane_record<TY, TZ>(DY, D, ty, tz, ring[k], dyy, dzz, &sm.inpl[g3][0][tid],
+                                         &sm.inyz[g3][tid]);
                     ++g;
+                    g3 = g3n;
                 }
                 // FP32 partial sums cover at most 40 planes before entering the double-float sums
-                if ((++nouter & 7) == 0) flush(acc, amax, a32);
+                if ((++nouter & 7) == 0) flush(acc, amax, THREADS, a32);
             }
-            flush(acc, amax, a32);
+            flush(acc, amax, THREADS, a32);
+            // every warp is done with the run's planes before its slots are reused
+            __syncthreads();
+            failed = sm.flag != 0;
         }
-#undef c1
-#undef c2
-#undef s1
-#undef s2
-#undef s0
-#undef m2
         if (failed) break;
 
         // ---- this CTA is done with lattice D: block reduction, per-lattice finish
-        DF tot[kSums];
-        float tmax = 0.f;
-        block_reduce_df<THREADS / 32>(acc, amax, sm.dfred, sm.mxred, tot, tmax);
+        DF tot[kSums], mine[kSums];
+        float tmax = 0.f, mmax;
+        load_sums(acc, amax, THREADS, mine, mmax);
+        block_reduce_df<THREADS / 32>(mine, mmax, sm.dfred, sm.mxred, tot, tmax, tid, CtaSync{});
         if (tid == 0) {
-            float4 *recp = reinterpret_cast<float4 *>(D.parts + (size_t)(blockIdx.x - D.cta_first) *
-                                                                    kPartialDoubles);
-            recp[0] = make_float4(tot[0].hi, tot[0].lo, tot[1].hi, tot[1].lo);
-            recp[1] = make_float4(tot[2].hi, tot[2].lo, tot[3].hi, tot[3].lo);
-            recp[2] = make_float4(tot[4].hi, tot[4].lo, tmax, 0.f);
+            write_record(D, (int)blockIdx.x - D.cta_first, tot, tmax);
             __threadfence();
             sm.last = (atomicAdd(&ctrl->done, 1u) == (unsigned)(D.cta_count - 1));
         }
         __syncthreads();
         if (sm.last) {
             __threadfence();
-            finish_lattice<THREADS / 32>(D, ctrl, cur, mode, pred, dry, sm.dfred, sm.mxred);
+            finish_lattice<THREADS / 32>(D, ctrl, cur, mode, pred, dry, sm.dfred, sm.mxred, tid,
+                                         CtaSync{});
         }
         __syncthreads();
     }
@@ -723,7 +804,7 @@ __global__ void __launch_bounds__(512, 2) k_fixup_batch(const InstDesc *__restri
             need &= need - 1;
             const int f = __shfl_sync(0xffffffffu, fix, j), cj = __shfl_sync(0xffffffffu, cur, j);
             const InstDesc &D = table[i0 + j];
-            fixup_rows(D.phi, D.vel, cj, D.n0, D.n1, D.n2, D.dt, f, wg, ws);
+            fixup_rows(D.phi, D.vel, cj, D.n0, D.n1, D.n2, D.dt.x, f, wg, ws);
         }
     }
 }
@@ -874,13 +955,15 @@ static bool fill_desc(InstDesc &d, const skyrme_lattice &lat, const skyrme_state
     d.nix = lat.n[0] - 4;
     d.units = (long long)nyt * d.nzt * d.nix;
     const double ih = 1.0 / lat.h, ih2 = ih * ih;
-    d.c1 = (float)(2.0 / 3.0 * ih);
-    d.c2 = (float)(-1.0 / 12.0 * ih);
-    d.s1 = (float)(4.0 / 3.0 * ih2);
-    d.s2 = (float)(-1.0 / 12.0 * ih2);
-    d.s0 = (float)(-2.5 * ih2);
+    auto pair = [](double w) { return make_float2((float)w, (float)w); };
+    d.c1 = pair(2.0 / 3.0 * ih);
+    d.c2 = pair(-1.0 / 12.0 * ih);
+    d.s1 = pair(4.0 / 3.0 * ih2);
+    d.s2 = pair(-1.0 / 12.0 * ih2);
+    d.s0 = pair(-2.5 * ih2);
     d.m2 = (float)(lat.m * lat.m);
-    d.dt = (float)dt;
+    d.dt = make_float2((float)dt, (float)dt);
+    d.dt2 = make_float2(2.f * (float)dt, 2.f * (float)dt);
     const double h3 = lat.h * lat.h * lat.h;
     d.h3_hi = (float)h3;
     d.h3_lo = (float)(h3 - (double)d.h3_hi);

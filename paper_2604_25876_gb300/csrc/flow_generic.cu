@@ -312,8 +312,6 @@ __global__ void k_reset_ctrl(Ctrl *c)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         c->E_prev = __longlong_as_double(0x7ff0000000000000LL);  // +inf
-        c->eprev_hi = __int_as_float(0x7f800000);
-        c->eprev_lo = 0.f;
         for (int i = 0; i < 8; ++i) c->last[i] = 0.0, c->energy[i] = 0.0;
         c->steps = 0;
         c->arrests = 0;

@@ -68,8 +68,7 @@ struct Ctrl {
     int hist;             // last 4 arrest decisions (bit 0 = latest)
     int pad_i;
     unsigned char pht[16];  // 2-bit saturating counters indexed by hist
-    float eprev_hi, eprev_lo;  // E_prev as an unevaluated float sum (FP32 streaming kernel)
-    double pad[2];
+    double pad[3];
 };
 static_assert(sizeof(Ctrl) <= 512, "control block must fit its 512-byte slot");
 static_assert(offsetof(Ctrl, pht) % 16 == 0, "pht is read as one 16-byte word");
@@ -293,11 +292,6 @@ __device__ __forceinline__ void finish_step(Ctrl *c, const double (&tot)[kPartia
     c->arrests += actual;
     c->fixups += (fix != 0);
     c->E_prev = E;
-    {
-        const float eh = (float)E;
-        c->eprev_hi = eh;
-        c->eprev_lo = isfinite(E) ? (float)(E - (double)eh) : 0.f;
-    }
     c->steps += 1;
     c->cur ^= 1;
     c->last[0] = E;

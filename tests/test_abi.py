@@ -85,3 +85,10 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(sk._build, "LIB", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         sk.load(build_if_missing=False)
+
+
+def test_fma_peak_rejects_bad_arguments_without_cuda():
+    lib = sk.load()
+    out = ctypes.c_double(0.0)
+    assert lib.skyrme_measure_fma_peak(7, ctypes.byref(out), None) == 1
+    assert lib.skyrme_measure_fma_peak(sk.PEAK_FP32, None, None) == 1
