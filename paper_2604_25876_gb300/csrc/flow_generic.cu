@@ -35,6 +35,8 @@ template <typename T> struct FlowParams {
     double *parts;
     int n0, n1, n2;
     T inv_h, inv_h2, m2, dt;
+    T w1, w2;      // first-derivative weights / h
+    T v1, v2, v0;  // second-derivative weights / h^2
     double h3;
     int mode;
 };
@@ -63,15 +65,71 @@ __device__ __forceinline__ void load_tile(vec4_t<T> *tile, const vec4_t<T> *phi,
     }
 }
 
+// Scaled stencils: w1 (p1 - m1) + w2 (p2 - m2) and v1 (p1 + m1) + v2 (p2 + m2) + v0 c
+template <typename T> __device__ __forceinline__ T sd1(T m2v, T m1v, T p1v, T p2v, T w1, T w2)
+{
+    return w1 * (p1v - m1v) + w2 * (p2v - m2v);
+}
+template <typename T>
+__device__ __forceinline__ T sd2(T m2v, T m1v, T c, T p1v, T p2v, T v1, T v2, T v0)
+{
+    return v1 * (p1v + m1v) + v2 * (p2v + m2v) + v0 * c;
+}
+template <typename T>
+__device__ __forceinline__ vec4_t<T> sd1v(const vec4_t<T> &m2v, const vec4_t<T> &m1v,
+                                          const vec4_t<T> &p1v, const vec4_t<T> &p2v, T w1, T w2)
+{
+    return make4<T>(sd1<T>(m2v.x, m1v.x, p1v.x, p2v.x, w1, w2), sd1<T>(m2v.y, m1v.y, p1v.y, p2v.y, w1, w2),
+                    sd1<T>(m2v.z, m1v.z, p1v.z, p2v.z, w1, w2), sd1<T>(m2v.w, m1v.w, p1v.w, p2v.w, w1, w2));
+}
+
+// Shared-memory layout of the tile kernels: the haloed field tile, then
+// d_x phi on the interior x-planes of the tile over (y, z) widened by 2, then
+// d_y phi on the interior (x, y) rows of the tile over z widened by 2.  The
+// mixed derivatives are first-derivative stencils of these (Section 3,
+// reading R1: d_xy = d_y(d_x phi), d_xz = d_z(d_x phi), d_yz = d_z(d_y phi)),
+// which costs a quarter of the FP64 operations of the 16-tap sums.
+constexpr int GDX = GTX * GSY * GSZ;  // entries of d_x phi
+constexpr int GDY = GTX * GTY * GSZ;  // entries of d_y phi
+template <typename T> constexpr size_t tile_smem_bytes()
+{
+    return (size_t)(GSX * GSY * GSZ + GDX + GDY) * sizeof(vec4_t<T>);
+}
+
+// Stage d_x phi and d_y phi of the tile (all threads), from the loaded tile.
+// Entries whose stencil leaves the lattice hold garbage that only sites
+// outside the interior read.
+template <typename T>
+__device__ __forceinline__ void stage_first_derivatives(const vec4_t<T> *tile, vec4_t<T> *dxs,
+                                                        vec4_t<T> *dys, T w1, T w2)
+{
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    auto P = [&](int tx, int ty, int tz) -> const vec4_t<T> & { return tile[(tx * GSY + ty) * GSZ + tz]; };
+    for (int i = tid; i < GDX; i += GTHREADS) {
+        const int lz = i % GSZ, ly = (i / GSZ) % GSY, lx = i / (GSZ * GSY);
+        dxs[i] = sd1v<T>(P(lx, ly, lz), P(lx + 1, ly, lz), P(lx + 3, ly, lz), P(lx + 4, ly, lz), w1, w2);
+    }
+    for (int i = tid; i < GDY; i += GTHREADS) {
+        const int lz = i % GSZ, ly = (i / GSZ) % GTY, lx = i / (GSZ * GTY);
+        dys[i] = sd1v<T>(P(lx + 2, ly, lz), P(lx + 2, ly + 1, lz), P(lx + 2, ly + 3, lz),
+                         P(lx + 2, ly + 4, lz), w1, w2);
+    }
+}
+
 // All derivatives of the site at local interior coordinate (lx, ly, lz).
 template <typename T>
-__device__ __forceinline__ void tile_derivatives(const vec4_t<T> *tile, int lx, int ly, int lz,
-                                                 T inv_h, T inv_h2, T phi[4], T d1[3][4],
+__device__ __forceinline__ void tile_derivatives(const vec4_t<T> *tile, const vec4_t<T> *dxs,
+                                                 const vec4_t<T> *dys, int lx, int ly, int lz,
+                                                 const FlowParams<T> &p, T phi[4], T d1[3][4],
                                                  T d2[3][4], T dm[3][4])
 {
     auto P = [&](int dx, int dy, int dz) -> vec4_t<T> {
         return tile[((lx + 2 + dx) * GSY + (ly + 2 + dy)) * GSZ + (lz + 2 + dz)];
     };
+    // d_x phi at (lx, ly + 2 + dy, lz + 2 + dz) and d_y phi at (lx, ly, lz + 2 + dz)
+    auto DX = [&](int dy, int dz) -> vec4_t<T> { return dxs[(lx * GSY + ly + 2 + dy) * GSZ + lz + 2 + dz]; };
+    auto DY = [&](int dz) -> vec4_t<T> { return dys[(lx * GTY + ly) * GSZ + lz + 2 + dz]; };
+    const T w1 = p.w1, w2 = p.w2, v1 = p.v1, v2 = p.v2, v0 = p.v0;
     const vec4_t<T> c = P(0, 0, 0);
     const int off[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
 #pragma unroll
@@ -82,39 +140,24 @@ __device__ __forceinline__ void tile_derivatives(const vec4_t<T> *tile, int lx, 
         const vec4_t<T> p2v = P(2 * off[i][0], 2 * off[i][1], 2 * off[i][2]);
 #pragma unroll
         for (int A = 0; A < 4; ++A) {
-            d1[i][A] = fd1<T>(comp<T>(m2v, A), comp<T>(m1v, A), comp<T>(p1v, A), comp<T>(p2v, A)) * inv_h;
-            d2[i][A] = fd2<T>(comp<T>(m2v, A), comp<T>(m1v, A), comp<T>(c, A), comp<T>(p1v, A),
-                              comp<T>(p2v, A)) * inv_h2;
+            if (i == 2)
+                d1[i][A] = sd1<T>(comp<T>(m2v, A), comp<T>(m1v, A), comp<T>(p1v, A), comp<T>(p2v, A), w1, w2);
+            d2[i][A] = sd2<T>(comp<T>(m2v, A), comp<T>(m1v, A), comp<T>(c, A), comp<T>(p1v, A),
+                              comp<T>(p2v, A), v1, v2, v0);
         }
     }
+    const vec4_t<T> dx0 = DX(0, 0), dy0 = DY(0);
+    const vec4_t<T> xym2 = DX(-2, 0), xym1 = DX(-1, 0), xyp1 = DX(1, 0), xyp2 = DX(2, 0);
+    const vec4_t<T> xzm2 = DX(0, -2), xzm1 = DX(0, -1), xzp1 = DX(0, 1), xzp2 = DX(0, 2);
+    const vec4_t<T> yzm2 = DY(-2), yzm1 = DY(-1), yzp1 = DY(1), yzp2 = DY(2);
 #pragma unroll
-    for (int A = 0; A < 4; ++A) phi[A] = comp<T>(c, A);
-    // mixed derivatives: outer stencil along the first axis of the pair applied
-    // to the inner stencil along the second
-    const int pr[3][2] = {{0, 1}, {0, 2}, {1, 2}};
-#pragma unroll
-    for (int p = 0; p < 3; ++p) {
-        const int a = pr[p][0], b = pr[p][1];
-        T inner[4][4];  // [outer offset index][A]
-        const int offs[4] = {-2, -1, 1, 2};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int oa = offs[k];
-            const vec4_t<T> q0 = P(oa * off[a][0] - 2 * off[b][0], oa * off[a][1] - 2 * off[b][1],
-                                   oa * off[a][2] - 2 * off[b][2]);
-            const vec4_t<T> q1 = P(oa * off[a][0] - off[b][0], oa * off[a][1] - off[b][1],
-                                   oa * off[a][2] - off[b][2]);
-            const vec4_t<T> q2 = P(oa * off[a][0] + off[b][0], oa * off[a][1] + off[b][1],
-                                   oa * off[a][2] + off[b][2]);
-            const vec4_t<T> q3 = P(oa * off[a][0] + 2 * off[b][0], oa * off[a][1] + 2 * off[b][1],
-                                   oa * off[a][2] + 2 * off[b][2]);
-#pragma unroll
-            for (int A = 0; A < 4; ++A)
-                inner[k][A] = fd1<T>(comp<T>(q0, A), comp<T>(q1, A), comp<T>(q2, A), comp<T>(q3, A));
-        }
-#pragma unroll
-        for (int A = 0; A < 4; ++A)
-            dm[p][A] = fd1<T>(inner[0][A], inner[1][A], inner[2][A], inner[3][A]) * inv_h2;
+    for (int A = 0; A < 4; ++A) {
+        phi[A] = comp<T>(c, A);
+        d1[0][A] = comp<T>(dx0, A);
+        d1[1][A] = comp<T>(dy0, A);
+        dm[0][A] = sd1<T>(comp<T>(xym2, A), comp<T>(xym1, A), comp<T>(xyp1, A), comp<T>(xyp2, A), w1, w2);
+        dm[1][A] = sd1<T>(comp<T>(xzm2, A), comp<T>(xzm1, A), comp<T>(xzp1, A), comp<T>(xzp2, A), w1, w2);
+        dm[2][A] = sd1<T>(comp<T>(yzm2, A), comp<T>(yzm1, A), comp<T>(yzp1, A), comp<T>(yzp2, A), w1, w2);
     }
 }
 
@@ -193,6 +236,10 @@ __global__ void __launch_bounds__(GTHREADS) k_tile(FlowParams<T> p, vec4_t<T> *f
     const int x0 = 2 + blockIdx.z * GTX, y0 = 2 + blockIdx.y * GTY, z0 = 2 + blockIdx.x * GTZ;
     load_tile<T>(tile, phi, x0, y0, z0, p.n0, p.n1, p.n2);
     __syncthreads();
+    vec4_t<T> *dxs = tile + GSX * GSY * GSZ;
+    vec4_t<T> *dys = dxs + GDX;
+    stage_first_derivatives<T>(tile, dxs, dys, p.w1, p.w2);
+    __syncthreads();
 
     const int lz = threadIdx.x, ly = threadIdx.y, lx = threadIdx.z;
     const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
@@ -200,7 +247,7 @@ __global__ void __launch_bounds__(GTHREADS) k_tile(FlowParams<T> p, vec4_t<T> *f
     double acc[6] = {0, 0, 0, 0, 0, 0};
     if (valid) {
         T ph[4], d1[3][4], d2[3][4], dm[3][4], F[4], dens[4];
-        tile_derivatives<T>(tile, lx, ly, lz, p.inv_h, p.inv_h2, ph, d1, d2, dm);
+        tile_derivatives<T>(tile, dxs, dys, lx, ly, lz, p, ph, d1, d2, dm);
         site_physics<T>(ph, d1, d2, dm, p.m2, F, dens);
         const size_t s = site_index(x, y, z, p.n1, p.n2);
         if (KIND == 0) {
@@ -335,7 +382,7 @@ TileGeom tile_geometry(const skyrme_lattice &lat)
     g.grid = dim3((iz + GTZ - 1) / GTZ, (iy + GTY - 1) / GTY, (ix + GTX - 1) / GTX);
     g.block = dim3(GTZ, GTY, GTX);
     g.nblocks = (int)(g.grid.x * g.grid.y * g.grid.z);
-    g.smem = (size_t)GSX * GSY * GSZ * (lat.precision == 64 ? sizeof(dvec4) : sizeof(float4));
+    g.smem = lat.precision == 64 ? tile_smem_bytes<double>() : tile_smem_bytes<float>();
     return g;
 }
 
@@ -353,6 +400,12 @@ template <typename T> static FlowParams<T> make_params(const FlowArgs &a, double
     p.n2 = a.n[2];
     p.inv_h = T(1.0 / a.h);
     p.inv_h2 = T(1.0 / (a.h * a.h));
+    const double ih = 1.0 / a.h, ih2 = ih * ih;
+    p.w1 = T(2.0 / 3.0 * ih);
+    p.w2 = T(-1.0 / 12.0 * ih);
+    p.v1 = T(4.0 / 3.0 * ih2);
+    p.v2 = T(-1.0 / 12.0 * ih2);
+    p.v0 = T(-2.5 * ih2);
     p.m2 = T(a.m * a.m);
     p.dt = T(a.dt);
     p.h3 = a.h * a.h * a.h;
@@ -369,7 +422,7 @@ static cudaError_t launch_tile(const skyrme_lattice &lat, const FlowParams<T> &p
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_tile<T, KIND>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(GSX * GSY * GSZ * sizeof(vec4_t<T>)));
+                                             (int)tile_smem_bytes<T>());
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
