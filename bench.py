@@ -169,13 +169,14 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ our kernels
-def kernel_fingerprint():
+def kernel_fingerprint(prec: int = 32):
+    """Hash of the sources of the step kernel of one precision: the FP32
+    streaming kernel or the tile kernels (FP64), with their shared header."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2604_25876_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.startswith("flow_") or name == "skyrme_device.cuh":
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(f.read())
+    for name in ("flow_f32.cu" if prec == 32 else "flow_generic.cu", "skyrme_device.cuh"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -188,7 +189,8 @@ def recorded_traffic(kernel_key: str, per_launch_sites: int):
             rec = json.load(f).get(kernel_key)
     except Exception:
         return None
-    if not rec or rec.get("fingerprint") != kernel_fingerprint():
+    prec = 64 if kernel_key.startswith("step_f64") else 32
+    if not rec or rec.get("fingerprint") != kernel_fingerprint(prec):
         return None
     scale = per_launch_sites / float(rec["sites"])
     return float(rec["dram_bytes_per_launch"]) * scale
