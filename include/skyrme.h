@@ -144,6 +144,23 @@ skyrme_status skyrme_graph_create(const skyrme_lattice *lat, double dt, int nste
 skyrme_status skyrme_graph_launch(skyrme_graph *g, void *stream);
 skyrme_status skyrme_graph_destroy(skyrme_graph *g);
 
+/* skyrme_graph_create_until: a graph that, on each launch, relaxes the flow
+ * until it has converged, without returning to the host: a device-side WHILE
+ * node repeats `chunk` iterations (as skyrme_flow_step launches them)
+ * followed by a check, for as long as
+ *   - the last iteration's delta = max over interior sites of |F| (Section 3
+ *     and the convergence residual of Section 7.9, reading R6) is above tol,
+ *   - fewer than max_steps iterations have run since this launch began, and
+ *   - no error has been recorded in the state.
+ * The flow therefore stops at the first chunk boundary where delta <= tol,
+ * or at the first one at or after max_steps; read the result with
+ * skyrme_read_report.  Arguments as for skyrme_graph_create, plus tol >= 0
+ * (finite), max_steps >= 1 and chunk >= 1 (SKYRME_EINVAL otherwise).  The
+ * same stream-capture requirements apply. */
+skyrme_status skyrme_graph_create_until(const skyrme_lattice *lat, double dt, int mode, double tol,
+                                        long long max_steps, int chunk, skyrme_state *st,
+                                        void *stream, skyrme_graph **out);
+
 /* ---- batched flow (FP32) ----
  * Many independent lattices, of uneven sizes, advanced together: every step
  * is one persistent launch over all of their work (plus, in ARRESTED mode,

@@ -85,6 +85,10 @@ _SIGNATURES = {
     "skyrme_energy_static": (ctypes.c_int, [ctypes.POINTER(c_lattice), _P,
                                             ctypes.POINTER(ctypes.c_double), _P]),
     "skyrme_measure_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P]),
+    "skyrme_graph_create_until": (ctypes.c_int, [ctypes.POINTER(c_lattice), ctypes.c_double,
+                                                 ctypes.c_int, ctypes.c_double, ctypes.c_longlong,
+                                                 ctypes.c_int, ctypes.POINTER(c_state), _P,
+                                                 ctypes.POINTER(ctypes.c_void_p)]),
     "skyrme_batch_scratch_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.POINTER(c_lattice)]),
     "skyrme_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(c_lattice),
                                            ctypes.POINTER(c_state), ctypes.POINTER(ctypes.c_double),
@@ -354,10 +358,13 @@ def measure_fma_peak(kind: int, stream=None) -> float:
 class FlowGraph:
     """A captured CUDA graph of ``nsteps`` flow iterations (skyrme_graph_*).
     ``stream`` must be a capturable (non-default) torch stream.  Pass
-    ``batch`` instead of (lat, st, dt, mode) to capture batched iterations."""
+    ``batch`` instead of (lat, st, dt, mode) to capture batched iterations.
+    Pass ``until=(tol, max_steps)`` for a graph that repeats chunks of
+    ``nsteps`` iterations on the device until delta <= tol or max_steps
+    iterations have run (skyrme_graph_create_until)."""
 
     def __init__(self, lat: Lattice = None, st: State = None, dt: float = 0.0, nsteps: int = 1,
-                 mode: int = ARRESTED, stream=None, batch=None):
+                 mode: int = ARRESTED, stream=None, batch=None, until=None):
         torch = _torch()
         dev = st.device if st is not None else batch.states[0].device
         self.stream = stream if stream is not None else torch.cuda.Stream(dev)
@@ -367,6 +374,13 @@ class FlowGraph:
         if batch is not None:
             _check(load().skyrme_batch_graph_create(batch._h, self.nsteps, sp, ctypes.byref(h)),
                    "skyrme_batch_graph_create")
+        elif until is not None:
+            tol, max_steps = until
+            cl, cs = lat.c(), st.c()
+            _check(load().skyrme_graph_create_until(ctypes.byref(cl), float(dt), int(mode),
+                                                    float(tol), int(max_steps), self.nsteps,
+                                                    ctypes.byref(cs), sp, ctypes.byref(h)),
+                   "skyrme_graph_create_until")
         else:
             cl, cs = lat.c(), st.c()
             _check(load().skyrme_graph_create(ctypes.byref(cl), float(dt), self.nsteps, int(mode),
@@ -392,6 +406,21 @@ class FlowGraph:
 
 
 TILES = [(8, 32), (4, 32), (16, 16), (8, 16)]
+
+
+def flow_until(lat: Lattice, dt: float, mode: int, st: State, tol: float, max_steps: int,
+               chunk: int = 64, stream=None) -> dict:
+    """Relax the flow on the device until delta = max |F| <= tol (checked
+    every ``chunk`` iterations) or ``max_steps`` iterations have run: one
+    launch of a run-to-tolerance graph.  Returns the final report."""
+    torch = _torch()
+    g = FlowGraph(lat, st, dt, chunk, mode, stream=stream, until=(tol, max_steps))
+    try:
+        g.launch()
+        g.stream.synchronize()
+        return read_report(lat, st)
+    finally:
+        g.close()
 
 
 class Batch:

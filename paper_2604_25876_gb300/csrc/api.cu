@@ -313,6 +313,80 @@ skyrme_status skyrme_graph_create(const skyrme_lattice *lat, double dt, int nste
     return SKYRME_OK;
 }
 
+// The flow run to a tolerance: arm kernel, then WHILE { chunk iterations;
+// check kernel } captured into the node's body through a second stream.
+skyrme_status skyrme_graph_create_until(const skyrme_lattice *lat, double dt, int mode, double tol,
+                                        long long max_steps, int chunk, skyrme_state *st,
+                                        void *stream, skyrme_graph **out)
+{
+    if (!out) return SKYRME_EINVAL;
+    *out = nullptr;
+    skyrme_status rc = check_state(lat, st);
+    if (rc != SKYRME_OK) return rc;
+    if (!(dt > 0.0) || !isfinite(dt) || !mode_ok(mode) || !(tol >= 0.0) || !isfinite(tol) ||
+        max_steps < 1 || chunk < 1)
+        return SKYRME_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    FlowArgs a = make_args(*lat, *st, dt, mode);
+    cudaStream_t body = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&body, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "create body stream");
+    skyrme_graph *g = new skyrme_graph();
+    g->nsteps = 0;
+    e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(body);
+        delete g;
+        return cuda_fail(e, "begin stream capture");
+    }
+    rc = [&]() -> skyrme_status {
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t cg = nullptr;
+        CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg), "capture info");
+        cudaGraphConditionalHandle h;
+        CK(cudaGraphConditionalHandleCreate(&h, cg, 0, 0), "conditional handle");
+        CK(launch_until_arm(a.ctrl, h, s), "arm kernel");
+        const cudaGraphNode_t *deps = nullptr;
+        size_t ndeps = 0;
+        CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, &deps, nullptr, &ndeps), "capture info");
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cn;
+        CK(cudaGraphAddNode(&cn, cg, deps, nullptr, ndeps, &cp), "while node");
+        CK(cudaStreamUpdateCaptureDependencies(s, &cn, nullptr, 1, cudaStreamSetCaptureDependencies),
+           "capture dependencies");
+        CK(cudaStreamBeginCaptureToGraph(body, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal),
+           "begin body capture");
+        skyrme_status brc = launch_iterations(*lat, a, chunk, body);
+        if (brc == SKYRME_OK && launch_until_check(a.ctrl, h, tol, max_steps, body) != cudaSuccess)
+            brc = cuda_fail(cudaGetLastError(), "check kernel");
+        cudaGraph_t done = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(body, &done);
+        if (brc != SKYRME_OK) return brc;
+        CK(ee, "end body capture");
+        return SKYRME_OK;
+    }();
+    e = cudaStreamEndCapture(s, &g->graph);
+    cudaStreamDestroy(body);
+    if (rc != SKYRME_OK || e != cudaSuccess) {
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        return rc != SKYRME_OK ? rc : cuda_fail(e, "end stream capture");
+    }
+    e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g->graph);
+        delete g;
+        return cuda_fail(e, "instantiate graph");
+    }
+    *out = g;
+    return SKYRME_OK;
+}
+
 skyrme_status skyrme_graph_launch(skyrme_graph *g, void *stream)
 {
     if (!g || !g->exec) return SKYRME_EINVAL;

@@ -371,7 +371,41 @@ __global__ void k_reset_ctrl(Ctrl *c)
         c->edone = 0;
         c->hist = 0;
         for (int i = 0; i < 16; ++i) c->pht[i] = 1;  // weakly "no arrest"
+        c->until_start = 0;
     }
+}
+
+// Run-to-tolerance graphs: a WHILE node repeats a body of `chunk` iterations.
+// k_until_arm (in front of the node) records the step count and enters the
+// loop; k_until_check (last in the body) keeps it going while the last
+// iteration's delta = max |F| is above tol, fewer than max_steps iterations
+// have run since the launch began, and no error was recorded.
+__global__ void k_until_arm(Ctrl *c, cudaGraphConditionalHandle h)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        c->until_start = c->steps;
+        cudaGraphSetConditional(h, c->status == 0 ? 1u : 0u);
+    }
+}
+__global__ void k_until_check(Ctrl *c, cudaGraphConditionalHandle h, double tol, long long max_steps)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const bool more = c->status == 0 && !(c->last[6] <= tol) &&
+                          c->steps - c->until_start < max_steps;
+        cudaGraphSetConditional(h, more ? 1u : 0u);
+    }
+}
+
+cudaError_t launch_until_arm(void *ctrl, unsigned long long handle, cudaStream_t s)
+{
+    k_until_arm<<<1, 32, 0, s>>>(static_cast<Ctrl *>(ctrl), handle);
+    return cudaGetLastError();
+}
+cudaError_t launch_until_check(void *ctrl, unsigned long long handle, double tol,
+                               long long max_steps, cudaStream_t s)
+{
+    k_until_check<<<1, 32, 0, s>>>(static_cast<Ctrl *>(ctrl), handle, tol, max_steps);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------- launchers

@@ -68,7 +68,8 @@ struct Ctrl {
     int hist;             // last 4 arrest decisions (bit 0 = latest)
     int pad_i;
     unsigned char pht[16];  // 2-bit saturating counters indexed by hist
-    double pad[3];
+    long long until_start;  // steps when a run-to-tolerance graph launch began
+    double pad[2];
 };
 static_assert(sizeof(Ctrl) <= 512, "control block must fit its 512-byte slot");
 static_assert(offsetof(Ctrl, pht) % 16 == 0, "pht is read as one 16-byte word");

@@ -49,6 +49,9 @@ cudaError_t launch_forces(const skyrme_lattice &lat, const FlowArgs &a, void *fo
                           cudaStream_t s);
 cudaError_t launch_load_finish(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s);
 cudaError_t launch_reset_ctrl(void *ctrl, cudaStream_t s);
+cudaError_t launch_until_arm(void *ctrl, unsigned long long handle, cudaStream_t s);
+cudaError_t launch_until_check(void *ctrl, unsigned long long handle, double tol,
+                               long long max_steps, cudaStream_t s);
 
 // Seeds (init_fields.cu)
 cudaError_t launch_seed(const skyrme_lattice &lat, const skyrme_seed &seed, const FlowArgs &a,

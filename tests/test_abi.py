@@ -92,3 +92,21 @@ def test_fma_peak_rejects_bad_arguments_without_cuda():
     out = ctypes.c_double(0.0)
     assert lib.skyrme_measure_fma_peak(7, ctypes.byref(out), None) == 1
     assert lib.skyrme_measure_fma_peak(sk.PEAK_FP32, None, None) == 1
+
+
+def test_run_to_tolerance_graph_rejects_bad_arguments_without_cuda():
+    lib = sk.load()
+    lat = sk.Lattice((16, 16, 16), 0.2, 1.0, 32).c()
+    st = sk.c_state((ctypes.c_void_p * 2)(0x10000, 0x20000), (ctypes.c_void_p * 2)(0x30000, 0x40000),
+                    ctypes.c_void_p(0x50000), ctypes.c_size_t(1 << 30))
+    out = ctypes.c_void_p()
+    f = lib.skyrme_graph_create_until
+    assert f(ctypes.byref(lat), 0.01, 1, 1e-3, 100, 10, ctypes.byref(st), None, None) == 1
+    assert f(ctypes.byref(lat), 0.01, 1, -1.0, 100, 10, ctypes.byref(st), None, ctypes.byref(out)) == 1
+    assert f(ctypes.byref(lat), 0.01, 1, float("nan"), 100, 10, ctypes.byref(st), None,
+             ctypes.byref(out)) == 1
+    assert f(ctypes.byref(lat), 0.01, 1, 1e-3, 0, 10, ctypes.byref(st), None, ctypes.byref(out)) == 1
+    assert f(ctypes.byref(lat), 0.01, 1, 1e-3, 100, 0, ctypes.byref(st), None, ctypes.byref(out)) == 1
+    assert f(ctypes.byref(lat), 0.0, 1, 1e-3, 100, 10, ctypes.byref(st), None, ctypes.byref(out)) == 1
+    assert f(ctypes.byref(lat), 0.01, 9, 1e-3, 100, 10, ctypes.byref(st), None, ctypes.byref(out)) == 1
+    assert not out.value
