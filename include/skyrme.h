@@ -178,7 +178,7 @@ skyrme_status skyrme_graph_create_until(const skyrme_lattice *lat, double dt, in
  *     lattices with `trials` dry steps each (outputs go to the inactive
  *     buffers; the flows do not advance) and keeps the fastest.
  *   skyrme_batch_set_tile / skyrme_batch_tile: choose or query the tile
- *     shape (0: 8x32, 1: 4x32, 2: 16x16, 3: 8x16 interior sites per CTA) and
+ *     shape (0: 8x32, 1: 4x32, 2: 16x16, 3: 8x16, 4: 16x32 interior sites per CTA) and
  *     the persistent grid.
  *   skyrme_batch_graph_create: capture nsteps batched iterations as a
  *     skyrme_graph (launch and destroy it with skyrme_graph_launch /

@@ -405,7 +405,7 @@ class FlowGraph:
             pass
 
 
-TILES = [(8, 32), (4, 32), (16, 16), (8, 16)]
+TILES = [(8, 32), (4, 32), (16, 16), (8, 16), (16, 32)]
 
 
 def flow_until(lat: Lattice, dt: float, mode: int, st: State, tol: float, max_steps: int,
