@@ -52,6 +52,12 @@ class _Report(ctypes.Structure):
                 ("delta", ctypes.c_double), ("arrested", ctypes.c_int)]
 
 
+class _Observables(ctypes.Structure):
+    _fields_ = [("B", ctypes.c_double), ("X", ctypes.c_double * 3), ("R", ctypes.c_double),
+                ("Q", ctypes.c_double * 9), ("U", ctypes.c_double * 9), ("V", ctypes.c_double * 9),
+                ("W", ctypes.c_double * 9), ("D", ctypes.c_double), ("E", ctypes.c_double)]
+
+
 def _load():
     global _lib
     with _lock:
@@ -77,6 +83,7 @@ def _load():
             lib.orc_seed_product.argtypes = [I3, D, ctypes.c_int, P, P, D, ctypes.c_int, P]
             lib.orc_seed_noise.argtypes = [I3, D, D, D, ctypes.c_uint64, P]
             lib.orc_apply_vacuum_boundary.argtypes = [I3, P]
+            lib.orc_observables.argtypes = [I3, D, D, P, ctypes.POINTER(_Observables)]
             lib.orc_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
             lib.orc_splitmix64.restype = ctypes.c_uint64
             lib.orc_normal.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
@@ -129,6 +136,19 @@ def forces(phi: np.ndarray, h: float, m: float):
     G, F, dens = (np.zeros_like(phi) for _ in range(3))
     lib.orc_forces(_dims(phi.shape[:3]), h, m, _ptr(phi), _ptr(G), _ptr(F), _ptr(dens))
     return G, F, dens
+
+
+def observables(phi: np.ndarray, h: float, m: float) -> dict:
+    """Section 5 observables of a static field (see orc_observables):
+    B, centre of mass X, RMS radius R, quadrupole Q, inertia tensors U, V, W
+    (3x3 arrays; W[i, j] with i isospin and j space), D-term D and energy E."""
+    lib = _load()
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    o = _Observables()
+    lib.orc_observables(_dims(phi.shape[:3]), h, m, _ptr(phi), ctypes.byref(o))
+    mat = lambda a: np.array(list(a)).reshape(3, 3)
+    return {"B": o.B, "X": np.array(list(o.X)), "R": o.R, "Q": mat(o.Q), "U": mat(o.U),
+            "V": mat(o.V), "W": mat(o.W), "D": o.D, "E": o.E}
 
 
 def energy(phi: np.ndarray, h: float, m: float) -> dict:

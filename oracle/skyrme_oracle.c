@@ -709,3 +709,256 @@ void orc_seed_noise(const int n[3], double h, double radius, double sigma,
     free(a);
     free(b);
 }
+
+/* ------------------------------------------------------------------------
+ * Section 5: physical properties of a static configuration
+ *
+ * Written in the paper's su(2) notation: U = phi^0 1 + i phi^a tau^a as a
+ * 2x2 complex matrix, the left currents L_k = U^dagger d_k U (Eq. "Stress
+ * tensor"), the isospin currents T_j = (i/2) U^dagger [tau^j, U], and traces
+ * of explicit 2x2 products.  r = x - X_c with X_c of Eq. "CoM".
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    cplx a[2][2];
+} mat2;
+
+static mat2 m2_zero(void)
+{
+    mat2 r;
+    memset(&r, 0, sizeof(r));
+    return r;
+}
+
+static mat2 m2_mul(mat2 p, mat2 q)
+{
+    mat2 r = m2_zero();
+    int i, j, k;
+    for (i = 0; i < 2; i++)
+        for (j = 0; j < 2; j++)
+            for (k = 0; k < 2; k++) r.a[i][j] = cadd(r.a[i][j], cmul(p.a[i][k], q.a[k][j]));
+    return r;
+}
+
+static mat2 m2_lin(double s, mat2 p, double t, mat2 q) /* s p + t q */
+{
+    mat2 r;
+    int i, j;
+    for (i = 0; i < 2; i++)
+        for (j = 0; j < 2; j++) {
+            r.a[i][j].re = s * p.a[i][j].re + t * q.a[i][j].re;
+            r.a[i][j].im = s * p.a[i][j].im + t * q.a[i][j].im;
+        }
+    return r;
+}
+
+static mat2 m2_adjoint(mat2 p)
+{
+    mat2 r;
+    int i, j;
+    for (i = 0; i < 2; i++)
+        for (j = 0; j < 2; j++) {
+            r.a[i][j].re = p.a[j][i].re;
+            r.a[i][j].im = -p.a[j][i].im;
+        }
+    return r;
+}
+
+static mat2 m2_times_i(mat2 p) /* i p */
+{
+    mat2 r;
+    int i, j;
+    for (i = 0; i < 2; i++)
+        for (j = 0; j < 2; j++) {
+            r.a[i][j].re = -p.a[i][j].im;
+            r.a[i][j].im = p.a[i][j].re;
+        }
+    return r;
+}
+
+static mat2 m2_commutator(mat2 p, mat2 q) { return m2_lin(1.0, m2_mul(p, q), -1.0, m2_mul(q, p)); }
+
+static double m2_retrace(mat2 p) { return p.a[0][0].re + p.a[1][1].re; }
+
+/* Pauli matrices tau^1, tau^2, tau^3 */
+static mat2 pauli(int a)
+{
+    mat2 r = m2_zero();
+    if (a == 0) {
+        r.a[0][1].re = 1.0;
+        r.a[1][0].re = 1.0;
+    } else if (a == 1) {
+        r.a[0][1].im = -1.0;
+        r.a[1][0].im = 1.0;
+    } else {
+        r.a[0][0].re = 1.0;
+        r.a[1][1].re = -1.0;
+    }
+    return r;
+}
+
+/* q^0 1 + i q^a tau^a for a real 4-vector q */
+static mat2 quaternion_matrix(const double q[4])
+{
+    mat2 r = m2_zero();
+    int a;
+    r.a[0][0].re = q[0];
+    r.a[1][1].re = q[0];
+    for (a = 0; a < 3; a++) r = m2_lin(1.0, r, q[a + 1], m2_times_i(pauli(a)));
+    return r;
+}
+
+static int levi3(int i, int j, int k)
+{
+    if (i == j || j == k || i == k) return 0;
+    return ((i == 0 && j == 1) || (i == 1 && j == 2) || (i == 2 && j == 0)) ? 1 : -1;
+}
+
+/* sums of one x-plane: pass 0 {b, x b, y b, z b}; pass 1 everything else */
+enum { OBS_B = 0, OBS_XB = 1, OBS_E = 4, OBS_R2B = 5, OBS_Q = 6, OBS_U = 15, OBS_V = 24,
+       OBS_W = 33, OBS_D = 42, OBS_N = 43 };
+
+static void observables_plane(const int n[3], double h, double m, const double *phi, int x,
+                              int pass, const double X[3], nsum *acc)
+{
+    int y, z, i, j, k, l, mm, nn, p, a;
+    mat2 tau[3];
+    for (a = 0; a < 3; a++) tau[a] = pauli(a);
+    for (y = 2; y <= n[1] - 3; y++)
+        for (z = 2; z <= n[2] - 3; z++) {
+            double d1[3][4], d2[3][4], dm[3][4], g[4], f[4], dens[4], xv[3], r[3], r2;
+            size_t s = site_index(n, x, y, z);
+            const double *ph = &phi[4 * s];
+            orc_site_derivatives(n, h, phi, x, y, z, d1, d2, dm);
+            orc_site_terms(ph, d1, d2, dm, m, g, f, dens);
+            xv[0] = coord(n, h, 0, x);
+            xv[1] = coord(n, h, 1, y);
+            xv[2] = coord(n, h, 2, z);
+            if (pass == 0) {
+                nsum_add(&acc[OBS_B], dens[3]);
+                for (i = 0; i < 3; i++) nsum_add(&acc[OBS_XB + i], xv[i] * dens[3]);
+                continue;
+            }
+            r2 = 0.0;
+            for (i = 0; i < 3; i++) {
+                r[i] = xv[i] - X[i];
+                r2 += r[i] * r[i];
+            }
+            {
+                mat2 U = quaternion_matrix(ph), Ud = m2_adjoint(U), L[3], T[3];
+                double Tij[3][3], Tkk, lag, tr_ll = 0.0, tr_cc = 0.0;
+                /* L_k is su(2)-valued; the lattice derivative of phi has a small
+                 * component along phi, which shows up as a multiple of the
+                 * identity in U^dagger d_k U: keep its traceless part */
+                for (k = 0; k < 3; k++) {
+                    mat2 full = m2_mul(Ud, quaternion_matrix(d1[k]));
+                    const double half_tr = 0.5 * m2_retrace(full);
+                    full.a[0][0].re -= half_tr;
+                    full.a[1][1].re -= half_tr;
+                    L[k] = full;
+                }
+                for (j = 0; j < 3; j++)
+                    T[j] = m2_lin(0.5, m2_times_i(m2_mul(Ud, m2_commutator(tau[j], U))), 0.0, U);
+                /* static Lagrangian density: (1/2) Tr(L_k L_k) + (1/16) Tr([L_i,L_j]^2) - m^2 Tr(1 - U) */
+                for (k = 0; k < 3; k++) tr_ll += m2_retrace(m2_mul(L[k], L[k]));
+                for (i = 0; i < 3; i++)
+                    for (j = 0; j < 3; j++) {
+                        mat2 c = m2_commutator(L[i], L[j]);
+                        tr_cc += m2_retrace(m2_mul(c, c));
+                    }
+                lag = 0.5 * tr_ll + tr_cc / 16.0 - m * m * (2.0 - m2_retrace(U));
+                /* Eq. "Stress tensor", spatial static part */
+                for (i = 0; i < 3; i++)
+                    for (j = 0; j < 3; j++) {
+                        double t = -m2_retrace(m2_mul(L[i], L[j]));
+                        for (k = 0; k < 3; k++)
+                            t -= 0.25 * m2_retrace(m2_mul(m2_commutator(L[i], L[k]),
+                                                          m2_commutator(L[j], L[k])));
+                        Tij[i][j] = t + (i == j ? lag : 0.0);
+                    }
+                Tkk = Tij[0][0] + Tij[1][1] + Tij[2][2];
+                nsum_add(&acc[OBS_E], dens[0] + dens[1] + dens[2]);
+                nsum_add(&acc[OBS_R2B], r2 * dens[3]);
+                /* Eq. "Q tensor" with rho = B0 / 2 */
+                for (i = 0; i < 3; i++)
+                    for (j = 0; j < 3; j++)
+                        nsum_add(&acc[OBS_Q + 3 * i + j],
+                                 (3.0 * r[i] * r[j] - (i == j ? r2 : 0.0)) * 0.5 * dens[3]);
+                /* Eqs. "U inertia tensor", "V inertia tensor", "W inertia tensor" */
+                for (i = 0; i < 3; i++)
+                    for (j = 0; j < 3; j++) {
+                        double u = m2_retrace(m2_mul(T[i], T[j])), v = 0.0, w = 0.0;
+                        for (k = 0; k < 3; k++)
+                            u += 0.25 * m2_retrace(m2_mul(m2_commutator(L[k], T[i]),
+                                                          m2_commutator(L[k], T[j])));
+                        for (l = 0; l < 3; l++)
+                            for (mm = 0; mm < 3; mm++)
+                                for (nn = 0; nn < 3; nn++)
+                                    for (p = 0; p < 3; p++) {
+                                        double e = (double)(levi3(i, l, mm) * levi3(j, nn, p));
+                                        double t;
+                                        if (e == 0.0) continue;
+                                        t = m2_retrace(m2_mul(L[mm], L[p]));
+                                        for (k = 0; k < 3; k++)
+                                            t += 0.25 * m2_retrace(m2_mul(m2_commutator(L[k], L[mm]),
+                                                                          m2_commutator(L[k], L[p])));
+                                        v += e * r[l] * r[nn] * t;
+                                    }
+                        for (l = 0; l < 3; l++)
+                            for (mm = 0; mm < 3; mm++) {
+                                double e = (double)levi3(j, l, mm), t;
+                                if (e == 0.0) continue;
+                                t = m2_retrace(m2_mul(T[i], L[mm]));
+                                for (k = 0; k < 3; k++)
+                                    t += 0.25 * m2_retrace(m2_mul(m2_commutator(L[k], T[i]),
+                                                                  m2_commutator(L[k], L[mm])));
+                                w += e * r[l] * t;
+                            }
+                        nsum_add(&acc[OBS_U + 3 * i + j], -u);
+                        nsum_add(&acc[OBS_V + 3 * i + j], -v);
+                        nsum_add(&acc[OBS_W + 3 * i + j], w);
+                    }
+                /* Eq. "D-term" integrand */
+                {
+                    double q = 0.0;
+                    for (i = 0; i < 3; i++)
+                        for (j = 0; j < 3; j++) q += r[i] * r[j] * Tij[i][j];
+                    nsum_add(&acc[OBS_D], q - r2 * Tkk / 3.0);
+                }
+            }
+        }
+}
+
+void orc_observables(const int n[3], double h, double m, const double *phi, orc_observables_t *out)
+{
+    int x, q, i, j;
+    const int nx = n[0];
+    const double h3 = h * h * h;
+    double X[3] = {0.0, 0.0, 0.0}, tot[OBS_N];
+    nsum *acc = (nsum *)calloc((size_t)nx * OBS_N, sizeof(nsum));
+    int pass;
+    for (pass = 0; pass < 2; pass++) {
+        nsum sum[OBS_N];
+        memset(acc, 0, (size_t)nx * OBS_N * sizeof(nsum));
+#pragma omp parallel for schedule(dynamic, 1)
+        for (x = 2; x <= nx - 3; x++) observables_plane(n, h, m, phi, x, pass, X, &acc[(size_t)x * OBS_N]);
+        memset(sum, 0, sizeof(sum));
+        for (x = 2; x <= nx - 3; x++)
+            for (q = 0; q < OBS_N; q++) nsum_add(&sum[q], nsum_get(&acc[(size_t)x * OBS_N + q]));
+        for (q = 0; q < OBS_N; q++) tot[q] = h3 * nsum_get(&sum[q]);
+        if (pass == 0) {
+            out->B = tot[OBS_B];
+            for (i = 0; i < 3; i++) X[i] = out->X[i] = tot[OBS_XB + i] / tot[OBS_B];
+        }
+    }
+    out->E = tot[OBS_E];
+    out->R = sqrt(tot[OBS_R2B] / out->B);
+    for (i = 0; i < 3; i++)
+        for (j = 0; j < 3; j++) {
+            out->Q[i][j] = tot[OBS_Q + 3 * i + j];
+            out->U[i][j] = tot[OBS_U + 3 * i + j];
+            out->V[i][j] = tot[OBS_V + 3 * i + j];
+            out->W[i][j] = tot[OBS_W + 3 * i + j];
+        }
+    out->D = -2.0 * out->E / 5.0 * tot[OBS_D];
+    free(acc);
+}

@@ -53,6 +53,22 @@ void orc_forces(const int n[3], double h, double m, const double *phi,
 void orc_energy(const int n[3], double h, double m, const double *phi,
                 double out[6]);
 
+/* Section 5 observables of a static field (h^3 times sums over interior
+ * sites; r = x - X_c):
+ *   B        baryon number (Eq. "B0_components" summed);
+ *   X[3]     centre of mass, Eq. "CoM";
+ *   R        RMS radius, Eq. "RMS radius";
+ *   Q        quadrupole, Eq. "Q tensor" with rho = B0 / 2;
+ *   U, V, W  isospin, spin and mixed inertia tensors, Eqs. "U/V/W inertia
+ *            tensor" (W[i][j]: i isospin, j space);
+ *   D        monopole D-term, Eq. "D-term", with E the static energy;
+ *   E        static energy (Eq. "SkyrmeEnergy_phi" summed). */
+typedef struct {
+    double B, X[3], R, Q[3][3], U[3][3], V[3][3], W[3][3], D, E;
+} orc_observables_t;
+void orc_observables(const int n[3], double h, double m, const double *phi,
+                     orc_observables_t *out);
+
 typedef struct {
     double E, E2, E4, E0, B, virial; /* of the field at the start of the step */
     double delta;                    /* max over interior sites of |F|      */
