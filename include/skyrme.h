@@ -211,6 +211,27 @@ skyrme_status skyrme_baryon_number(const skyrme_lattice *lat, skyrme_state *st, 
 skyrme_status skyrme_virial(const skyrme_lattice *lat, skyrme_state *st, double *V,
                             void *stream);
 
+/* ---- Section 5 observables of the current field ----
+ * skyrme_observables: h^3-weighted sums over interior sites of
+ *   B        the baryon number (Eq. "B0_components");
+ *   X        the centre of mass, Eq. "CoM" (x_i = (i - (n_i - 1)/2) h);
+ *   R        the RMS radius, Eq. "RMS radius", about X;
+ *   Q        the quadrupole tensor, Eq. "Q tensor", with rho = B0/2;
+ *   U, V, W  the isospin, spin and mixed inertia tensors, Eqs. "U/V/W
+ *            inertia tensor" (W[i][j]: i isospin, j space); the lattice
+ *            current L_k is the traceless part of U^dagger d_k U;
+ *   D        the monopole D-term, Eq. "D-term", about X;
+ *   E        the static energy used by D (Eq. "SkyrmeEnergy_phi").
+ * All moments are taken about X.  Two passes over the field in FP64 (whatever
+ * its precision), in a fixed order; uses the state's scratch; synchronises
+ * `stream`.  SKYRME_EINVAL when B is 0 (no centre of mass), SKYRME_ENONFINITE
+ * when a sum is not finite; `out` is zeroed in both cases. */
+typedef struct {
+    double B, X[3], R, Q[3][3], U[3][3], V[3][3], W[3][3], D, E;
+} skyrme_observables_t;
+skyrme_status skyrme_observables(const skyrme_lattice *lat, skyrme_state *st,
+                                 skyrme_observables_t *out, void *stream);
+
 /* ---- per-site values of the current field (asynchronous) ----
  * force (device, nullable): F at interior sites, 0 on the boundary layers,
  * same site layout and precision as phi.  dens (device, nullable): per site

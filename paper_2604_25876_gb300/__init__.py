@@ -24,6 +24,12 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "buffer too small", 3: "CUDA error"
           4: "non-finite value", 5: "device wait timed out", 6: "unsupported"}
 
 
+class c_observables(ctypes.Structure):
+    _fields_ = [("B", ctypes.c_double), ("X", ctypes.c_double * 3), ("R", ctypes.c_double),
+                ("Q", ctypes.c_double * 9), ("U", ctypes.c_double * 9), ("V", ctypes.c_double * 9),
+                ("W", ctypes.c_double * 9), ("D", ctypes.c_double), ("E", ctypes.c_double)]
+
+
 class SkyrmeError(RuntimeError):
     def __init__(self, status: int, where: str, detail: str = ""):
         self.status = status
@@ -85,6 +91,8 @@ _SIGNATURES = {
     "skyrme_energy_static": (ctypes.c_int, [ctypes.POINTER(c_lattice), _P,
                                             ctypes.POINTER(ctypes.c_double), _P]),
     "skyrme_measure_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P]),
+    "skyrme_observables": (ctypes.c_int, [ctypes.POINTER(c_lattice), ctypes.POINTER(c_state),
+                                          ctypes.POINTER(c_observables), _P]),
     "skyrme_graph_create_until": (ctypes.c_int, [ctypes.POINTER(c_lattice), ctypes.c_double,
                                                  ctypes.c_int, ctypes.c_double, ctypes.c_longlong,
                                                  ctypes.c_int, ctypes.POINTER(c_state), _P,
@@ -328,6 +336,19 @@ def virial(lat: Lattice, st: State, stream=None) -> float:
     _check(load().skyrme_virial(ctypes.byref(cl), ctypes.byref(cs), ctypes.byref(out),
                                 _stream_ptr(stream, st.device)), "skyrme_virial")
     return out.value
+
+
+def observables(lat: Lattice, st: State, stream=None) -> dict:
+    """Section 5 observables of the current field (skyrme_observables): B,
+    centre of mass X, RMS radius R, quadrupole Q, inertia tensors U, V, W
+    (3x3 lists; W[i][j] with i isospin, j space), D-term D and energy E."""
+    o = c_observables()
+    cl, cs = lat.c(), st.c()
+    _check(load().skyrme_observables(ctypes.byref(cl), ctypes.byref(cs), ctypes.byref(o),
+                                     _stream_ptr(stream, st.device)), "skyrme_observables")
+    mat = lambda a: [list(a[0:3]), list(a[3:6]), list(a[6:9])]
+    return {"B": o.B, "X": list(o.X), "R": o.R, "Q": mat(o.Q), "U": mat(o.U), "V": mat(o.V),
+            "W": mat(o.W), "D": o.D, "E": o.E}
 
 
 def forces(lat: Lattice, st: State, want_dens: bool = True, stream=None):

@@ -452,6 +452,18 @@ skyrme_status skyrme_virial(const skyrme_lattice *lat, skyrme_state *st, double 
     return rc;
 }
 
+skyrme_status skyrme_observables(const skyrme_lattice *lat, skyrme_state *st,
+                                 skyrme_observables_t *out, void *stream)
+{
+    skyrme_status rc = check_state(lat, st);
+    if (rc != SKYRME_OK) return rc;
+    if (!out) return SKYRME_EINVAL;
+    const ScratchLayout L = scratch_layout(*lat);
+    if (L.total - L.energy_off < observables_parts_bytes()) return SKYRME_ENOMEM;
+    FlowArgs a = make_args(*lat, *st, 0.0, MODE_ARRESTED);
+    return compute_observables(*lat, a, out, static_cast<cudaStream_t>(stream));
+}
+
 skyrme_status skyrme_forces(const skyrme_lattice *lat, skyrme_state *st, void *force, void *dens,
                             void *stream)
 {

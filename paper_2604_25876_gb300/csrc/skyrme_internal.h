@@ -53,6 +53,11 @@ cudaError_t launch_until_arm(void *ctrl, unsigned long long handle, cudaStream_t
 cudaError_t launch_until_check(void *ctrl, unsigned long long handle, double tol,
                                long long max_steps, cudaStream_t s);
 
+// Section 5 observables (observables.cu)
+skyrme_status compute_observables(const skyrme_lattice &lat, const FlowArgs &a,
+                                  skyrme_observables_t *out, cudaStream_t s);
+size_t observables_parts_bytes();
+
 // Seeds (init_fields.cu)
 cudaError_t launch_seed(const skyrme_lattice &lat, const skyrme_seed &seed, const FlowArgs &a,
                         cudaStream_t s);

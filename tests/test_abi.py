@@ -110,3 +110,12 @@ def test_run_to_tolerance_graph_rejects_bad_arguments_without_cuda():
     assert f(ctypes.byref(lat), 0.0, 1, 1e-3, 100, 10, ctypes.byref(st), None, ctypes.byref(out)) == 1
     assert f(ctypes.byref(lat), 0.01, 9, 1e-3, 100, 10, ctypes.byref(st), None, ctypes.byref(out)) == 1
     assert not out.value
+
+
+def test_observables_rejects_bad_arguments_without_cuda():
+    lib = sk.load()
+    lat = sk.Lattice((16, 16, 16), 0.2, 1.0, 64).c()
+    st = sk.c_state((ctypes.c_void_p * 2)(0x10000, 0x20000), (ctypes.c_void_p * 2)(0x30000, 0x40000),
+                    ctypes.c_void_p(0x50000), ctypes.c_size_t(1 << 30))
+    assert lib.skyrme_observables(ctypes.byref(lat), ctypes.byref(st), None, None) == 1
+    assert lib.skyrme_observables(ctypes.byref(lat), None, ctypes.byref(sk.c_observables()), None) == 1
