@@ -58,6 +58,12 @@ class _Observables(ctypes.Structure):
                 ("W", ctypes.c_double * 9), ("D", ctypes.c_double), ("E", ctypes.c_double)]
 
 
+class _RenderParams(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("view", ctypes.c_double * 9),
+                ("levelset", ctypes.c_double), ("transfer_scale", ctypes.c_double),
+                ("brightness", ctypes.c_double), ("step", ctypes.c_double)]
+
+
 def _load():
     global _lib
     with _lock:
@@ -84,6 +90,9 @@ def _load():
             lib.orc_seed_noise.argtypes = [I3, D, D, D, ctypes.c_uint64, P]
             lib.orc_apply_vacuum_boundary.argtypes = [I3, P]
             lib.orc_observables.argtypes = [I3, D, D, P, ctypes.POINTER(_Observables)]
+            lib.orc_render_volume_from_field.argtypes = [I3, D, P, P]
+            lib.orc_render_volume.argtypes = [I3, P, ctypes.POINTER(_RenderParams), P]
+            lib.orc_render_sample.argtypes = [I3, P, P, P]
             lib.orc_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
             lib.orc_splitmix64.restype = ctypes.c_uint64
             lib.orc_normal.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
@@ -149,6 +158,37 @@ def observables(phi: np.ndarray, h: float, m: float) -> dict:
     mat = lambda a: np.array(list(a)).reshape(3, 3)
     return {"B": o.B, "X": np.array(list(o.X)), "R": o.R, "Q": mat(o.Q), "U": mat(o.U),
             "V": mat(o.V), "W": mat(o.W), "D": o.D, "E": o.E}
+
+
+def render_volume_from_field(phi: np.ndarray, h: float) -> np.ndarray:
+    """(n0, n1, n2, 4) volume {B0 / max B0, unit pions} (orc_render_volume_from_field)."""
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    vol = np.zeros_like(phi)
+    _load().orc_render_volume_from_field(_dims(phi.shape[:3]), h, _ptr(phi), _ptr(vol))
+    return vol
+
+
+def render_volume(vol: np.ndarray, width: int, height: int, view=None, levelset: float = 0.2,
+                  transfer_scale: float = 4.0, brightness: float = 1.0,
+                  step: float = 0.01) -> np.ndarray:
+    """(height, width, 4) RGBA image of a volume (orc_render_volume)."""
+    vol = np.ascontiguousarray(vol, dtype=np.float64)
+    rp = _RenderParams(int(width), int(height),
+                       (ctypes.c_double * 9)(*np.asarray(view if view is not None else np.eye(3),
+                                                         dtype=np.float64).ravel()),
+                       levelset, transfer_scale, brightness, step)
+    out = np.zeros((int(height), int(width), 4))
+    _load().orc_render_volume(_dims(vol.shape[:3]), _ptr(vol), ctypes.byref(rp), _ptr(out))
+    return out
+
+
+def render_sample(vol: np.ndarray, g) -> np.ndarray:
+    """Trilinear sample of the volume at lattice coordinates g (orc_render_sample)."""
+    vol = np.ascontiguousarray(vol, dtype=np.float64)
+    gg = np.ascontiguousarray(g, dtype=np.float64)
+    out = np.zeros(4)
+    _load().orc_render_sample(_dims(vol.shape[:3]), _ptr(vol), _ptr(gg), _ptr(out))
+    return out
 
 
 def energy(phi: np.ndarray, h: float, m: float) -> dict:

@@ -962,3 +962,136 @@ void orc_observables(const int n[3], double h, double m, const double *phi, orc_
     out->D = -2.0 * out->E / 5.0 * tot[OBS_D];
     free(acc);
 }
+
+/* ------------------------------------------------------------------------
+ * Section 6.2 (ray tracing): a headless volume render of the baryon density
+ *
+ * The volume holds, per site, {B0 / max B0, unit pion vector} (zero pions where
+ * the pion vector vanishes); B0 is the flow's baryon density at interior
+ * sites and 0 on the boundary layers.  Rays (perspective camera, fixed step)
+ * sample it by trilinear interpolation; the transfer function and the
+ * front-to-back compositing are those the paper states.  Readings are in the
+ * header file.
+ * ------------------------------------------------------------------------ */
+void orc_render_volume_from_field(const int n[3], double h, const double *phi, double *vol)
+{
+    size_t total = (size_t)n[0] * n[1] * n[2], s;
+    double bmax = 0.0;
+    int x;
+    double *b = (double *)calloc(total, sizeof(double));
+#pragma omp parallel for schedule(static)
+    for (x = 2; x <= n[0] - 3; x++) {
+        int y, z;
+        for (y = 2; y <= n[1] - 3; y++)
+            for (z = 2; z <= n[2] - 3; z++) {
+                double d1[3][4], d2[3][4], dm[3][4], g[4], f[4], dens[4];
+                size_t i = site_index(n, x, y, z);
+                orc_site_derivatives(n, h, phi, x, y, z, d1, d2, dm);
+                orc_site_terms(&phi[4 * i], d1, d2, dm, 0.0, g, f, dens);
+                b[i] = dens[3];
+            }
+    }
+    for (s = 0; s < total; s++)
+        if (b[s] > bmax) bmax = b[s];
+    for (s = 0; s < total; s++) {
+        const double *p = &phi[4 * s];
+        const double np = sqrt(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
+        int a;
+        vol[4 * s] = bmax > 0.0 ? b[s] / bmax : 0.0;
+        for (a = 1; a < 4; a++) vol[4 * s + a] = np > 0.0 ? p[a] / np : 0.0;
+    }
+    free(b);
+}
+
+/* trilinear interpolation of the 4-component volume at lattice coordinates g */
+void orc_render_sample(const int n[3], const double *vol, const double g[3], double out[4])
+{
+    int i0[3], c, a;
+    double w[3];
+    for (a = 0; a < 3; a++) {
+        double t = g[a];
+        if (t < 0.0) t = 0.0;
+        if (t > (double)(n[a] - 1)) t = (double)(n[a] - 1);
+        i0[a] = (int)floor(t);
+        if (i0[a] > n[a] - 2) i0[a] = n[a] - 2;
+        w[a] = t - (double)i0[a];
+    }
+    for (c = 0; c < 4; c++) out[c] = 0.0;
+    for (a = 0; a < 8; a++) {
+        const int dx = a & 1, dy = (a >> 1) & 1, dz = (a >> 2) & 1;
+        const double wt = (dx ? w[0] : 1.0 - w[0]) * (dy ? w[1] : 1.0 - w[1]) * (dz ? w[2] : 1.0 - w[2]);
+        const double *v = &vol[4 * site_index(n, i0[0] + dx, i0[1] + dy, i0[2] + dz)];
+        for (c = 0; c < 4; c++) out[c] += wt * v[c];
+    }
+}
+
+void orc_render_volume(const int n[3], const double *vol, const orc_render_params *rp,
+                       double *rgba)
+{
+    double half[3], s = 0.0;
+    int a, px;
+    for (a = 0; a < 3; a++) {
+        half[a] = 0.5 * (double)(n[a] - 1);
+        if (half[a] > s) s = half[a];
+    }
+#pragma omp parallel for schedule(dynamic, 4)
+    for (px = 0; px < rp->width * rp->height; px++) {
+        const int ix = px % rp->width, iy = px / rp->width;
+        const double aspect = (double)rp->width / (double)rp->height;
+        const double u = (2.0 * (ix + 0.5) / rp->width - 1.0) * aspect;
+        const double v = 2.0 * (iy + 0.5) / rp->height - 1.0;
+        double dv[3] = {u, v, -ORC_RENDER_FOCAL}, ov[3] = {0.0, 0.0, ORC_RENDER_EYE};
+        double o[3], d[3], nd = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+        double tnear = -1e300, tfar = 1e300, sum[4] = {0.0, 0.0, 0.0, 0.0}, t;
+        int i, j, c;
+        for (i = 0; i < 3; i++) dv[i] /= nd;
+        /* view space -> box space: o = R ov, d = R dv (R row-major) */
+        for (i = 0; i < 3; i++) {
+            o[i] = 0.0;
+            d[i] = 0.0;
+            for (j = 0; j < 3; j++) {
+                o[i] += rp->view[3 * i + j] * ov[j];
+                d[i] += rp->view[3 * i + j] * dv[j];
+            }
+        }
+        /* slab intersection with the box |p_i| <= half_i / s */
+        for (i = 0; i < 3; i++) {
+            const double b = half[i] / s;
+            if (d[i] != 0.0) {
+                double t0 = (-b - o[i]) / d[i], t1 = (b - o[i]) / d[i];
+                if (t0 > t1) {
+                    const double tmp = t0;
+                    t0 = t1;
+                    t1 = tmp;
+                }
+                if (t0 > tnear) tnear = t0;
+                if (t1 < tfar) tfar = t1;
+            } else if (o[i] < -b || o[i] > b) {
+                tnear = 1.0;
+                tfar = 0.0;
+            }
+        }
+        if (tnear < 0.0) tnear = 0.0;
+        for (t = tnear; t <= tfar; t += rp->step) {
+            double p[3], g[3], smp[4], input, col[4];
+            for (i = 0; i < 3; i++) {
+                p[i] = o[i] + t * d[i];
+                g[i] = p[i] * s + half[i];
+            }
+            orc_render_sample(n, vol, g, smp);
+            input = (smp[0] - rp->levelset) * rp->transfer_scale;
+            if (input < 0.0) continue; /* rejected */
+            /* colour = input^2 (pion_1, pion_2, pion_3, 1 / input) */
+            col[0] = input * input * smp[1];
+            col[1] = input * input * smp[2];
+            col[2] = input * input * smp[3];
+            col[3] = input;
+            for (c = 0; c < 4; c++) sum[c] += col[c] * (1.0 - sum[3]);
+            if (sum[3] > ORC_RENDER_ALPHA_STOP) break;
+        }
+        for (c = 0; c < 4; c++) {
+            double val = sum[c] * rp->brightness;
+            rgba[4 * (size_t)px + c] = val < 0.0 ? 0.0 : (val > 1.0 ? 1.0 : val);
+        }
+    }
+}

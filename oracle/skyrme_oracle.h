@@ -69,6 +69,39 @@ typedef struct {
 void orc_observables(const int n[3], double h, double m, const double *phi,
                      orc_observables_t *out);
 
+/* Section 6.2 (ray tracing), headless.
+ *   orc_render_volume_from_field: vol (4 doubles per site) = {B0 / max B0,
+ *     pion / |pion|}, B0 the flow's baryon density (0 on the boundary layers,
+ *     and the first component 0 everywhere when max B0 <= 0).
+ *   orc_render_volume: one RGBA (4 doubles, each in [0, 1]) per pixel, row by
+ *     row from the bottom (y up).  Readings where the paper is silent:
+ *     - the box: lattice coordinates g map to box coordinates (g - (n-1)/2)/s,
+ *       s the largest (n_i - 1)/2, so the longest axis spans [-1, 1];
+ *     - the camera: eye at (0, 0, ORC_RENDER_EYE) in view space, pixel (u, v)
+ *       in [-aspect, aspect] x [-1, 1] looking along (u, v, -ORC_RENDER_FOCAL);
+ *       view is the row-major rotation taking view-space vectors to box space;
+ *     - samples at t = t_near + k step along the unit ray inside the box,
+ *       trilinear interpolation of all four volume components (clamped to the
+ *       lattice);
+ *     - input = (b - levelset) * transfer_scale, skipped when negative;
+ *       colour = input^2 (pion_1, pion_2, pion_3, 1/input);
+ *     - front-to-back compositing: sum += colour (1 - sum_alpha), stopped
+ *       once sum_alpha > ORC_RENDER_ALPHA_STOP;
+ *     - the result times brightness, each component clamped to [0, 1]. */
+#define ORC_RENDER_EYE 4.0
+#define ORC_RENDER_FOCAL 2.0
+#define ORC_RENDER_ALPHA_STOP 0.95
+typedef struct {
+    int width, height;
+    double view[9];
+    double levelset, transfer_scale, brightness, step;
+} orc_render_params;
+void orc_render_volume_from_field(const int n[3], double h, const double *phi, double *vol);
+void orc_render_volume(const int n[3], const double *vol, const orc_render_params *rp,
+                       double *rgba);
+/* the trilinear sample of the volume at lattice coordinates g (clamped) */
+void orc_render_sample(const int n[3], const double *vol, const double g[3], double out[4]);
+
 typedef struct {
     double E, E2, E4, E0, B, virial; /* of the field at the start of the step */
     double delta;                    /* max over interior sites of |F|      */
