@@ -232,6 +232,57 @@ typedef struct {
 skyrme_status skyrme_observables(const skyrme_lattice *lat, skyrme_state *st,
                                  skyrme_observables_t *out, void *stream);
 
+/* ---- headless volume render of the baryon density (Section 6.2) ----
+ * The paper ray-traces B0 in an OpenGL viewer; here the picture is written to
+ * a caller-owned device RGBA buffer (one float4 per pixel, each channel in
+ * [0, 1], rows from the bottom of the image, y up).
+ *
+ * skyrme_render_volume: the volume of the current field, one record of four
+ *   doubles per site in the field's site order: {B0 / max B0, pion / |pion|}.
+ *   B0 is the lattice baryon density of Eq. "B0_components" at interior
+ *   sites and 0 on the two boundary layers; max B0 is taken over the lattice,
+ *   and B0 / max B0 is 0 everywhere when max B0 <= 0.  The pion unit vector
+ *   (phi_1, phi_2, phi_3) / |pion| is 0 where the pion is 0.  `vol` is a
+ *   device buffer of at least skyrme_render_volume_bytes(lat) bytes, 32-byte
+ *   aligned, owned by the caller.  Uses the state's scratch; asynchronous.
+ *
+ * skyrme_render_rays: ray-march a volume of that layout (device, n[0]*n[1]*n[2]
+ *   records, 32-byte aligned, n[i] >= 2) into `rgba` (device, width*height
+ *   float4, 16-byte aligned, owned by the caller).  Camera and box:
+ *   - the lattice box is scaled so that its longest axis spans [-1, 1], lattice
+ *     coordinate g mapping to (g - (n-1)/2) / s, s = max (n_i - 1)/2;
+ *   - the eye is at (0, 0, 4) in view space; pixel (u, v) in [-aspect, aspect]
+ *     x [-1, 1] looks along (u, v, -2); `view` is the row-major rotation that
+ *     takes view-space vectors to box space;
+ *   - samples at t = t_near + k step along the unit ray inside the box take a
+ *     trilinear interpolation of all four components, clamped to the lattice;
+ *   - input = (b - levelset) transfer_scale, skipped when negative; colour =
+ *     input^2 (pion_1, pion_2, pion_3, 1 / input), composited front to back
+ *     (sum += colour (1 - sum_alpha)), stopping once sum_alpha > 0.95;
+ *   - the pixel is sum * brightness clamped to [0, 1].
+ *   SKYRME_EINVAL for width or height < 1, more than SKYRME_RENDER_MAX_PIXELS
+ *   pixels, step outside [SKYRME_RENDER_MIN_STEP, 1], non-finite values, a
+ *   view that is not a rotation (rows orthonormal to 1e-9), or null or
+ *   misaligned pointers.  Asynchronous.
+ *
+ * skyrme_render: skyrme_render_volume into `work` followed by
+ *   skyrme_render_rays. */
+#define SKYRME_RENDER_MAX_PIXELS (1LL << 26)
+#define SKYRME_RENDER_MIN_STEP 1e-4
+typedef struct {
+    int width, height;
+    double view[9];
+    double levelset, transfer_scale, brightness, step;
+} skyrme_render_params;
+size_t skyrme_render_volume_bytes(const skyrme_lattice *lat);
+skyrme_status skyrme_render_volume(const skyrme_lattice *lat, skyrme_state *st, void *vol,
+                                   size_t vol_bytes, void *stream);
+skyrme_status skyrme_render_rays(const int n[3], const void *vol,
+                                 const skyrme_render_params *params, float *rgba, void *stream);
+skyrme_status skyrme_render(const skyrme_lattice *lat, skyrme_state *st,
+                            const skyrme_render_params *params, void *work, size_t work_bytes,
+                            float *rgba, void *stream);
+
 /* ---- per-site values of the current field (asynchronous) ----
  * force (device, nullable): F at interior sites, 0 on the boundary layers,
  * same site layout and precision as phi.  dens (device, nullable): per site

@@ -30,6 +30,12 @@ class c_observables(ctypes.Structure):
                 ("W", ctypes.c_double * 9), ("D", ctypes.c_double), ("E", ctypes.c_double)]
 
 
+class c_render_params(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("view", ctypes.c_double * 9),
+                ("levelset", ctypes.c_double), ("transfer_scale", ctypes.c_double),
+                ("brightness", ctypes.c_double), ("step", ctypes.c_double)]
+
+
 class SkyrmeError(RuntimeError):
     def __init__(self, status: int, where: str, detail: str = ""):
         self.status = status
@@ -93,6 +99,13 @@ _SIGNATURES = {
     "skyrme_measure_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P]),
     "skyrme_observables": (ctypes.c_int, [ctypes.POINTER(c_lattice), ctypes.POINTER(c_state),
                                           ctypes.POINTER(c_observables), _P]),
+    "skyrme_render_volume_bytes": (ctypes.c_size_t, [ctypes.POINTER(c_lattice)]),
+    "skyrme_render_volume": (ctypes.c_int, [ctypes.POINTER(c_lattice), ctypes.POINTER(c_state), _P,
+                                            ctypes.c_size_t, _P]),
+    "skyrme_render_rays": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), _P,
+                                          ctypes.POINTER(c_render_params), _P, _P]),
+    "skyrme_render": (ctypes.c_int, [ctypes.POINTER(c_lattice), ctypes.POINTER(c_state),
+                                     ctypes.POINTER(c_render_params), _P, ctypes.c_size_t, _P, _P]),
     "skyrme_graph_create_until": (ctypes.c_int, [ctypes.POINTER(c_lattice), ctypes.c_double,
                                                  ctypes.c_int, ctypes.c_double, ctypes.c_longlong,
                                                  ctypes.c_int, ctypes.POINTER(c_state), _P,
@@ -362,6 +375,75 @@ def forces(lat: Lattice, st: State, want_dens: bool = True, stream=None):
                                 ctypes.c_void_p(D.data_ptr()) if D is not None else None,
                                 _stream_ptr(stream, st.device)), "skyrme_forces")
     return F, D
+
+
+RENDER_MIN_STEP = 1e-4
+RENDER_MAX_PIXELS = 1 << 26
+
+
+def render_params(width: int, height: int, view=None, levelset: float = 0.2,
+                  transfer_scale: float = 4.0, brightness: float = 1.0,
+                  step: float = 0.01) -> c_render_params:
+    """Parameters of the volume render; ``view`` is a row-major 3x3 rotation
+    taking view-space vectors to box space (identity by default)."""
+    v = np.eye(3) if view is None else np.asarray(view, dtype=np.float64).reshape(3, 3)
+    return c_render_params(int(width), int(height), (ctypes.c_double * 9)(*v.ravel().tolist()),
+                           float(levelset), float(transfer_scale), float(brightness), float(step))
+
+
+def render_volume(lat: Lattice, st: State, out=None, stream=None):
+    """Per-site volume {B0 / max B0, pion unit vector} of the current field as
+    a float64 device tensor of shape (Nx, Ny, Nz, 4) (skyrme_render_volume)."""
+    torch = _torch()
+    shape = tuple(int(v) for v in lat.n) + (4,)
+    vol = out if out is not None else torch.empty(shape, dtype=torch.float64, device=st.device)
+    cl, cs = lat.c(), st.c()
+    _check(load().skyrme_render_volume(ctypes.byref(cl), ctypes.byref(cs),
+                                       ctypes.c_void_p(vol.data_ptr()),
+                                       ctypes.c_size_t(vol.numel() * vol.element_size()),
+                                       _stream_ptr(stream, st.device)), "skyrme_render_volume")
+    return vol
+
+
+def render_rays(vol, params: c_render_params, stream=None):
+    """Ray-march a (Nx, Ny, Nz, 4) float64 device volume; returns a float32
+    device tensor of shape (height, width, 4), row 0 at the bottom."""
+    torch = _torch()
+    if vol.dtype != torch.float64 or vol.dim() != 4 or vol.shape[3] != 4 or not vol.is_contiguous():
+        raise ValueError("vol must be a contiguous float64 tensor of shape (Nx, Ny, Nz, 4)")
+    rgba = torch.empty((params.height, params.width, 4), dtype=torch.float32, device=vol.device)
+    n = (ctypes.c_int * 3)(*[int(v) for v in vol.shape[:3]])
+    _check(load().skyrme_render_rays(n, ctypes.c_void_p(vol.data_ptr()), ctypes.byref(params),
+                                     ctypes.c_void_p(rgba.data_ptr()),
+                                     _stream_ptr(stream, vol.device)), "skyrme_render_rays")
+    return rgba
+
+
+def render(lat: Lattice, st: State, params: c_render_params, work=None, stream=None):
+    """Volume render of the current field's baryon density (skyrme_render);
+    returns a float32 device tensor of shape (height, width, 4)."""
+    torch = _torch()
+    if work is None:
+        work = torch.empty(load().skyrme_render_volume_bytes(ctypes.byref(lat.c())),
+                           dtype=torch.uint8, device=st.device)
+    rgba = torch.empty((params.height, params.width, 4), dtype=torch.float32, device=st.device)
+    cl, cs = lat.c(), st.c()
+    _check(load().skyrme_render(ctypes.byref(cl), ctypes.byref(cs), ctypes.byref(params),
+                                ctypes.c_void_p(work.data_ptr()),
+                                ctypes.c_size_t(work.numel() * work.element_size()),
+                                ctypes.c_void_p(rgba.data_ptr()), _stream_ptr(stream, st.device)),
+           "skyrme_render")
+    return rgba
+
+
+def save_ppm(path: str, rgba) -> None:
+    """Write an RGBA image (height, width, 4; row 0 at the bottom, channels in
+    [0, 1]) as a binary PPM, top row first, alpha dropped."""
+    a = np.asarray(rgba.cpu() if hasattr(rgba, "cpu") else rgba, dtype=np.float64)
+    rgb = np.clip(np.rint(a[::-1, :, :3] * 255.0), 0, 255).astype(np.uint8)
+    with open(path, "wb") as f:
+        f.write(b"P6\n%d %d\n255\n" % (rgb.shape[1], rgb.shape[0]))
+        f.write(rgb.tobytes())
 
 
 PEAK_FP32, PEAK_FP64 = 0, 1

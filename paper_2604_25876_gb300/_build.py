@@ -21,6 +21,10 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-fast-math",
          "--expt-relaxed-constexpr", "-I" + INCLUDE]
+# Per-file extras: the ray-marcher rounds every multiply and add separately, so
+# that its sample, skip and stop decisions match a plain C restatement built
+# with contraction off.
+FILE_FLAGS = {"render.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:
@@ -43,6 +47,7 @@ def _fingerprint(srcs, deps) -> str:
         with open(p, "rb") as f:
             h.update(p.encode() + f.read())
     h.update(" ".join(ARCH + FLAGS).encode())
+    h.update(repr(sorted(FILE_FLAGS.items())).encode())
     return h.hexdigest()
 
 
@@ -61,7 +66,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     for s in srcs:
         o = os.path.join(OBJDIR, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
-        cmd = [cc] + ARCH + FLAGS + ["-c", s, "-o", o]
+        cmd = [cc] + ARCH + FLAGS + FILE_FLAGS.get(os.path.basename(s), []) + ["-c", s, "-o", o]
         if verbose:
             print(" ".join(cmd))
         procs.append((s, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

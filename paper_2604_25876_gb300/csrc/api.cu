@@ -480,4 +480,49 @@ skyrme_status skyrme_forces(const skyrme_lattice *lat, skyrme_state *st, void *f
     return SKYRME_OK;
 }
 
+size_t skyrme_render_volume_bytes(const skyrme_lattice *lat)
+{
+    if (!lattice_ok(lat)) return 0;
+    return (size_t)lat->n[0] * lat->n[1] * lat->n[2] * 4 * sizeof(double);
+}
+
+skyrme_status skyrme_render_volume(const skyrme_lattice *lat, skyrme_state *st, void *vol,
+                                   size_t vol_bytes, void *stream)
+{
+    skyrme_status rc = check_state(lat, st);
+    if (rc != SKYRME_OK) return rc;
+    if (!vol || ((uintptr_t)vol % 32)) return SKYRME_EINVAL;
+    if (vol_bytes < skyrme_render_volume_bytes(lat)) return SKYRME_ENOMEM;
+    const ScratchLayout L = scratch_layout(*lat);
+    FlowArgs a = make_args(*lat, *st, 0.0, MODE_ARRESTED);
+    void *bmax = static_cast<char *>(st->scratch) + L.energy_off;
+    CK(launch_render_volume(*lat, a, vol, bmax, static_cast<cudaStream_t>(stream)), "render volume");
+    return SKYRME_OK;
+}
+
+skyrme_status skyrme_render_rays(const int n[3], const void *vol,
+                                 const skyrme_render_params *params, float *rgba, void *stream)
+{
+    if (!n || !params || !vol || !rgba) return SKYRME_EINVAL;
+    if (((uintptr_t)vol % 32) || ((uintptr_t)rgba % 16)) return SKYRME_EINVAL;
+    for (int i = 0; i < 3; ++i)
+        if (n[i] < 2 || n[i] > (1 << 20)) return SKYRME_EINVAL;
+    if (!render_params_valid(*params)) return SKYRME_EINVAL;
+    CK(launch_render_rays(n, vol, *params, rgba, static_cast<cudaStream_t>(stream)), "render rays");
+    return SKYRME_OK;
+}
+
+skyrme_status skyrme_render(const skyrme_lattice *lat, skyrme_state *st,
+                            const skyrme_render_params *params, void *work, size_t work_bytes,
+                            float *rgba, void *stream)
+{
+    skyrme_status rc = check_state(lat, st);
+    if (rc != SKYRME_OK) return rc;
+    if (!params || !render_params_valid(*params) || !rgba || ((uintptr_t)rgba % 16))
+        return SKYRME_EINVAL;
+    rc = skyrme_render_volume(lat, st, work, work_bytes, stream);
+    if (rc != SKYRME_OK) return rc;
+    return skyrme_render_rays(lat->n, work, params, rgba, stream);
+}
+
 }  // extern "C"

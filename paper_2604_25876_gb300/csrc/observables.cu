@@ -25,6 +25,7 @@
 #include <math.h>
 #include <string.h>
 
+#include "lattice_sites.cuh"
 #include "skyrme_device.cuh"
 #include "skyrme_internal.h"
 
@@ -50,17 +51,6 @@ template <typename T> struct ObsArgs {
     double X[3];    // centre of mass (pass 1)
 };
 
-__device__ __forceinline__ void load_site(const float4 *p, size_t i, double v[4])
-{
-    const float4 q = __ldg(p + i);
-    v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
-}
-__device__ __forceinline__ void load_site(const dvec4 *p, size_t i, double v[4])
-{
-    const dvec4 q = p[i];
-    v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
-}
-
 template <typename T, int PASS>
 __global__ void __launch_bounds__(kObsThreads) k_observables(ObsArgs<T> a)
 {
@@ -81,25 +71,8 @@ __global__ void __launch_bounds__(kObsThreads) k_observables(ObsArgs<T> a)
         const size_t c = x * sx + y * sy + z;
         double ph[4], d[3][4];
         load_site(phi, c, ph);
-        const size_t st[3] = {sx, sy, 1};
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            double m2v[4], m1v[4], p1v[4], p2v[4];
-            load_site(phi, c - 2 * st[k], m2v);
-            load_site(phi, c - st[k], m1v);
-            load_site(phi, c + st[k], p1v);
-            load_site(phi, c + 2 * st[k], p2v);
-#pragma unroll
-            for (int A = 0; A < 4; ++A) d[k][A] = a.w1 * (p1v[A] - m1v[A]) + a.w2 * (p2v[A] - m2v[A]);
-        }
-        // baryon density -det[phi, d_x phi, d_y phi, d_z phi] / (2 pi^2), lattice derivatives
-        const double s0 = ph[0] * d[0][1] - d[0][0] * ph[1], s1 = ph[0] * d[0][2] - d[0][0] * ph[2];
-        const double s2 = ph[0] * d[0][3] - d[0][0] * ph[3], s3 = ph[1] * d[0][2] - d[0][1] * ph[2];
-        const double s4 = ph[1] * d[0][3] - d[0][1] * ph[3], s5 = ph[2] * d[0][3] - d[0][2] * ph[3];
-        const double q5 = d[1][2] * d[2][3] - d[2][2] * d[1][3], q4 = d[1][1] * d[2][3] - d[2][1] * d[1][3];
-        const double q3 = d[1][1] * d[2][2] - d[2][1] * d[1][2], q2 = d[1][0] * d[2][3] - d[2][0] * d[1][3];
-        const double q1 = d[1][0] * d[2][2] - d[2][0] * d[1][2], q0 = d[1][0] * d[2][1] - d[2][0] * d[1][1];
-        const double b = -0.050660591821168885 * (s0 * q5 - s1 * q4 + s2 * q3 + s3 * q2 - s4 * q1 + s5 * q0);
+        site_first_derivatives(phi, c, sx, sy, a.w1, a.w2, d);
+        const double b = baryon_density(ph, d);
         const double xv[3] = {((double)x - 0.5 * (a.n0 - 1)) * a.h, ((double)y - 0.5 * (a.n1 - 1)) * a.h,
                               ((double)z - 0.5 * (a.n2 - 1)) * a.h};
         if (PASS == 0) {

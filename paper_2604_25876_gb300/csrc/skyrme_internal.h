@@ -58,6 +58,13 @@ skyrme_status compute_observables(const skyrme_lattice &lat, const FlowArgs &a,
                                   skyrme_observables_t *out, cudaStream_t s);
 size_t observables_parts_bytes();
 
+// Volume render of the baryon density (render.cu)
+bool render_params_valid(const skyrme_render_params &p);
+cudaError_t launch_render_volume(const skyrme_lattice &lat, const FlowArgs &a, void *vol,
+                                 void *bmax_scratch, cudaStream_t s);
+cudaError_t launch_render_rays(const int n[3], const void *vol, const skyrme_render_params &p,
+                               float *rgba, cudaStream_t s);
+
 // Seeds (init_fields.cu)
 cudaError_t launch_seed(const skyrme_lattice &lat, const skyrme_seed &seed, const FlowArgs &a,
                         cudaStream_t s);

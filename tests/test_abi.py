@@ -119,3 +119,48 @@ def test_observables_rejects_bad_arguments_without_cuda():
                     ctypes.c_void_p(0x50000), ctypes.c_size_t(1 << 30))
     assert lib.skyrme_observables(ctypes.byref(lat), ctypes.byref(st), None, None) == 1
     assert lib.skyrme_observables(ctypes.byref(lat), None, ctypes.byref(sk.c_observables()), None) == 1
+
+
+def test_render_rejects_bad_arguments_without_cuda():
+    lib = sk.load()
+    lat = sk.Lattice((16, 20, 24), 0.2, 1.0, 32).c()
+    assert lib.skyrme_render_volume_bytes(ctypes.byref(lat)) == 16 * 20 * 24 * 32
+    bad_lat = sk.Lattice((4, 20, 24), 0.2, 1.0, 32).c()
+    assert lib.skyrme_render_volume_bytes(ctypes.byref(bad_lat)) == 0
+    st = sk.c_state((ctypes.c_void_p * 2)(0x10000, 0x20000), (ctypes.c_void_p * 2)(0x30000, 0x40000),
+                    ctypes.c_void_p(0x50000), ctypes.c_size_t(1 << 30))
+    need = 16 * 20 * 24 * 32
+    # volume: null, misaligned, too small
+    assert lib.skyrme_render_volume(ctypes.byref(lat), ctypes.byref(st), None, need, None) == 1
+    assert lib.skyrme_render_volume(ctypes.byref(lat), ctypes.byref(st), ctypes.c_void_p(0x60010),
+                                    need, None) == 1
+    assert lib.skyrme_render_volume(ctypes.byref(lat), ctypes.byref(st), ctypes.c_void_p(0x60000),
+                                    need - 1, None) == 2
+    n = (ctypes.c_int * 3)(16, 20, 24)
+    vol, rgba = ctypes.c_void_p(0x60000), ctypes.c_void_p(0x70000)
+    good = sk.render_params(32, 24)
+    rot = sk.render_params(32, 24, view=[[0, 1, 0], [-1, 0, 0], [0, 0, 1]])
+    # a valid call would launch kernels: only invalid ones run here
+    for p in (sk.render_params(0, 24), sk.render_params(32, -1), sk.render_params(1 << 14, 1 << 13),
+              sk.render_params(32, 24, step=0.0), sk.render_params(32, 24, step=1e-5),
+              sk.render_params(32, 24, step=2.0), sk.render_params(32, 24, step=float("nan")),
+              sk.render_params(32, 24, levelset=float("inf")),
+              sk.render_params(32, 24, brightness=float("nan")),
+              sk.render_params(32, 24, view=2 * sk.np.eye(3)),
+              sk.render_params(32, 24, view=[[1, 0, 0], [0, 1, 0], [0, 1e-6, 1]]),
+              sk.render_params(32, 24, view=sk.np.zeros((3, 3)))):
+        assert lib.skyrme_render_rays(n, vol, ctypes.byref(p), rgba, None) == 1
+        assert lib.skyrme_render(ctypes.byref(lat), ctypes.byref(st), ctypes.byref(p), vol, need,
+                                 rgba, None) == 1
+    for p in (good, rot):
+        assert lib.skyrme_render_rays(None, vol, ctypes.byref(p), rgba, None) == 1
+        assert lib.skyrme_render_rays(n, None, ctypes.byref(p), rgba, None) == 1
+        assert lib.skyrme_render_rays(n, vol, ctypes.byref(p), None, None) == 1
+        assert lib.skyrme_render_rays(n, ctypes.c_void_p(0x60008), ctypes.byref(p), rgba, None) == 1
+        assert lib.skyrme_render_rays(n, vol, ctypes.byref(p), ctypes.c_void_p(0x70004), None) == 1
+        assert lib.skyrme_render_rays(n, vol, None, rgba, None) == 1
+        assert lib.skyrme_render_rays((ctypes.c_int * 3)(1, 20, 24), vol, ctypes.byref(p), rgba,
+                                      None) == 1
+        assert lib.skyrme_render(ctypes.byref(lat), None, ctypes.byref(p), vol, need, rgba, None) == 1
+        assert lib.skyrme_render(ctypes.byref(lat), ctypes.byref(st), ctypes.byref(p), vol, need - 1,
+                                 rgba, None) == 2
