@@ -9,7 +9,11 @@ it with ctypes + NumPy.
 
 Paper passages: Section 2.1 (energy and baryon densities), Section 3 (flow
 equation, Euler-Lagrange gradient, stencils, arrest, projection, vacuum box),
-Section 4 (rational-map and product ansätze), Section 5.6 (virial).
+Section 4 (rational-map and product ansätze), Section 5.6 (virial), Section
+7.8 (extension potentials and the BPS sextic term).
+
+Wherever a mass ``m`` is taken, a ``Model`` may be passed instead to switch on
+the extension terms.
 """
 from __future__ import annotations
 
@@ -49,7 +53,33 @@ class _Report(ctypes.Structure):
     _fields_ = [("E", ctypes.c_double), ("E2", ctypes.c_double),
                 ("E4", ctypes.c_double), ("E0", ctypes.c_double),
                 ("B", ctypes.c_double), ("virial", ctypes.c_double),
-                ("delta", ctypes.c_double), ("arrested", ctypes.c_int)]
+                ("delta", ctypes.c_double), ("arrested", ctypes.c_int),
+                ("E6", ctypes.c_double)]
+
+
+class _Model(ctypes.Structure):
+    _fields_ = [("mx", ctypes.c_double), ("my", ctypes.c_double), ("mz", ctypes.c_double),
+                ("mw", ctypes.c_double), ("c6", ctypes.c_double)]
+
+
+@dataclass(frozen=True)
+class Model:
+    """Section 7.8 extension model: potential 2 mx^2 (1 - phi0) + my^2 (1 - phi0^2)
+    + mz^2 (1 - phi0)^2 + mw^2 (1 - phi0)^4 / 2 and the sextic term
+    c6 4 pi^4 (B0)^2 in the static energy density."""
+    mx: float
+    my: float = 0.0
+    mz: float = 0.0
+    mw: float = 0.0
+    c6: float = 0.0
+
+    def c(self) -> _Model:
+        return _Model(float(self.mx), float(self.my), float(self.mz), float(self.mw),
+                      float(self.c6))
+
+
+def _model(m) -> _Model:
+    return m.c() if isinstance(m, Model) else Model(float(m)).c()
 
 
 class _Observables(ctypes.Structure):
@@ -89,6 +119,16 @@ def _load():
             lib.orc_seed_product.argtypes = [I3, D, ctypes.c_int, P, P, D, ctypes.c_int, P]
             lib.orc_seed_noise.argtypes = [I3, D, D, D, ctypes.c_uint64, P]
             lib.orc_apply_vacuum_boundary.argtypes = [I3, P]
+            PM = ctypes.POINTER(_Model)
+            lib.orc_site_terms_model.argtypes = [P, P, P, P, PM, P, P, P]
+            lib.orc_forces_model.argtypes = [I3, D, PM, P, P, P, P]
+            lib.orc_energy_model.argtypes = [I3, D, PM, P, P]
+            lib.orc_anf_step_model.argtypes = [I3, D, PM, D, ctypes.c_int, P, P, P, P,
+                                               ctypes.POINTER(_Report)]
+            lib.orc_anf_step_model.restype = ctypes.c_int
+            lib.orc_flow_model.argtypes = [I3, D, PM, D, ctypes.c_int, ctypes.c_int, P, P, P, P,
+                                           ctypes.POINTER(_Report)]
+            lib.orc_flow_model.restype = ctypes.c_longlong
             lib.orc_observables.argtypes = [I3, D, D, P, ctypes.POINTER(_Observables)]
             lib.orc_render_volume_from_field.argtypes = [I3, D, P, P]
             lib.orc_render_volume.argtypes = [I3, P, ctypes.POINTER(_RenderParams), P]
@@ -128,22 +168,33 @@ def site_derivatives(phi: np.ndarray, h: float, x: int, y: int, z: int):
     return d1, d2, dm
 
 
-def site_terms(phi0, d1, d2, dm, m: float):
-    """(G, F, dens) at one site from its value and derivatives."""
+def site_terms(phi0, d1, d2, dm, m):
+    """(G, F, dens) at one site from its value and derivatives; dens =
+    (e2, e4, e0, b) for a mass m, (e2, e4, e0, b, e6) for a ``Model``."""
     lib = _load()
     args = [np.ascontiguousarray(a, dtype=np.float64) for a in (phi0, d1, d2, dm)]
-    G, F, dens = np.zeros(4), np.zeros(4), np.zeros(4)
-    lib.orc_site_terms(*[_ptr(a) for a in args], m, _ptr(G), _ptr(F), _ptr(dens))
+    G, F = np.zeros(4), np.zeros(4)
+    if isinstance(m, Model):
+        dens = np.zeros(5)
+        md = m.c()
+        lib.orc_site_terms_model(*[_ptr(a) for a in args], ctypes.byref(md), _ptr(G), _ptr(F),
+                                 _ptr(dens))
+    else:
+        dens = np.zeros(4)
+        lib.orc_site_terms(*[_ptr(a) for a in args], m, _ptr(G), _ptr(F), _ptr(dens))
     return G, F, dens
 
 
 # ------------------------------------------------------------- lattice level
-def forces(phi: np.ndarray, h: float, m: float):
-    """(G, F, dens) arrays of shape (Nx,Ny,Nz,4); zero on boundary layers."""
+def forces(phi: np.ndarray, h: float, m):
+    """(G, F, dens) arrays of shape (Nx,Ny,Nz,4); zero on boundary layers.
+    dens = (e2, e4, e0, b) per site; ``m`` a mass or a ``Model``."""
     lib = _load()
     phi = np.ascontiguousarray(phi, dtype=np.float64)
     G, F, dens = (np.zeros_like(phi) for _ in range(3))
-    lib.orc_forces(_dims(phi.shape[:3]), h, m, _ptr(phi), _ptr(G), _ptr(F), _ptr(dens))
+    md = _model(m)
+    lib.orc_forces_model(_dims(phi.shape[:3]), h, ctypes.byref(md), _ptr(phi), _ptr(G), _ptr(F),
+                         _ptr(dens))
     return G, F, dens
 
 
@@ -191,12 +242,14 @@ def render_sample(vol: np.ndarray, g) -> np.ndarray:
     return out
 
 
-def energy(phi: np.ndarray, h: float, m: float) -> dict:
+def energy(phi: np.ndarray, h: float, m) -> dict:
+    """E, E2, E4, E0, E6, B and the virial of a field; ``m`` a mass or a ``Model``."""
     lib = _load()
     phi = np.ascontiguousarray(phi, dtype=np.float64)
-    out = np.zeros(6)
-    lib.orc_energy(_dims(phi.shape[:3]), h, m, _ptr(phi), _ptr(out))
-    return dict(zip(("E", "E2", "E4", "E0", "B", "virial"), out.tolist()))
+    out = np.zeros(7)
+    md = _model(m)
+    lib.orc_energy_model(_dims(phi.shape[:3]), h, ctypes.byref(md), _ptr(phi), _ptr(out))
+    return dict(zip(("E", "E2", "E4", "E0", "E6", "B", "virial"), out.tolist()))
 
 
 @dataclass
@@ -214,7 +267,7 @@ def new_state(phi: np.ndarray) -> FlowState:
     return FlowState(phi=phi, v=np.zeros_like(phi))
 
 
-def flow(st: FlowState, h: float, m: float, dt: float, nsteps: int,
+def flow(st: FlowState, h: float, m, dt: float, nsteps: int,
          mode: int = ARRESTED, reports: bool = False):
     """Advance ``st`` by ``nsteps`` iterations; returns a list of per-step dicts
     when ``reports`` is true, else None.  Raises on a non-finite value."""
@@ -223,15 +276,16 @@ def flow(st: FlowState, h: float, m: float, dt: float, nsteps: int,
     work = np.zeros_like(st.phi)
     e_prev = np.array([st.E_prev])
     reps = (_Report * max(nsteps, 1))()
-    got = lib.orc_flow(_dims(n), h, m, dt, mode, nsteps, _ptr(st.phi), _ptr(st.v),
-                       _ptr(work), _ptr(e_prev), reps)
+    md = _model(m)
+    got = lib.orc_flow_model(_dims(n), h, ctypes.byref(md), dt, mode, nsteps, _ptr(st.phi),
+                             _ptr(st.v), _ptr(work), _ptr(e_prev), reps)
     st.E_prev = float(e_prev[0])
     if got < 0:
         raise FloatingPointError("oracle flow produced a non-finite value")
     st.steps += nsteps
     st.arrests += int(got)
     if reports:
-        return [dict(E=r.E, E2=r.E2, E4=r.E4, E0=r.E0, B=r.B, virial=r.virial,
+        return [dict(E=r.E, E2=r.E2, E4=r.E4, E0=r.E0, E6=r.E6, B=r.B, virial=r.virial,
                      delta=r.delta, arrested=r.arrested) for r in reps[:nsteps]]
     return None
 

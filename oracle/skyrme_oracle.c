@@ -19,6 +19,8 @@
  *   Section 4.1  rational-map ansatz, Table 1 (B = 1 and B = 4 maps)
  *   Section 4.2  product ansatz, Eq. "Product ansatz"
  *   Section 5.6  virial V = integral of T_kk
+ *   Section 7.8  extension models: the modified-pion, loosely and lightly
+ *                bound potentials and the BPS sextic term
  *
  * Readings where the paper is silent or ambiguous (each is a choice the CUDA
  * library makes the same way):
@@ -34,7 +36,13 @@
  *   - energies are h^3 times the sum over interior sites;
  *   - delta is the largest |F| over interior sites;
  *   - virial V = -E2 + E4 - 3 E0 (Derrick scaling of the three terms, which
- *     equals the integral of T_kk of Eq. "Stress tensor" for static fields).
+ *     equals the integral of T_kk of Eq. "Stress tensor" for static fields);
+ *     with the sextic term V = -E2 + E4 - 3 E0 + 3 E6 (E6 scales as lambda^3);
+ *   - the sextic term's c6 4 pi^4 (B0)^2 enters the static energy density
+ *     with a plus sign (a static energy bounded below for c6 >= 0), and the
+ *     flow sees only its static energy (the flow's kinetic term is the plain
+ *     sum of squared velocities);
+ *   - E0 is the sum of all four potentials.
  */
 #include "skyrme_oracle.h"
 
@@ -135,10 +143,109 @@ static int perm_sign(const int *p, int len)
     return s;
 }
 
+/* Levi-Civita symbol eps_{abcd} with eps_{0123} = +1 (0 for a repeated index). */
+static int levi4(int a, int b, int c, int d)
+{
+    int p[4];
+    if (a == b || a == c || a == d || b == c || b == d || c == d) return 0;
+    p[0] = a;
+    p[1] = b;
+    p[2] = c;
+    p[3] = d;
+    return perm_sign(p, 4);
+}
+
+/* Section 7.8, BPS sextic term.  With the rows R_0 = phi, R_1 = d_x phi,
+ * R_2 = d_y phi, R_3 = d_z phi and D = eps_{ABCD} R_0^A R_1^B R_2^C R_3^D,
+ * B0 = -D / (2 pi^2), so the static density c6 4 pi^4 (B0)^2 is c6 D^2.  Its
+ * Euler-Lagrange gradient, written out by the chain rule:
+ *   G6_A = d(c6 D^2)/dphi^A - d_i [ d(c6 D^2)/d(d_i phi^A) ]
+ *        = 2 c6 [ D C_0^A - sum_i ( (d_i D) C_{1+i}^A + D d_i C_{1+i}^A ) ]
+ * with the cofactors C_r^A = dD/dR_r^A, d_i D = sum_r C_r . d_i R_r and
+ * d_i C_r^A = sum_{s != r} (d^2 D / dR_r^A dR_s^B) d_i R_s^B, where
+ * d_i R_0 = d_i phi and d_i R_{1+j} = d_i d_j phi (H[i][j]). */
+static void sextic_gradient(const double phi[4], const double d1[3][4],
+                            const double H[3][3][4], double c6, double G6[4])
+{
+    const double *R[4];
+    double dR[3][4][4];       /* dR[i][r][A] = d_i R_r^A */
+    double C[4][4];           /* dD / dR_r^A */
+    double C2[4][4][4][4];    /* d^2 D / dR_r^A dR_s^B, r != s */
+    double D = 0.0, dD[3], dC[3][4][4];
+    int idx[4], i, r, s, A, B, k;
+
+    R[0] = phi;
+    R[1] = d1[0];
+    R[2] = d1[1];
+    R[3] = d1[2];
+    memset(C, 0, sizeof(C));
+    memset(C2, 0, sizeof(C2));
+    for (idx[0] = 0; idx[0] < 4; idx[0]++)
+        for (idx[1] = 0; idx[1] < 4; idx[1]++)
+            for (idx[2] = 0; idx[2] < 4; idx[2]++)
+                for (idx[3] = 0; idx[3] < 4; idx[3]++) {
+                    const int e = levi4(idx[0], idx[1], idx[2], idx[3]);
+                    if (e == 0) continue;
+                    D += e * R[0][idx[0]] * R[1][idx[1]] * R[2][idx[2]] * R[3][idx[3]];
+                    for (r = 0; r < 4; r++) {
+                        double prod = e;
+                        for (k = 0; k < 4; k++)
+                            if (k != r) prod *= R[k][idx[k]];
+                        C[r][idx[r]] += prod;
+                        for (s = 0; s < 4; s++) {
+                            double p2 = e;
+                            if (s == r) continue;
+                            for (k = 0; k < 4; k++)
+                                if (k != r && k != s) p2 *= R[k][idx[k]];
+                            C2[r][s][idx[r]][idx[s]] += p2;
+                        }
+                    }
+                }
+    for (i = 0; i < 3; i++)
+        for (A = 0; A < 4; A++) {
+            dR[i][0][A] = d1[i][A];
+            for (r = 1; r < 4; r++) dR[i][r][A] = H[i][r - 1][A];
+        }
+    for (i = 0; i < 3; i++) {
+        dD[i] = 0.0;
+        for (r = 0; r < 4; r++)
+            for (A = 0; A < 4; A++) dD[i] += C[r][A] * dR[i][r][A];
+        for (r = 0; r < 4; r++)
+            for (A = 0; A < 4; A++) {
+                double t = 0.0;
+                for (s = 0; s < 4; s++) {
+                    if (s == r) continue;
+                    for (B = 0; B < 4; B++) t += C2[r][s][A][B] * dR[i][s][B];
+                }
+                dC[i][r][A] = t;
+            }
+    }
+    for (A = 0; A < 4; A++) {
+        double div = 0.0;
+        for (i = 0; i < 3; i++) div += dD[i] * C[1 + i][A] + D * dC[i][1 + i][A];
+        G6[A] = 2.0 * c6 * (D * C[0][A] - div);
+    }
+}
+
 void orc_site_terms(const double phi[4], const double d1[3][4],
                     const double d2[3][4], const double dm[3][4], double m,
                     double G[4], double F[4], double dens[4])
 {
+    orc_model md;
+    double d5[5];
+    int q;
+    md.mx = m;
+    md.my = md.mz = md.mw = md.c6 = 0.0;
+    orc_site_terms_model(phi, d1, d2, dm, &md, G, F, d5);
+    for (q = 0; q < 4; q++) dens[q] = d5[q];
+}
+
+void orc_site_terms_model(const double phi[4], const double d1[3][4],
+                          const double d2[3][4], const double dm[3][4],
+                          const orc_model *md, double G[4], double F[4],
+                          double dens[5])
+{
+    const double m = md->mx;
     double H[3][3][4]; /* d_i d_j phi^A */
     double a[3][3];    /* d_i phi . d_j phi */
     double tra, Gphi, sumsq;
@@ -178,6 +285,18 @@ void orc_site_terms(const double phi[4], const double d1[3][4],
             for (j = 0; j < 3; j++) t3 += H[i][j][A] * a[i][j];
         G[A] = -2.0 * (t1 + t2 - t3 + (A == 0 ? m * m : 0.0));
     }
+    /* Section 7.8 potentials m_y^2 (1 - phi0^2) + m_z^2 (1 - phi0)^2
+     * + (1/2) m_w^2 (1 - phi0)^4: their derivatives in phi^0 */
+    {
+        const double u = 1.0 - phi[0];
+        G[0] += -2.0 * md->my * md->my * phi[0] - 2.0 * md->mz * md->mz * u
+                - 2.0 * md->mw * md->mw * u * u * u;
+    }
+    if (md->c6 != 0.0) {
+        double G6[4];
+        sextic_gradient(phi, d1, (const double(*)[3][4])H, md->c6, G6);
+        for (A = 0; A < 4; A++) G[A] += G6[A];
+    }
 
     /* Eq. "Newton_flow": phi_tt^A = -dE/dphi^A + (dE/dphi^B phi^B) phi^A */
     Gphi = 0.0;
@@ -190,7 +309,11 @@ void orc_site_terms(const double phi[4], const double d1[3][4],
         for (j = 0; j < 3; j++) sumsq += a[i][j] * a[i][j];
     dens[0] = tra;
     dens[1] = 0.5 * (tra * tra - sumsq);
-    dens[2] = 2.0 * m * m * (1.0 - phi[0]);
+    {
+        const double u = 1.0 - phi[0];
+        dens[2] = 2.0 * m * m * u + md->my * md->my * (1.0 - phi[0] * phi[0])
+                  + md->mz * md->mz * u * u + 0.5 * md->mw * md->mw * u * u * u * u;
+    }
 
     /* Eq. "B0_components" (sign reading in the file header) */
     {
@@ -220,19 +343,22 @@ void orc_site_terms(const double phi[4], const double d1[3][4],
         }
         dens[3] = -s / (12.0 * M_PI * M_PI);
     }
+    /* Section 7.8: c6 4 pi^4 (B0)^2 */
+    dens[4] = md->c6 * 4.0 * M_PI * M_PI * M_PI * M_PI * dens[3] * dens[3];
 }
 
 /* ------------------------------------------------------------------------
  * whole-lattice passes
  * ------------------------------------------------------------------------ */
 typedef struct {
-    nsum e[4];
+    nsum e[5];
     double fmax;
     int bad;
 } plane_acc;
 
-/* Per-site work for one x-plane; writes G/F/dens when requested. */
-static void plane_pass(const int n[3], double h, double m, const double *phi,
+/* Per-site work for one x-plane; writes G/F/dens (e2, e4, e0, b) when
+ * requested and sums e2, e4, e0, b, e6. */
+static void plane_pass(const int n[3], double h, const orc_model *md, const double *phi,
                        int x, double *G, double *F, double *dens,
                        plane_acc *acc)
 {
@@ -240,17 +366,17 @@ static void plane_pass(const int n[3], double h, double m, const double *phi,
     memset(acc, 0, sizeof(*acc));
     for (y = 2; y <= n[1] - 3; y++)
         for (z = 2; z <= n[2] - 3; z++) {
-            double d1[3][4], d2[3][4], dm[3][4], g[4], f[4], d[4], fn;
+            double d1[3][4], d2[3][4], dm[3][4], g[4], f[4], d[5], fn;
             size_t s = site_index(n, x, y, z);
             orc_site_derivatives(n, h, phi, x, y, z, d1, d2, dm);
-            orc_site_terms(&phi[4 * s], d1, d2, dm, m, g, f, d);
+            orc_site_terms_model(&phi[4 * s], d1, d2, dm, md, g, f, d);
             for (q = 0; q < 4; q++) {
                 if (G) G[4 * s + q] = g[q];
                 if (F) F[4 * s + q] = f[q];
                 if (dens) dens[4 * s + q] = d[q];
-                nsum_add(&acc->e[q], d[q]);
                 if (!isfinite(f[q]) || !isfinite(d[q])) acc->bad = 1;
             }
+            for (q = 0; q < 5; q++) nsum_add(&acc->e[q], d[q]);
             fn = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2] + f[3] * f[3]);
             if (fn > acc->fmax) acc->fmax = fn;
         }
@@ -268,68 +394,99 @@ static void zero_boundary(const int n[3], double *arr)
                            4 * sizeof(double));
 }
 
-/* Sum the per-plane accumulators in plane order. */
-static void lattice_pass(const int n[3], double h, double m, const double *phi,
-                         double *G, double *F, double *dens, double sums[4],
+/* Sum the per-plane accumulators in plane order: sums = {e2, e4, e0, b, e6}. */
+static void lattice_pass(const int n[3], double h, const orc_model *md, const double *phi,
+                         double *G, double *F, double *dens, double sums[5],
                          double *fmax, int *bad)
 {
     int x, q;
     int nx = n[0];
     plane_acc *acc = (plane_acc *)calloc((size_t)nx, sizeof(plane_acc));
-    nsum tot[4];
+    nsum tot[5];
 #pragma omp parallel for schedule(dynamic, 1)
-    for (x = 2; x <= nx - 3; x++) plane_pass(n, h, m, phi, x, G, F, dens, &acc[x]);
+    for (x = 2; x <= nx - 3; x++) plane_pass(n, h, md, phi, x, G, F, dens, &acc[x]);
     memset(tot, 0, sizeof(tot));
     *fmax = 0.0;
     *bad = 0;
     for (x = 2; x <= nx - 3; x++) {
-        for (q = 0; q < 4; q++) nsum_add(&tot[q], nsum_get(&acc[x].e[q]));
+        for (q = 0; q < 5; q++) nsum_add(&tot[q], nsum_get(&acc[x].e[q]));
         if (acc[x].fmax > *fmax) *fmax = acc[x].fmax;
         if (acc[x].bad) *bad = 1;
     }
-    for (q = 0; q < 4; q++) sums[q] = nsum_get(&tot[q]);
+    for (q = 0; q < 5; q++) sums[q] = nsum_get(&tot[q]);
     free(acc);
+}
+
+static orc_model standard_model(double m)
+{
+    orc_model md;
+    md.mx = m;
+    md.my = md.mz = md.mw = md.c6 = 0.0;
+    return md;
+}
+
+void orc_forces_model(const int n[3], double h, const orc_model *md, const double *phi,
+                      double *G, double *F, double *dens)
+{
+    double sums[5], fmax;
+    int bad;
+    zero_boundary(n, G);
+    zero_boundary(n, F);
+    zero_boundary(n, dens);
+    lattice_pass(n, h, md, phi, G, F, dens, sums, &fmax, &bad);
 }
 
 void orc_forces(const int n[3], double h, double m, const double *phi,
                 double *G, double *F, double *dens)
 {
-    double sums[4], fmax;
+    const orc_model md = standard_model(m);
+    orc_forces_model(n, h, &md, phi, G, F, dens);
+}
+
+void orc_energy_model(const int n[3], double h, const orc_model *md, const double *phi,
+                      double out[7])
+{
+    double sums[5], fmax, h3 = h * h * h;
     int bad;
-    zero_boundary(n, G);
-    zero_boundary(n, F);
-    zero_boundary(n, dens);
-    lattice_pass(n, h, m, phi, G, F, dens, sums, &fmax, &bad);
+    lattice_pass(n, h, md, phi, NULL, NULL, NULL, sums, &fmax, &bad);
+    out[1] = h3 * sums[0];
+    out[2] = h3 * sums[1];
+    out[3] = h3 * sums[2];
+    out[4] = h3 * sums[4];
+    out[0] = out[1] + out[2] + out[3] + out[4];
+    out[5] = h3 * sums[3];
+    out[6] = -out[1] + out[2] - 3.0 * out[3] + 3.0 * out[4];
 }
 
 void orc_energy(const int n[3], double h, double m, const double *phi,
                 double out[6])
 {
-    double sums[4], fmax, h3 = h * h * h;
-    int bad;
-    lattice_pass(n, h, m, phi, NULL, NULL, NULL, sums, &fmax, &bad);
-    out[1] = h3 * sums[0];
-    out[2] = h3 * sums[1];
-    out[3] = h3 * sums[2];
-    out[0] = out[1] + out[2] + out[3];
-    out[4] = h3 * sums[3];
-    out[5] = -out[1] + out[2] - 3.0 * out[3];
+    const orc_model md = standard_model(m);
+    double o7[7];
+    orc_energy_model(n, h, &md, phi, o7);
+    out[0] = o7[0];
+    out[1] = o7[1];
+    out[2] = o7[2];
+    out[3] = o7[3];
+    out[4] = o7[5];
+    out[5] = o7[6];
 }
 
-int orc_anf_step(const int n[3], double h, double m, double dt, int mode,
-                 double *phi, double *v, double *work, double *E_prev,
-                 orc_report *rep)
+int orc_anf_step_model(const int n[3], double h, const orc_model *md, double dt, int mode,
+                       double *phi, double *v, double *work, double *E_prev,
+                       orc_report *rep)
 {
-    double sums[4], fmax, h3 = h * h * h, E, E2, E4, E0;
+    double sums[5], fmax, h3 = h * h * h, E, E2, E4, E0, E6;
     int bad, arrested = 0, x;
     size_t nsite = (size_t)n[0] * n[1] * n[2];
 
     zero_boundary(n, work);
-    lattice_pass(n, h, m, phi, NULL, work, NULL, sums, &fmax, &bad);
+    lattice_pass(n, h, md, phi, NULL, work, NULL, sums, &fmax, &bad);
     E2 = h3 * sums[0];
     E4 = h3 * sums[1];
     E0 = h3 * sums[2];
-    E = E2 + E4 + E0;
+    E6 = h3 * sums[4];
+    E = E2 + E4 + E0 + E6;
 
     /* arrest: the static energy rose, so the fictitious velocity is zeroed
      * while the field is kept (Section 3). */
@@ -366,22 +523,31 @@ int orc_anf_step(const int n[3], double h, double m, double dt, int mode,
         rep->E4 = E4;
         rep->E0 = E0;
         rep->B = h3 * sums[3];
-        rep->virial = -E2 + E4 - 3.0 * E0;
+        rep->virial = -E2 + E4 - 3.0 * E0 + 3.0 * E6;
         rep->delta = fmax;
         rep->arrested = arrested;
+        rep->E6 = E6;
     }
     return (bad || !isfinite(E)) ? -1 : 0;
 }
 
-long long orc_flow(const int n[3], double h, double m, double dt, int mode,
-                   int nsteps, double *phi, double *v, double *work,
-                   double *E_prev, orc_report *reps)
+int orc_anf_step(const int n[3], double h, double m, double dt, int mode,
+                 double *phi, double *v, double *work, double *E_prev,
+                 orc_report *rep)
+{
+    const orc_model md = standard_model(m);
+    return orc_anf_step_model(n, h, &md, dt, mode, phi, v, work, E_prev, rep);
+}
+
+long long orc_flow_model(const int n[3], double h, const orc_model *md, double dt, int mode,
+                         int nsteps, double *phi, double *v, double *work,
+                         double *E_prev, orc_report *reps)
 {
     long long arrests = 0;
     int s;
     for (s = 0; s < nsteps; s++) {
         orc_report r;
-        if (orc_anf_step(n, h, m, dt, mode, phi, v, work, E_prev, &r) != 0) {
+        if (orc_anf_step_model(n, h, md, dt, mode, phi, v, work, E_prev, &r) != 0) {
             if (reps) reps[s] = r;
             return -1;
         }
@@ -389,6 +555,14 @@ long long orc_flow(const int n[3], double h, double m, double dt, int mode,
         if (reps) reps[s] = r;
     }
     return arrests;
+}
+
+long long orc_flow(const int n[3], double h, double m, double dt, int mode,
+                   int nsteps, double *phi, double *v, double *work,
+                   double *E_prev, orc_report *reps)
+{
+    const orc_model md = standard_model(m);
+    return orc_flow_model(n, h, &md, dt, mode, nsteps, phi, v, work, E_prev, reps);
 }
 
 /* ------------------------------------------------------------------------

@@ -41,6 +41,22 @@ void orc_site_terms(const double phi[4], const double d1[3][4],
                     const double d2[3][4], const double dm[3][4], double m,
                     double G[4], double F[4], double dens[4]);
 
+/* ---- extension models (Section 7.8) ----
+ * The potential is 2 mx^2 (1 - phi0) + my^2 (1 - phi0^2) + mz^2 (1 - phi0)^2
+ * + (1/2) mw^2 (1 - phi0)^4 (standard, modified pion, loosely bound and
+ * lightly bound), and the BPS sextic term adds c6 4 pi^4 (B0)^2 to the static
+ * energy density.  {m, 0, 0, 0, 0} is the standard model of Section 2.1. */
+typedef struct {
+    double mx, my, mz, mw, c6;
+} orc_model;
+
+/* As orc_site_terms for a model: dens = {e2, e4, e0, b, e6}, e0 the sum of
+ * the four potentials, e6 = c6 4 pi^4 b^2. */
+void orc_site_terms_model(const double phi[4], const double d1[3][4],
+                          const double d2[3][4], const double dm[3][4],
+                          const orc_model *md, double G[4], double F[4],
+                          double dens[5]);
+
 /* ---- whole-lattice operations ---- */
 
 /* G, F and densities at every interior site (zero on the boundary layers).
@@ -52,6 +68,14 @@ void orc_forces(const int n[3], double h, double m, const double *phi,
  * V = -E2 + E4 - 3 E0 (the virial, Section 5.6). */
 void orc_energy(const int n[3], double h, double m, const double *phi,
                 double out[6]);
+
+/* Model versions: dens keeps {e2, e4, e0, b} per site (e6 = c6 4 pi^4 b^2);
+ * out = {E, E2, E4, E0, E6, B, V}, E = E2 + E4 + E0 + E6 and
+ * V = -E2 + E4 - 3 E0 + 3 E6. */
+void orc_forces_model(const int n[3], double h, const orc_model *md, const double *phi,
+                      double *G, double *F, double *dens);
+void orc_energy_model(const int n[3], double h, const orc_model *md, const double *phi,
+                      double out[7]);
 
 /* Section 5 observables of a static field (h^3 times sums over interior
  * sites; r = x - X_c):
@@ -106,6 +130,7 @@ typedef struct {
     double E, E2, E4, E0, B, virial; /* of the field at the start of the step */
     double delta;                    /* max over interior sites of |F|      */
     int arrested;                    /* 1 when the velocity was zeroed       */
+    double E6;                       /* sextic part of E (0 without it)      */
 } orc_report;
 
 enum { ORC_NEWTON = 0, ORC_ARRESTED = 1, ORC_GRADIENT = 2 };
@@ -127,6 +152,14 @@ int orc_anf_step(const int n[3], double h, double m, double dt, int mode,
 long long orc_flow(const int n[3], double h, double m, double dt, int mode,
                    int nsteps, double *phi, double *v, double *work,
                    double *E_prev, orc_report *reps);
+
+/* Model versions of the step and the flow (E includes E6). */
+int orc_anf_step_model(const int n[3], double h, const orc_model *md, double dt, int mode,
+                       double *phi, double *v, double *work, double *E_prev,
+                       orc_report *rep);
+long long orc_flow_model(const int n[3], double h, const orc_model *md, double dt, int mode,
+                         int nsteps, double *phi, double *v, double *work,
+                         double *E_prev, orc_report *reps);
 
 /* ---- initial fields (Section 4) ---- */
 
