@@ -28,7 +28,7 @@
 extern "C" {
 #endif
 
-#define SKYRME_ABI_VERSION 1
+#define SKYRME_ABI_VERSION 2
 
 typedef enum {
     SKYRME_OK = 0,
@@ -37,7 +37,7 @@ typedef enum {
     SKYRME_ECUDA = 3,       /* a CUDA runtime call failed (the message is in skyrme_last_cuda_error) */
     SKYRME_ENONFINITE = 4,  /* a NaN/Inf appeared in a force, density or energy sum */
     SKYRME_ETIMEOUT = 5,    /* a bounded device-side wait gave up */
-    SKYRME_EUNSUPPORTED = 6 /* the request is valid but not implemented for this precision */
+    SKYRME_EUNSUPPORTED = 6 /* the request is valid but not implemented for this precision or model */
 } skyrme_status;
 
 /* Flow equations of Section 3.  ARRESTED is the arrested Newton flow
@@ -45,11 +45,27 @@ typedef enum {
  * without arrest, GRADIENT the first-order flow phi_t = F. */
 typedef enum { SKYRME_NEWTON = 0, SKYRME_ARRESTED = 1, SKYRME_GRADIENT = 2 } skyrme_flow_mode;
 
+/* The model (Section 2.1, extended by the options of Section 7.8):
+ *   static energy density  e2 + e4 + e0 + e6, with
+ *   e0 = 2 m^2 (1 - phi^0) + m_y^2 (1 - (phi^0)^2) + m_z^2 (1 - phi^0)^2
+ *        + (1/2) m_w^2 (1 - phi^0)^4
+ *        (standard pion mass, modified pion mass, loosely bound and lightly
+ *        bound potentials) and
+ *   e6 = c6 4 pi^4 (B0)^2  (the BPS sextic term, B0 of Eq. "B0_components").
+ * All five coefficients are finite and >= 0; m_y = m_z = m_w = c6 = 0 is the
+ * standard model.  A lattice with any of the four extension coefficients
+ * non-zero is an "extended" lattice: its flow runs on the tile kernels (FP32
+ * or FP64), and the batched flow and the Section 5 observables reject it with
+ * SKYRME_EUNSUPPORTED. */
 typedef struct {
     int n[3];       /* sites per axis (x slowest, z fastest); each >= 5 */
     double h;       /* lattice spacing, > 0, equal on every axis */
     double m;       /* pion mass of the 2 m^2 (1 - phi^0) potential (Eq. SkyrmeEnergy_phi) */
     int precision;  /* 32: float4 field and velocity, FP64 sums; 64: double4 */
+    double m_y;     /* modified pion mass: m_y^2 (1 - (phi^0)^2) */
+    double m_z;     /* loosely bound potential: m_z^2 (1 - phi^0)^2 */
+    double m_w;     /* lightly bound potential: (1/2) m_w^2 (1 - phi^0)^4 */
+    double c6;      /* BPS sextic term: c6 4 pi^4 (B0)^2 */
 } skyrme_lattice;
 
 enum {
@@ -87,9 +103,10 @@ typedef struct {
 /* Result of the latest flow iteration, read back from the control block. */
 typedef struct {
     double E, E2, E4, E0;  /* static energy of the field at the start of the
-                              iteration and its quadratic, quartic and mass parts */
+                              iteration and its quadratic, quartic and potential
+                              parts (E = E2 + E4 + E0 + E6) */
     double B;              /* baryon number, Eq. "B0_components" integrated */
-    double virial;         /* V = -E2 + E4 - 3 E0 (Section 5.6) */
+    double virial;         /* V = -E2 + E4 - 3 E0 + 3 E6 (Section 5.6, Derrick scaling) */
     double delta;          /* max over interior sites of |F| (the residual of Section 3) */
     double rms_force;      /* sqrt(mean |F|^2) over interior sites */
     long long steps;       /* iterations completed since the field was set */
@@ -97,6 +114,7 @@ typedef struct {
     long long fixups;      /* speculative updates corrected after the energy was known */
     int cur;               /* index (0/1) of the buffers holding the current field */
     int status;            /* sticky device-side status (skyrme_status) */
+    double E6;             /* sextic part of E (0 without the sextic term) */
 } skyrme_report;
 
 /* ---- queries ---- */
@@ -203,13 +221,17 @@ skyrme_status skyrme_read_report(const skyrme_lattice *lat, const skyrme_state *
 
 /* ---- reductions of the current field (synchronise the stream) ----
  * out6 = {E, E2, E4, E0, B, V}: h^3 times FP64 sums over interior sites of
- * the densities of Eq. SkyrmeEnergy_phi and Eq. B0_components; V as above. */
+ * the densities of Eq. SkyrmeEnergy_phi (with the model's e0 and e6) and
+ * Eq. B0_components; E and V include the sextic part, which
+ * skyrme_sextic_energy returns on its own. */
 skyrme_status skyrme_energy(const skyrme_lattice *lat, skyrme_state *st, double out6[6],
                             void *stream);
 skyrme_status skyrme_baryon_number(const skyrme_lattice *lat, skyrme_state *st, double *B,
                                    void *stream);
 skyrme_status skyrme_virial(const skyrme_lattice *lat, skyrme_state *st, double *V,
                             void *stream);
+skyrme_status skyrme_sextic_energy(const skyrme_lattice *lat, skyrme_state *st, double *E6,
+                                   void *stream);
 
 /* ---- Section 5 observables of the current field ----
  * skyrme_observables: h^3-weighted sums over interior sites of
@@ -286,7 +308,8 @@ skyrme_status skyrme_render(const skyrme_lattice *lat, skyrme_state *st,
 /* ---- per-site values of the current field (asynchronous) ----
  * force (device, nullable): F at interior sites, 0 on the boundary layers,
  * same site layout and precision as phi.  dens (device, nullable): per site
- * {e2, e4, e0, b} in the same precision. */
+ * {e2, e4, e0, b} in the same precision (e0 the model's whole potential; the
+ * sextic density is c6 4 pi^4 b^2). */
 skyrme_status skyrme_forces(const skyrme_lattice *lat, skyrme_state *st, void *force,
                             void *dens, void *stream);
 

@@ -47,7 +47,8 @@ class SkyrmeError(RuntimeError):
 
 class c_lattice(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int * 3), ("h", ctypes.c_double), ("m", ctypes.c_double),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("m_y", ctypes.c_double), ("m_z", ctypes.c_double),
+                ("m_w", ctypes.c_double), ("c6", ctypes.c_double)]
 
 
 class c_seed(ctypes.Structure):
@@ -68,7 +69,8 @@ class c_report(ctypes.Structure):
                 ("E0", ctypes.c_double), ("B", ctypes.c_double), ("virial", ctypes.c_double),
                 ("delta", ctypes.c_double), ("rms_force", ctypes.c_double),
                 ("steps", ctypes.c_longlong), ("arrests", ctypes.c_longlong),
-                ("fixups", ctypes.c_longlong), ("cur", ctypes.c_int), ("status", ctypes.c_int)]
+                ("fixups", ctypes.c_longlong), ("cur", ctypes.c_int), ("status", ctypes.c_int),
+                ("E6", ctypes.c_double)]
 
 
 # Exported symbols with their ctypes signatures (also checked by the ABI tests).
@@ -92,6 +94,8 @@ _SIGNATURES = {
                                             ctypes.POINTER(ctypes.c_double), _P]),
     "skyrme_virial": (ctypes.c_int, [ctypes.POINTER(c_lattice), ctypes.POINTER(c_state),
                                      ctypes.POINTER(ctypes.c_double), _P]),
+    "skyrme_sextic_energy": (ctypes.c_int, [ctypes.POINTER(c_lattice), ctypes.POINTER(c_state),
+                                            ctypes.POINTER(ctypes.c_double), _P]),
     "skyrme_forces": (ctypes.c_int, [ctypes.POINTER(c_lattice), ctypes.POINTER(c_state), _P, _P,
                                      _P]),
     "skyrme_energy_static": (ctypes.c_int, [ctypes.POINTER(c_lattice), _P,
@@ -175,14 +179,26 @@ def _stream_ptr(stream=None, device=None):
 # --------------------------------------------------------------- lattice
 @dataclass
 class Lattice:
+    """Lattice and model: n sites per axis, spacing h, pion mass m, precision
+    32 or 64, and the Section 7.8 extension coefficients m_y (modified pion
+    mass), m_z (loosely bound), m_w (lightly bound) and c6 (sextic term)."""
     n: Sequence[int]
     h: float
     m: float = 0.0
     precision: int = 32
+    m_y: float = 0.0
+    m_z: float = 0.0
+    m_w: float = 0.0
+    c6: float = 0.0
 
     def c(self) -> c_lattice:
         return c_lattice((ctypes.c_int * 3)(*[int(v) for v in self.n]), float(self.h),
-                         float(self.m), int(self.precision))
+                         float(self.m), int(self.precision), float(self.m_y), float(self.m_z),
+                         float(self.m_w), float(self.c6))
+
+    @property
+    def extended(self) -> bool:
+        return any(v != 0.0 for v in (self.m_y, self.m_z, self.m_w, self.c6))
 
     @property
     def dtype(self):
@@ -348,6 +364,28 @@ def virial(lat: Lattice, st: State, stream=None) -> float:
     out = ctypes.c_double()
     _check(load().skyrme_virial(ctypes.byref(cl), ctypes.byref(cs), ctypes.byref(out),
                                 _stream_ptr(stream, st.device)), "skyrme_virial")
+    return out.value
+
+
+def energy_static(lat: Lattice, phi, stream=None) -> dict:
+    """skyrme_energy_static of a device field tensor (Nx, Ny, Nz, 4) in the
+    lattice's precision: E, E2, E4, E0, B and the virial, allocating nothing."""
+    if phi.dtype != lat.dtype or not phi.is_contiguous() or tuple(phi.shape) != tuple(
+            int(v) for v in lat.n) + (4,):
+        raise ValueError("phi must be a contiguous (Nx, Ny, Nz, 4) tensor of the lattice dtype")
+    cl = lat.c()
+    out = (ctypes.c_double * 6)()
+    _check(load().skyrme_energy_static(ctypes.byref(cl), ctypes.c_void_p(phi.data_ptr()), out,
+                                       _stream_ptr(stream, phi.device)), "skyrme_energy_static")
+    return dict(zip(("E", "E2", "E4", "E0", "B", "virial"), list(out)))
+
+
+def sextic_energy(lat: Lattice, st: State, stream=None) -> float:
+    """E6 = h^3 sum of c6 4 pi^4 (B0)^2 of the current field (skyrme_sextic_energy)."""
+    cl, cs = lat.c(), st.c()
+    out = ctypes.c_double()
+    _check(load().skyrme_sextic_energy(ctypes.byref(cl), ctypes.byref(cs), ctypes.byref(out),
+                                       _stream_ptr(stream, st.device)), "skyrme_sextic_energy")
     return out.value
 
 

@@ -47,6 +47,9 @@ static bool lattice_ok(const skyrme_lattice *lat)
     for (int i = 0; i < 3; ++i)
         if (lat->n[i] < 5 || lat->n[i] > 4096) return false;
     if (!(lat->h > 0.0) || !isfinite(lat->h) || !isfinite(lat->m) || lat->m < 0.0) return false;
+    const double ext[4] = {lat->m_y, lat->m_z, lat->m_w, lat->c6};
+    for (double v : ext)
+        if (!isfinite(v) || v < 0.0) return false;
     if (lat->precision != 32 && lat->precision != 64) return false;
     const double sites = (double)lat->n[0] * lat->n[1] * lat->n[2];
     return sites < 4.0e9;
@@ -137,6 +140,10 @@ static FlowArgs make_args(const skyrme_lattice &lat, const skyrme_state &st, dou
     for (int i = 0; i < 3; ++i) a.n[i] = lat.n[i];
     a.h = lat.h;
     a.m = lat.m;
+    a.my = lat.m_y;
+    a.mz = lat.m_z;
+    a.mw = lat.m_w;
+    a.c6 = lat.c6;
     a.dt = dt;
     a.mode = mode;
     return a;
@@ -164,6 +171,7 @@ static void fill_report(const Ctrl &c, skyrme_report *r)
     r->fixups = c.fixups;
     r->cur = c.cur;
     r->status = c.status;
+    r->E6 = c.e6_last;
 }
 
 extern "C" {
@@ -240,7 +248,8 @@ skyrme_status skyrme_load_field(const skyrme_lattice *lat, skyrme_state *st, voi
 static skyrme_status launch_iterations(const skyrme_lattice &lat, const FlowArgs &a, int nsteps,
                                        cudaStream_t s)
 {
-    const bool fast = lat.precision == 32 && f32_fast_path_available(lat);
+    // the streaming FP32 kernel implements the standard model only
+    const bool fast = lat.precision == 32 && !lattice_extended(lat) && f32_fast_path_available(lat);
     for (int k = 0; k < nsteps; ++k) {
         if (fast) CK(launch_step_f32_fast(lat, a, s), "step kernel (fp32)");
         else CK(launch_step(lat, a, s), "step kernel");
@@ -452,12 +461,30 @@ skyrme_status skyrme_virial(const skyrme_lattice *lat, skyrme_state *st, double 
     return rc;
 }
 
+skyrme_status skyrme_sextic_energy(const skyrme_lattice *lat, skyrme_state *st, double *E6,
+                                   void *stream)
+{
+    if (!E6) return SKYRME_EINVAL;
+    skyrme_status rc = check_state(lat, st);
+    if (rc != SKYRME_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    FlowArgs a = make_args(*lat, *st, 0.0, MODE_ARRESTED);
+    CK(launch_energy(*lat, a, s), "energy kernel");
+    Ctrl c;
+    rc = copy_ctrl(*st, &c, s);
+    if (rc != SKYRME_OK) return rc;
+    *E6 = c.e6_energy;
+    return isfinite(*E6) ? SKYRME_OK : SKYRME_ENONFINITE;
+}
+
 skyrme_status skyrme_observables(const skyrme_lattice *lat, skyrme_state *st,
                                  skyrme_observables_t *out, void *stream)
 {
     skyrme_status rc = check_state(lat, st);
     if (rc != SKYRME_OK) return rc;
     if (!out) return SKYRME_EINVAL;
+    // Section 5 gives the currents and the stress tensor of the standard model
+    if (lattice_extended(*lat)) return SKYRME_EUNSUPPORTED;
     const ScratchLayout L = scratch_layout(*lat);
     if (L.total - L.energy_off < observables_parts_bytes()) return SKYRME_ENOMEM;
     FlowArgs a = make_args(*lat, *st, 0.0, MODE_ARRESTED);

@@ -40,7 +40,8 @@ static_assert(sizeof(StaticHeader) <= kStaticHeaderBytes, "header must fit");
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_energy_static(const vec4_t<T> *__restrict__ phi, int n0,
-                                                       int n1, int n2, T inv_h, T m2, double h3,
+                                                       int n1, int n2, T inv_h, T m2,
+                                                       ExtModel<T> ext, bool extended, double h3,
                                                        unsigned char *scratch)
 {
     StaticHeader *hdr = reinterpret_cast<StaticHeader *>(scratch);
@@ -48,7 +49,7 @@ __global__ void __launch_bounds__(256) k_energy_static(const vec4_t<T> *__restri
     const int x = 2 + blockIdx.x;
     const int iy = n1 - 4, iz = n2 - 4;
     const size_t sy = (size_t)n2, sx = (size_t)n1 * n2;
-    double acc[4] = {0, 0, 0, 0};
+    double acc[5] = {0, 0, 0, 0, 0};
     for (int i = threadIdx.x; i < iy * iz; i += blockDim.x) {
         const int y = 2 + i / iz, z = 2 + i % iz;
         const size_t s = (size_t)x * sx + (size_t)y * sy + z;
@@ -88,32 +89,39 @@ __global__ void __launch_bounds__(256) k_energy_static(const vec4_t<T> *__restri
                       (r0[2] * r1[3] - r1[2] * r0[3]) * (r2[0] * r3[1] - r3[0] * r2[1]);
         acc[0] += (double)tra;
         acc[1] += (double)(T(0.5) * (tra * tra - sq));
-        acc[2] += (double)(T(2) * m2 * (T(1) - c.x));
+        T e0 = T(2) * m2 * (T(1) - c.x);
+        if (extended) {
+            // Section 7.8 potentials and the sextic term c6 4 pi^4 (B0)^2 = c6 det^2
+            const T u = T(1) - c.x;
+            e0 += ext.my2 * (T(1) - c.x * c.x) + ext.mz2 * u * u + T(0.5) * ext.mw2 * u * u * u * u;
+            acc[4] += (double)(ext.c6 * det * det);
+        }
+        acc[2] += (double)e0;
         acc[3] += (double)det;
     }
-    __shared__ double red[4 * 8];
+    __shared__ double red[5 * 8];
     __shared__ int s_last;
-    double tot[4];
-    block_reduce<4, -1>(acc, red, tot);
+    double tot[5];
+    block_reduce<5, -1>(acc, red, tot);
     if (threadIdx.x == 0) {
         double *rec = records + (size_t)blockIdx.x * kPartialDoubles;
-        for (int q = 0; q < 4; ++q) rec[q] = tot[q];
+        for (int q = 0; q < 5; ++q) rec[q] = tot[q];
         __threadfence();
         s_last = (atomicAdd(&hdr->counter, 1u) == gridDim.x - 1);
     }
     __syncthreads();
     if (!s_last || threadIdx.x != 0) return;
     __threadfence();
-    double sum[4] = {0, 0, 0, 0};
+    double sum[5] = {0, 0, 0, 0, 0};
     for (unsigned int b = 0; b < gridDim.x; ++b)
-        for (int q = 0; q < 4; ++q) sum[q] += __ldcg(records + (size_t)b * kPartialDoubles + q);
-    const double E2 = h3 * sum[0], E4 = h3 * sum[1], E0 = h3 * sum[2];
-    hdr->result[0] = E2 + E4 + E0;
+        for (int q = 0; q < 5; ++q) sum[q] += __ldcg(records + (size_t)b * kPartialDoubles + q);
+    const double E2 = h3 * sum[0], E4 = h3 * sum[1], E0 = h3 * sum[2], E6 = h3 * sum[4];
+    hdr->result[0] = E2 + E4 + E0 + E6;
     hdr->result[1] = E2;
     hdr->result[2] = E4;
     hdr->result[3] = E0;
     hdr->result[4] = h3 * sum[3] * -0.050660591821168885;  // b = -det / (2 pi^2)
-    hdr->result[5] = -E2 + E4 - 3.0 * E0;
+    hdr->result[5] = -E2 + E4 - 3.0 * E0 + 3.0 * E6;
     hdr->counter = 0;
 }
 
@@ -149,6 +157,9 @@ extern "C" skyrme_status skyrme_energy_static(const skyrme_lattice *lat, const v
     for (int i = 0; i < 3; ++i)
         if (lat->n[i] < 5 || lat->n[i] > 4096) return SKYRME_EINVAL;
     if (!(lat->h > 0.0) || (lat->precision != 32 && lat->precision != 64)) return SKYRME_EINVAL;
+    const double coef[5] = {lat->m, lat->m_y, lat->m_z, lat->m_w, lat->c6};
+    for (double v : coef)
+        if (!isfinite(v) || v < 0.0) return SKYRME_EINVAL;
     // one partial record per interior x-plane must fit the static scratch
     if (lat->n[0] - 4 > kStaticMaxPlanes) return SKYRME_EINVAL;
     const size_t align = lat->precision == 64 ? 32 : 16;
@@ -164,14 +175,20 @@ extern "C" skyrme_status skyrme_energy_static(const skyrme_lattice *lat, const v
     const double h = lat->h;
     const unsigned grid = (unsigned)(lat->n[0] - 4);
     unsigned char *sp = static_cast<unsigned char *>(scratch);
-    if (lat->precision == 64)
+    const bool ext = lattice_extended(*lat);
+    if (lat->precision == 64) {
+        const ExtModel<double> x{lat->m_y * lat->m_y, lat->m_z * lat->m_z, lat->m_w * lat->m_w,
+                                 lat->c6};
         k_energy_static<double><<<grid, 256, 0, s>>>(static_cast<const dvec4 *>(phi), lat->n[0],
                                                      lat->n[1], lat->n[2], 1.0 / h,
-                                                     lat->m * lat->m, h * h * h, sp);
-    else
+                                                     lat->m * lat->m, x, ext, h * h * h, sp);
+    } else {
+        const ExtModel<float> x{(float)(lat->m_y * lat->m_y), (float)(lat->m_z * lat->m_z),
+                                (float)(lat->m_w * lat->m_w), (float)lat->c6};
         k_energy_static<float><<<grid, 256, 0, s>>>(static_cast<const float4 *>(phi), lat->n[0],
                                                     lat->n[1], lat->n[2], (float)(1.0 / h),
-                                                    (float)(lat->m * lat->m), h * h * h, sp);
+                                                    (float)(lat->m * lat->m), x, ext, h * h * h, sp);
+    }
     if (cudaGetLastError() != cudaSuccess) return SKYRME_ECUDA;
     double res[8];
     if (cudaMemcpyAsync(res, sp + offsetof(StaticHeader, result), 6 * sizeof(double),

@@ -1157,6 +1157,10 @@ skyrme_status skyrme_batch_create(int ninst, const skyrme_lattice *lats, skyrme_
         if (!state_ok_for_batch(&lats[i], &states[i])) return SKYRME_EINVAL;
         if (!(dt[i] > 0.0)) return SKYRME_EINVAL;
     }
+    // the streaming kernel implements the standard model only (Section 7.8
+    // extensions run on the single-lattice tile kernels)
+    for (int i = 0; i < ninst; ++i)
+        if (lattice_extended(lats[i])) return SKYRME_EUNSUPPORTED;
     if (!f32_fast_path_available(lats[0])) return SKYRME_EUNSUPPORTED;
     skyrme_batch *b = new skyrme_batch();
     b->ninst = ninst;

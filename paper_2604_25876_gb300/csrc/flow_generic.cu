@@ -35,6 +35,7 @@ template <typename T> struct FlowParams {
     double *parts;
     int n0, n1, n2;
     T inv_h, inv_h2, m2, dt;
+    ExtModel<T> ext;  // Section 7.8 extension terms (used by EXT instantiations)
     T w1, w2;      // first-derivative weights / h
     T v1, v2, v0;  // second-derivative weights / h^2
     double h3;
@@ -169,15 +170,17 @@ __device__ __forceinline__ void normalise_store(vec4_t<T> *dst, const T t[4])
     store4<T>(dst, make4<T>(t[0] * r, t[1] * r, t[2] * r, t[3] * r));
 }
 
-// Per-CTA partial record + last-CTA finish.
-template <typename T>
-__device__ __forceinline__ void reduce_and_finish(const FlowParams<T> &p, double (&acc)[6],
+// Per-CTA partial record + last-CTA finish.  acc = {e2, e4, e0, b, |F|^2,
+// |F|^2 (max), e6}; the sextic sum is reduced only when EXT.
+template <typename T, bool EXT>
+__device__ __forceinline__ void reduce_and_finish(const FlowParams<T> &p, double (&acc)[7],
                                                   bool energy_only, int pred)
 {
     __shared__ double red[8 * (GTHREADS / 32)];
     __shared__ int s_last;
-    double tot6[6];
-    block_reduce<6, 5>(acc, red, tot6);
+    constexpr int NQ = EXT ? 7 : 6;
+    double tot6[NQ];
+    block_reduce<NQ, 5>(*reinterpret_cast<double(*)[NQ]>(acc), red, tot6);
     const int nblocks = gridDim.x * gridDim.y * gridDim.z;
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
@@ -186,7 +189,7 @@ __device__ __forceinline__ void reduce_and_finish(const FlowParams<T> &p, double
 #pragma unroll
         for (int q = 0; q < 6; ++q) rec[q] = tot6[q];
         rec[6] = 0.0;
-        rec[7] = 0.0;
+        rec[7] = EXT ? tot6[NQ - 1] : 0.0;
         __threadfence();
         unsigned int *ctr = energy_only ? &p.ctrl->edone : &p.ctrl->done;
         const unsigned int t = atomicAdd(ctr, 1u);
@@ -203,12 +206,14 @@ __device__ __forceinline__ void reduce_and_finish(const FlowParams<T> &p, double
         if (energy_only) {
             Ctrl *c = p.ctrl;
             const double E2 = p.h3 * tot[0], E4 = p.h3 * tot[1], E0 = p.h3 * tot[2];
-            c->energy[0] = E2 + E4 + E0;
+            const double E6 = p.h3 * tot[7];
+            c->energy[0] = E2 + E4 + E0 + E6;
             c->energy[1] = E2;
             c->energy[2] = E4;
             c->energy[3] = E0;
             c->energy[4] = p.h3 * tot[3];
-            c->energy[5] = -E2 + E4 - 3.0 * E0;
+            c->energy[5] = -E2 + E4 - 3.0 * E0 + 3.0 * E6;
+            c->e6_energy = E6;
             c->energy[6] = sqrt(tot[5]);
             c->energy[7] = sqrt(tot[4] / nsites);
             if (!(isfinite(c->energy[0]) && isfinite(c->energy[4]))) c->status = DEV_NONFINITE;
@@ -219,8 +224,9 @@ __device__ __forceinline__ void reduce_and_finish(const FlowParams<T> &p, double
     }
 }
 
-// kind 0: fused step; kind 1: energy only; kind 2: per-site dump
-template <typename T, int KIND>
+// kind 0: fused step; kind 1: energy only; kind 2: per-site dump.
+// EXT: the Section 7.8 extension terms are included.
+template <typename T, int KIND, bool EXT>
 __global__ void __launch_bounds__(GTHREADS) k_tile(FlowParams<T> p, vec4_t<T> *fout,
                                                    vec4_t<T> *dout)
 {
@@ -244,11 +250,12 @@ __global__ void __launch_bounds__(GTHREADS) k_tile(FlowParams<T> p, vec4_t<T> *f
     const int lz = threadIdx.x, ly = threadIdx.y, lx = threadIdx.z;
     const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
     const bool valid = (x <= p.n0 - 3) && (y <= p.n1 - 3) && (z <= p.n2 - 3);
-    double acc[6] = {0, 0, 0, 0, 0, 0};
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
     if (valid) {
-        T ph[4], d1[3][4], d2[3][4], dm[3][4], F[4], dens[4];
+        T ph[4], d1[3][4], d2[3][4], dm[3][4], F[4], dens[4], e6 = T(0);
         tile_derivatives<T>(tile, dxs, dys, lx, ly, lz, p, ph, d1, d2, dm);
-        site_physics<T>(ph, d1, d2, dm, p.m2, F, dens);
+        site_physics<T, EXT>(ph, d1, d2, dm, p.m2, F, dens, &p.ext, &e6);
+        acc[6] = (double)e6;
         const size_t s = site_index(x, y, z, p.n1, p.n2);
         if (KIND == 0) {
             T t[4];
@@ -281,7 +288,7 @@ __global__ void __launch_bounds__(GTHREADS) k_tile(FlowParams<T> p, vec4_t<T> *f
         acc[5] = f2;
     }
     if (KIND == 2) return;
-    reduce_and_finish<T>(p, acc, KIND == 1, pred);
+    reduce_and_finish<T, EXT>(p, acc, KIND == 1, pred);
 }
 
 // Pointwise correction of a mispredicted arrest decision: the step ran with
@@ -372,6 +379,8 @@ __global__ void k_reset_ctrl(Ctrl *c)
         c->hist = 0;
         for (int i = 0; i < 16; ++i) c->pht[i] = 1;  // weakly "no arrest"
         c->until_start = 0;
+        c->e6_last = 0.0;
+        c->e6_energy = 0.0;
     }
 }
 
@@ -441,27 +450,39 @@ template <typename T> static FlowParams<T> make_params(const FlowArgs &a, double
     p.v2 = T(-1.0 / 12.0 * ih2);
     p.v0 = T(-2.5 * ih2);
     p.m2 = T(a.m * a.m);
+    p.ext.my2 = T(a.my * a.my);
+    p.ext.mz2 = T(a.mz * a.mz);
+    p.ext.mw2 = T(a.mw * a.mw);
+    p.ext.c6 = T(a.c6);
     p.dt = T(a.dt);
     p.h3 = a.h * a.h * a.h;
     p.mode = a.mode;
     return p;
 }
 
-template <typename T, int KIND>
-static cudaError_t launch_tile(const skyrme_lattice &lat, const FlowParams<T> &p, vec4_t<T> *fo,
-                               vec4_t<T> *dout, cudaStream_t s)
+template <typename T, int KIND, bool EXT>
+static cudaError_t launch_tile_model(const skyrme_lattice &lat, const FlowParams<T> &p,
+                                     vec4_t<T> *fo, vec4_t<T> *dout, cudaStream_t s)
 {
     const TileGeom g = tile_geometry(lat);
     static thread_local bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_tile<T, KIND>,
+        cudaError_t e = cudaFuncSetAttribute(k_tile<T, KIND, EXT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)tile_smem_bytes<T>());
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    k_tile<T, KIND><<<g.grid, g.block, g.smem, s>>>(p, fo, dout);
+    k_tile<T, KIND, EXT><<<g.grid, g.block, g.smem, s>>>(p, fo, dout);
     return cudaGetLastError();
+}
+
+template <typename T, int KIND>
+static cudaError_t launch_tile(const skyrme_lattice &lat, const FlowParams<T> &p, vec4_t<T> *fo,
+                               vec4_t<T> *dout, cudaStream_t s)
+{
+    return lattice_extended(lat) ? launch_tile_model<T, KIND, true>(lat, p, fo, dout, s)
+                                 : launch_tile_model<T, KIND, false>(lat, p, fo, dout, s);
 }
 
 cudaError_t launch_step(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s)

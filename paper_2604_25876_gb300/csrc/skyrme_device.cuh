@@ -69,13 +69,14 @@ struct Ctrl {
     int pad_i;
     unsigned char pht[16];  // 2-bit saturating counters indexed by hist
     long long until_start;  // steps when a run-to-tolerance graph launch began
-    double pad[2];
+    double e6_last;         // sextic energy of the latest iteration's start field
+    double e6_energy;       // sextic energy of skyrme_energy
 };
 static_assert(sizeof(Ctrl) <= 512, "control block must fit its 512-byte slot");
 static_assert(offsetof(Ctrl, pht) % 16 == 0, "pht is read as one 16-byte word");
 
 constexpr int kCtrlBytes = 512;
-constexpr int kPartialDoubles = 8;  // per CTA: e2, e4, e0, b, sum|F|^2, max|F|^2, nsites, pad
+constexpr int kPartialDoubles = 8;  // per CTA: e2, e4, e0, b, sum|F|^2, max|F|^2, nsites, e6
 
 enum Mode { MODE_NEWTON = 0, MODE_ARRESTED = 1, MODE_GRADIENT = 2 };
 enum DevStatus { DEV_OK = 0, DEV_NONFINITE = 4, DEV_TIMEOUT = 5 };
@@ -104,13 +105,75 @@ __device__ __forceinline__ T fd2(T m2v, T m1v, T c, T p1v, T p2v)
     return W<T>::s1 * (p1v + m1v) + W<T>::s2 * (p2v + m2v) + W<T>::s0 * c;
 }
 
+// ------------------------------------------------------ extension models
+// Section 7.8 options beyond the standard pion mass: squared masses of the
+// modified pion, loosely and lightly bound potentials and the sextic
+// coefficient.
+template <typename T> struct ExtModel {
+    T my2, mz2, mw2, c6;
+};
+
+// n with n . x = det[x; a; b; c] (rows), by 2x2 minors of (b, c).
+template <typename T>
+__device__ __forceinline__ void cross3(const T a[4], const T b[4], const T c[4], T n[4])
+{
+    const T m01 = b[0] * c[1] - b[1] * c[0], m02 = b[0] * c[2] - b[2] * c[0];
+    const T m03 = b[0] * c[3] - b[3] * c[0], m12 = b[1] * c[2] - b[2] * c[1];
+    const T m13 = b[1] * c[3] - b[3] * c[1], m23 = b[2] * c[3] - b[3] * c[2];
+    n[0] = a[1] * m23 - a[2] * m13 + a[3] * m12;
+    n[1] = a[2] * m03 - a[0] * m23 - a[3] * m02;
+    n[2] = a[0] * m13 - a[1] * m03 + a[3] * m01;
+    n[3] = a[1] * m02 - a[0] * m12 - a[2] * m01;
+}
+
+// Adds the extension terms to the Euler-Lagrange gradient G (before the
+// tangent projection); returns their potential density in e0x and the sextic
+// density in e6.
+//   potentials: d/dphi^0 of m_y^2 (1 - phi0^2) + m_z^2 u^2 + m_w^2 u^4 / 2, u = 1 - phi0;
+//   sextic, with D = det[phi, u, v, w] (u, v, w = d_x, d_y, d_z phi) and
+//   e6 = c6 4 pi^4 (B0)^2 = c6 D^2: the Euler-Lagrange operator of c6 D^2 is
+//     2 c6 [ 4 D P - sum_i (d_i D) Q_i ],  P = dD/dphi, Q_i = dD/d(d_i phi),
+//   d_i D = sum_j Q_j . d_i d_j phi.  The 4 D P collects D P and the divergence
+//   of the cofactors, sum_i d_i Q_i = -3 P (the d_i d_j phi parts cancel in
+//   pairs because d_i d_j = d_j d_i on the lattice too).
+template <typename T>
+__device__ __forceinline__ void extension_terms(const T phi[4], const T d1[3][4], const T d2[3][4],
+                                                const T dm[3][4], const ExtModel<T> &x, T G[4],
+                                                T &e0x, T &e6)
+{
+    const T u = T(1) - phi[0];
+    const T u2 = u * u;
+    G[0] -= T(2) * (x.my2 * phi[0] + x.mz2 * u + x.mw2 * u2 * u);
+    e0x = x.my2 * (T(1) - phi[0] * phi[0]) + x.mz2 * u2 + T(0.5) * x.mw2 * u2 * u2;
+    T P[4], Q0[4], Q1[4], Q2[4];
+    cross3<T>(d1[0], d1[1], d1[2], P);
+    cross3<T>(phi, d1[1], d1[2], Q0);
+    cross3<T>(phi, d1[0], d1[2], Q1);
+    cross3<T>(phi, d1[0], d1[1], Q2);
+#pragma unroll
+    for (int A = 0; A < 4; ++A) Q0[A] = -Q0[A], Q2[A] = -Q2[A];
+    auto dot = [](const T *a, const T *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2] + a[3] * b[3]; };
+    const T D = dot(phi, P);
+    const T dD0 = dot(Q0, d2[0]) + dot(Q1, dm[0]) + dot(Q2, dm[1]);
+    const T dD1 = dot(Q0, dm[0]) + dot(Q1, d2[1]) + dot(Q2, dm[2]);
+    const T dD2 = dot(Q0, dm[1]) + dot(Q1, dm[2]) + dot(Q2, d2[2]);
+    const T two_c6 = T(2) * x.c6, four_D = T(4) * D;
+#pragma unroll
+    for (int A = 0; A < 4; ++A)
+        G[A] += two_c6 * (four_D * P[A] - dD0 * Q0[A] - dD1 * Q1[A] - dD2 * Q2[A]);
+    e6 = x.c6 * D * D;
+}
+
 // ------------------------------------------------------------ site physics
 // Inputs: phi (4), first derivatives d1[i][A], second derivatives d2[i][A]
 // (d_ii) and mixed dm[p][A] for p = xy, xz, yz, all already scaled by 1/h, 1/h^2.
-// Outputs: tangent force F (4) and densities {e2, e4, e0, b}.
-template <typename T>
+// Outputs: tangent force F (4) and densities {e2, e4, e0, b}; with EXT the
+// extension terms of `ext` are included (e0 then holds the whole potential)
+// and the sextic density goes to e6.
+template <typename T, bool EXT = false>
 __device__ __forceinline__ void site_physics(const T phi[4], const T d1[3][4], const T d2[3][4],
-                                             const T dm[3][4], T m2, T F[4], T dens[4])
+                                             const T dm[3][4], T m2, T F[4], T dens[4],
+                                             const ExtModel<T> *ext = nullptr, T *e6 = nullptr)
 {
     auto dot = [](const T *a, const T *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2] + a[3] * b[3]; };
     const T a00 = dot(d1[0], d1[0]), a11 = dot(d1[1], d1[1]), a22 = dot(d1[2], d1[2]);
@@ -138,6 +201,8 @@ __device__ __forceinline__ void site_physics(const T phi[4], const T d1[3][4], c
         G[A] = T(-2) * brace;
     }
     G[0] -= T(2) * m2;
+    T e0x = T(0);
+    if constexpr (EXT) extension_terms<T>(phi, d1, d2, dm, *ext, G, e0x, *e6);
     const T Gphi = G[0] * phi[0] + G[1] * phi[1] + G[2] * phi[2] + G[3] * phi[3];
 #pragma unroll
     for (int A = 0; A < 4; ++A) F[A] = Gphi * phi[A] - G[A];
@@ -146,6 +211,7 @@ __device__ __forceinline__ void site_physics(const T phi[4], const T d1[3][4], c
     const T sq = a00 * a00 + a11 * a11 + a22 * a22 + T(2) * (a01 * a01 + a02 * a02 + a12 * a12);
     dens[1] = T(0.5) * (tra * tra - sq);
     dens[2] = T(2) * m2 * (T(1) - phi[0]);
+    if constexpr (EXT) dens[2] += e0x;
     // b = -(1/2 pi^2) det[phi, d_x phi, d_y phi, d_z phi] (Laplace expansion in 2x2 minors)
     const T *r0 = phi, *r1 = d1[0], *r2 = d1[1], *r3 = d1[2];
     const T s0 = r0[0] * r1[1] - r1[0] * r0[1];
@@ -269,8 +335,8 @@ __device__ __forceinline__ void reduce_partials(const double *parts, int nparts,
 __device__ __forceinline__ void finish_step(Ctrl *c, const double (&tot)[kPartialDoubles],
                                             double h3, int mode, int pred)
 {
-    const double E2 = h3 * tot[0], E4 = h3 * tot[1], E0 = h3 * tot[2];
-    const double E = E2 + E4 + E0;
+    const double E2 = h3 * tot[0], E4 = h3 * tot[1], E0 = h3 * tot[2], E6 = h3 * tot[7];
+    const double E = E2 + E4 + E0 + E6;
     const double B = h3 * tot[3];
     const double delta = sqrt(tot[5]);
     const double rms = tot[6] > 0.0 ? sqrt(tot[4] / tot[6]) : 0.0;
@@ -300,7 +366,8 @@ __device__ __forceinline__ void finish_step(Ctrl *c, const double (&tot)[kPartia
     c->last[2] = E4;
     c->last[3] = E0;
     c->last[4] = B;
-    c->last[5] = -E2 + E4 - 3.0 * E0;
+    c->last[5] = -E2 + E4 - 3.0 * E0 + 3.0 * E6;
+    c->e6_last = E6;
     c->last[6] = delta;
     c->last[7] = rms;
     if (!(isfinite(E) && isfinite(B) && isfinite(tot[4]))) c->status = DEV_NONFINITE;

@@ -38,8 +38,15 @@ struct FlowArgs {
     double *energy_parts;
     int n[3];
     double h, m, dt;
+    double my, mz, mw, c6;  // Section 7.8 extension coefficients
     int mode;
 };
+
+// A lattice with any Section 7.8 extension term switched on.
+inline bool lattice_extended(const skyrme_lattice &lat)
+{
+    return lat.m_y != 0.0 || lat.m_z != 0.0 || lat.m_w != 0.0 || lat.c6 != 0.0;
+}
 
 // Kernels (asynchronous, return the launch error)
 cudaError_t launch_step(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s);

@@ -36,7 +36,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_abi_version_and_status_strings():
     lib = sk.load()
-    assert lib.skyrme_abi_version() == 1
+    assert lib.skyrme_abi_version() == 2
     assert lib.skyrme_status_string(0) == b"ok"
     assert lib.skyrme_status_string(4) == b"non-finite value detected"
 
@@ -164,3 +164,34 @@ def test_render_rejects_bad_arguments_without_cuda():
         assert lib.skyrme_render(ctypes.byref(lat), None, ctypes.byref(p), vol, need, rgba, None) == 1
         assert lib.skyrme_render(ctypes.byref(lat), ctypes.byref(st), ctypes.byref(p), vol, need - 1,
                                  rgba, None) == 2
+
+
+def test_extension_coefficients_are_validated_and_gated_without_cuda():
+    lib = sk.load()
+    base = dict(n=(16, 16, 16), h=0.2, m=1.0, precision=32)
+    ok = sk.Lattice(**base, m_y=0.5, m_z=0.3, m_w=0.2, c6=0.4)
+    assert ok.extended and not sk.Lattice(**base).extended
+    c = ok.c()
+    assert lib.skyrme_scratch_bytes(ctypes.byref(c)) > 0
+    for bad in (dict(m_y=-0.1), dict(m_z=float("nan")), dict(m_w=float("inf")), dict(c6=-1.0)):
+        c = sk.Lattice(**base, **bad).c()
+        assert lib.skyrme_scratch_bytes(ctypes.byref(c)) == 0, bad
+        out = (ctypes.c_double * 6)()
+        assert lib.skyrme_energy_static(ctypes.byref(c), ctypes.c_void_p(0x10000), out, None) == 1
+    st = sk.c_state((ctypes.c_void_p * 2)(0x10000, 0x20000), (ctypes.c_void_p * 2)(0x30000, 0x40000),
+                    ctypes.c_void_p(0x50000), ctypes.c_size_t(1 << 30))
+    c = ok.c()
+    # Section 5 observables are those of the standard model
+    assert lib.skyrme_observables(ctypes.byref(c), ctypes.byref(st),
+                                  ctypes.byref(sk.c_observables()), None) == 6
+    # the batched streaming kernel implements the standard model only
+    lats = (sk.c_lattice * 1)(c)
+    sts = (sk.c_state * 1)(st)
+    dts = (ctypes.c_double * 1)(0.01)
+    out = ctypes.c_void_p()
+    need = lib.skyrme_batch_scratch_bytes(1, lats)
+    assert lib.skyrme_batch_create(1, lats, sts, dts, 1, ctypes.c_void_p(0x100000), need,
+                                   ctypes.byref(out)) == 6
+    assert not out.value
+    # a null result pointer
+    assert lib.skyrme_sextic_energy(ctypes.byref(c), ctypes.byref(st), None, None) == 1
