@@ -41,6 +41,7 @@ BYTES_PER_SITE_F64 = 128
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0     # GB/s, used only when the measured peaks file is absent
 FLOPS_PER_SITE = 590      # algorithmic FP operations per site-update (FMA = 2)
+FLOPS_PER_SITE_EXT = 860  # with the Section 7.8 potentials and sextic term
 GRAPH_CHUNK = 250         # iterations per captured CUDA graph
 
 
@@ -90,6 +91,28 @@ def reduce_over_ranks(local_ms: float, local_units: float, ws: int):
     return float(t.item()), float(u.item())
 
 
+def lattice_of(sk, wl, prec):
+    return sk.Lattice(wl.n, wl.h, wl.m, prec, m_y=wl.m_y, m_z=wl.m_z, m_w=wl.m_w, c6=wl.c6)
+
+
+def oracle_mass(oracle, wl):
+    """The oracle's model argument: the pion mass, or the extension model."""
+    return oracle.Model(wl.m, wl.m_y, wl.m_z, wl.m_w, wl.c6) if wl.extended else wl.m
+
+
+def flops_per_site(wl):
+    return FLOPS_PER_SITE_EXT if wl.extended else FLOPS_PER_SITE
+
+
+def step_kernel_key(wl, prec):
+    """Name of the step kernel a workload runs on (the traffic record key):
+    the FP32 streaming kernel for the standard model, the tile kernels for
+    FP64 and for extended models."""
+    if prec == 32 and not wl.extended:
+        return f"step_f32_{wl.name}"
+    return f"step_tile_f{prec}_{wl.name}" if wl.extended else f"step_f64_{wl.name}"
+
+
 def l2_note(wl):
     mb = 4 * (16 if wl.precision == 32 else 32) * int(np.prod(wl.n)) / 1e6
     rel = "larger than" if mb > 129 else "smaller than"
@@ -102,6 +125,7 @@ def workload_config(wl):
         "lattice": list(wl.n),
         "h": wl.h,
         "m": wl.m,
+        **({"m_y": wl.m_y, "m_z": wl.m_z, "m_w": wl.m_w, "c6": wl.c6} if wl.extended else {}),
         "dt": wl.dt,
         "dt_configured": wl.dt_configured,
         "seed": wl.description,
@@ -169,12 +193,14 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ our kernels
-def kernel_fingerprint(prec: int = 32):
-    """Hash of the sources of the step kernel of one precision: the FP32
-    streaming kernel or the tile kernels (FP64), with their shared header."""
+def kernel_fingerprint(kernel_key: str):
+    """Hash of the sources of a step kernel: the FP32 streaming kernel
+    (keys step_f32_*) or the tile kernels (every other key), with their
+    shared header."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2604_25876_gb300", "csrc")
-    for name in ("flow_f32.cu" if prec == 32 else "flow_generic.cu", "skyrme_device.cuh"):
+    src = "flow_f32.cu" if kernel_key.startswith("step_f32_") else "flow_generic.cu"
+    for name in (src, "skyrme_device.cuh"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -189,8 +215,7 @@ def recorded_traffic(kernel_key: str, per_launch_sites: int):
             rec = json.load(f).get(kernel_key)
     except Exception:
         return None
-    prec = 64 if kernel_key.startswith("step_f64") else 32
-    if not rec or rec.get("fingerprint") != kernel_fingerprint(prec):
+    if not rec or rec.get("fingerprint") != kernel_fingerprint(kernel_key):
         return None
     scale = per_launch_sites / float(rec["sites"])
     return float(rec["dram_bytes_per_launch"]) * scale
@@ -206,7 +231,7 @@ def run_ours(args, ws, rank, local):
     sk.load()
     wl = workloads.ALL[args.workload]()
     prec = wl.precision
-    lat = sk.Lattice(wl.n, wl.h, wl.m, prec)
+    lat = lattice_of(sk, wl, prec)
     st = sk.State(lat, dev)
     seed = sk.Seed.from_spec(wl.seed)
     sk.init_field(lat, seed, st)
@@ -267,25 +292,27 @@ def run_ours(args, ws, rank, local):
     # the roofline is the slower of the HBM and ALU bounds (site-updates/s)
     bytes_site = BYTES_PER_SITE_F32 * (1 if prec == 32 else 2)
     alu_tflops = alu["fp32_tflops"] if prec == 32 else alu["fp64_tflops"]
+    fps = flops_per_site(wl)
+    key = step_kernel_key(wl, prec)
     hbm_bound = hbm * 1e9 / bytes_site / 1e9
-    alu_bound = alu_tflops * 1e12 / FLOPS_PER_SITE / 1e9
+    alu_bound = alu_tflops * 1e12 / fps / 1e9
     bounds = {"hbm_bound_gsites": round(hbm_bound, 2), "alu_bound_gsites": round(alu_bound, 3),
-              "alu_peaks": alu, "algorithmic_flops_per_site": FLOPS_PER_SITE,
-              "algorithmic_bytes_per_site": bytes_site}
+              "alu_peaks": alu, "algorithmic_flops_per_site": fps,
+              "algorithmic_bytes_per_site": bytes_site, "kernel": key}
     if hbm_bound <= alu_bound:
         achieved = bytes_site * sites / (mean_iter * 1e-3) / 1e9
         roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                     "frac": round(achieved / hbm, 4),
-                    "traffic": recorded_traffic(f"step_f{prec}_{wl.name}", sites),
+                    "traffic": recorded_traffic(key, sites),
                     "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
                     if peak_kind == "measured" else "fallback 6.8 TB/s",
                     "duration": "mean per iteration (step kernel + fix-up check) from CUDA "
                                 "events around each graph replay", **bounds}
     else:
-        tfl = FLOPS_PER_SITE * sites / (mean_iter * 1e-3) / 1e12
+        tfl = fps * sites / (mean_iter * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": round(tfl, 4), "peak": alu_tflops,
                     "unit": "TFLOP/s", "frac": round(tfl / alu_tflops, 4),
-                    "traffic": recorded_traffic(f"step_f{prec}_{wl.name}", sites),
+                    "traffic": recorded_traffic(key, sites),
                     "peak_source": "measured FP%d FMA throughput (skyrme_measure_fma_peak)" % prec,
                     "duration": "mean per iteration (step kernel + fix-up check) from CUDA "
                                 "events around each graph replay", **bounds}
@@ -298,9 +325,10 @@ def run_ours(args, ws, rank, local):
            "gpu_launches": 2 * K, "graph_chunk": chunk, "clocks": clk,
            "flow": {"steps_done": rep["steps"], "arrests": rep["arrests"],
                     "fixups": rep["fixups"], "E": rep["E"], "B": rep["B"],
-                    "virial": rep["virial"], "delta": rep["delta"]}}
+                    "virial": rep["virial"], "delta": rep["delta"],
+                    **({"E6": rep["E6"]} if wl.extended else {})}}
 
-    if not args.no_extras and prec == 32:
+    if not args.no_extras and prec == 32 and not wl.extended:
         out["batched"] = run_batched(sk, torch, dev, ws, rank)
     if rank == 0 and not args.no_extras:
         out["e2e"] = run_e2e(sk, torch, dev, wl, K)
@@ -366,7 +394,7 @@ def run_e2e(sk, torch, dev, wl, K):
     """The same metric through the public API with host buffers: upload the
     seed field from pinned host memory, K flow iterations with the report read
     back, download the final field; all inside the timed region."""
-    lat = sk.Lattice(wl.n, wl.h, wl.m, wl.precision)
+    lat = lattice_of(sk, wl, wl.precision)
     st = sk.State(lat, dev)
     sk.init_field(lat, sk.Seed.from_spec(wl.seed), st)
     host_in = torch.empty(st.phi[0].shape, dtype=lat.dtype, pin_memory=True)
@@ -398,7 +426,7 @@ def run_fp64_compare(sk, torch, dev, wl, nsteps, rep32, fp64_tflops):
     """FP64 GPU flow of the same workload for the same iterations (validated
     against the FP64 oracle by the parity tests): its throughput, its ALU
     roofline and the FP32 energy error relative to it."""
-    lat = sk.Lattice(wl.n, wl.h, wl.m, 64)
+    lat = lattice_of(sk, wl, 64)
     st = sk.State(lat, dev)
     sk.init_field(lat, sk.Seed.from_spec(wl.seed), st)
     stream = torch.cuda.current_stream(dev)
@@ -411,13 +439,13 @@ def run_fp64_compare(sk, torch, dev, wl, nsteps, rep32, fp64_tflops):
     torch.cuda.synchronize(dev)
     ms = a.elapsed_time(b)
     gs = wl.interior_sites * nsteps / (ms * 1e-3) / 1e9
-    tfl = gs * FLOPS_PER_SITE / 1e3
+    tfl = gs * flops_per_site(wl) / 1e3
     return {"value": round(gs, 4), "unit": UNIT, "steps": nsteps,
             "roofline": {"bound": "alu", "achieved": round(tfl, 4),
                          "peak": fp64_tflops, "unit": "TFLOP/s",
                          "frac": round(tfl / fp64_tflops, 4),
                          "peak_source": "measured FP64 FMA throughput (skyrme_measure_fma_peak)",
-                         "algorithmic_flops_per_site": FLOPS_PER_SITE},
+                         "algorithmic_flops_per_site": flops_per_site(wl)},
             "E_fp64": rep["E"],
             "fp32_energy_rel_err": abs(rep32["E"] - rep["E"]) / abs(rep["E"])
             if rep32["steps"] == rep["steps"] else None}
@@ -435,12 +463,13 @@ def run_cpu_baseline(wl, seconds):
         phi = oracle.seed_product(n, wl.h, wl.seed.positions, wl.seed.quaternions,
                                   wl.seed.profile_scale, wl.seed.symmetrise)
     st = oracle.new_state(phi)
+    m = oracle_mass(oracle, wl)
     t = time.perf_counter()
-    oracle.flow(st, wl.h, wl.m, wl.dt, 1)
+    oracle.flow(st, wl.h, m, wl.dt, 1)
     one = time.perf_counter() - t
     steps = max(1, int(seconds / max(one, 1e-6)))
     t = time.perf_counter()
-    oracle.flow(st, wl.h, wl.m, wl.dt, steps)
+    oracle.flow(st, wl.h, m, wl.dt, steps)
     el = time.perf_counter() - t
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": round(wl.interior_sites * steps / el / 1e9, 6), "unit": UNIT,

@@ -66,6 +66,29 @@ __device__ __forceinline__ void load_tile(vec4_t<T> *tile, const vec4_t<T> *phi,
     }
 }
 
+// The same staging with asynchronous copies (cp.async, 16 bytes per site of
+// an FP32 field), committed as one group: the copies of the next tile fly
+// while the current one is computed.
+__device__ __forceinline__ void load_tile_async(float4 *tile, const float4 *phi, int x0, int y0,
+                                                int z0, int n0, int n1, int n2)
+{
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    for (int i = tid; i < GSX * GSY * GSZ; i += GTHREADS) {
+        const int lz = i % GSZ, ly = (i / GSZ) % GSY, lx = i / (GSZ * GSY);
+        const int x = x0 - 2 + lx, y = y0 - 2 + ly, z = z0 - 2 + lz;
+        if (x < n0 && y < n1 && z < n2) {
+            const unsigned dst = static_cast<unsigned>(__cvta_generic_to_shared(tile + i));
+            const size_t src = __cvta_generic_to_global(phi + site_index(x, y, z, n1, n2));
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void wait_tile_async()
+{
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 // Scaled stencils: w1 (p1 - m1) + w2 (p2 - m2) and v1 (p1 + m1) + v2 (p2 + m2) + v0 c
 template <typename T> __device__ __forceinline__ T sd1(T m2v, T m1v, T p1v, T p2v, T w1, T w2)
 {
@@ -90,11 +113,14 @@ __device__ __forceinline__ vec4_t<T> sd1v(const vec4_t<T> &m2v, const vec4_t<T> 
 // mixed derivatives are first-derivative stencils of these (Section 3,
 // reading R1: d_xy = d_y(d_x phi), d_xz = d_z(d_x phi), d_yz = d_z(d_y phi)),
 // which costs a quarter of the FP64 operations of the 16-tap sums.
+// FP32 kernels keep two field tiles, the next one arriving by cp.async.
 constexpr int GDX = GTX * GSY * GSZ;  // entries of d_x phi
 constexpr int GDY = GTX * GTY * GSZ;  // entries of d_y phi
+constexpr int GTILE = GSX * GSY * GSZ;  // entries of one haloed field tile
+template <typename T> constexpr int kTileBufs = sizeof(T) == 4 ? 2 : 1;
 template <typename T> constexpr size_t tile_smem_bytes()
 {
-    return (size_t)(GSX * GSY * GSZ + GDX + GDY) * sizeof(vec4_t<T>);
+    return (size_t)(kTileBufs<T> * GTILE + GDX + GDY) * sizeof(vec4_t<T>);
 }
 
 // Stage d_x phi and d_y phi of the tile (all threads), from the loaded tile.
@@ -224,14 +250,23 @@ __device__ __forceinline__ void reduce_and_finish(const FlowParams<T> &p, double
     }
 }
 
+// Resident 256-thread CTAs per SM the register allocation is sized for:
+// three for FP32 (24 warps to hide the latency of the tile loads), two for the
+// standard FP64 kernels, one for the extended FP64 kernels (bound by the FP64
+// pipe either way).
+template <typename T, bool EXT>
+constexpr int kTileMinBlocks = sizeof(T) == 4 ? 3 : (EXT ? 1 : 2);
+
 // kind 0: fused step; kind 1: energy only; kind 2: per-site dump.
 // EXT: the Section 7.8 extension terms are included.
 template <typename T, int KIND, bool EXT>
-__global__ void __launch_bounds__(GTHREADS) k_tile(FlowParams<T> p, vec4_t<T> *fout,
+__global__ void __launch_bounds__(GTHREADS, kTileMinBlocks<T, EXT>) k_tile(FlowParams<T> p, vec4_t<T> *fout,
                                                    vec4_t<T> *dout)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    vec4_t<T> *tile = reinterpret_cast<vec4_t<T> *>(smem_raw);
+    vec4_t<T> *tiles = reinterpret_cast<vec4_t<T> *>(smem_raw);
+    vec4_t<T> *dxs = tiles + kTileBufs<T> * GTILE;
+    vec4_t<T> *dys = dxs + GDX;
     const int cur = __ldcg(&p.ctrl->cur);
     const int pred = (KIND == 0 && p.mode == MODE_ARRESTED) ? __ldcg(&p.ctrl->pred) : 0;
     // buffers selected by value (a run-time index into the parameter copies it to the stack)
@@ -239,29 +274,65 @@ __global__ void __launch_bounds__(GTHREADS) k_tile(FlowParams<T> p, vec4_t<T> *f
     const vec4_t<T> *vin = cur ? p.vel[1] : p.vel[0];
     vec4_t<T> *phi_out = cur ? p.phi[0] : p.phi[1];
     vec4_t<T> *vel_out = cur ? p.vel[0] : p.vel[1];
-    const int x0 = 2 + blockIdx.z * GTX, y0 = 2 + blockIdx.y * GTY, z0 = 2 + blockIdx.x * GTZ;
-    load_tile<T>(tile, phi, x0, y0, z0, p.n0, p.n1, p.n2);
-    __syncthreads();
-    vec4_t<T> *dxs = tile + GSX * GSY * GSZ;
-    vec4_t<T> *dys = dxs + GDX;
-    stage_first_derivatives<T>(tile, dxs, dys, p.w1, p.w2);
-    __syncthreads();
-
     const int lz = threadIdx.x, ly = threadIdx.y, lx = threadIdx.z;
-    const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
-    const bool valid = (x <= p.n0 - 3) && (y <= p.n1 - 3) && (z <= p.n2 - 3);
+    // persistent CTAs walk the tiles z-fastest, so CTAs in flight share halos in L2
+    const int nz = (p.n2 - 4 + GTZ - 1) / GTZ, ny = (p.n1 - 4 + GTY - 1) / GTY;
+    const int ntiles = nz * ny * ((p.n0 - 4 + GTX - 1) / GTX);
+    // Per-thread sums {e2, e4, e0, b, |F|^2, max |F|^2, e6}.  The FP32 kernels
+    // add in FP32 over at most kFoldTiles tiles and then fold into FP64, so
+    // that the FP64 pipe (1/64 of the FP32 rate) does a few operations per
+    // thread instead of seven per site; FP64 kernels add in FP64 directly.
+    constexpr int kFoldTiles = sizeof(T) == 4 ? 32 : 1;
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    if (valid) {
+    T part[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+    int pending = 0;
+    auto fold = [&]() {
+#pragma unroll
+        for (int q = 0; q < 7; ++q)
+            acc[q] = (q == 5) ? fmax(acc[q], (double)part[q]) : acc[q] + (double)part[q];
+#pragma unroll
+        for (int q = 0; q < 7; ++q) part[q] = T(0);
+        pending = 0;
+    };
+    auto x0_of = [&](int t) { return 2 + (t / (nz * ny)) * GTX; };
+    auto y0_of = [&](int t) { return 2 + ((t / nz) % ny) * GTY; };
+    auto z0_of = [&](int t) { return 2 + (t % nz) * GTZ; };
+    if constexpr (kTileBufs<T> == 2) {
+        if (blockIdx.x < ntiles)
+            load_tile_async(tiles, phi, x0_of(blockIdx.x), y0_of(blockIdx.x), z0_of(blockIdx.x),
+                            p.n0, p.n1, p.n2);
+    }
+    int buf = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, buf ^= (kTileBufs<T> - 1)) {
+        const int x0 = x0_of(t), y0 = y0_of(t), z0 = z0_of(t);
+        vec4_t<T> *tile = tiles + buf * GTILE;
+        if constexpr (kTileBufs<T> == 2) {
+            wait_tile_async();  // this thread's copies of tile t have landed
+            // every thread's copies have landed, and every thread is done with
+            // the other buffer and with the staged derivatives of tile t - grid
+            __syncthreads();
+            const int tn = t + gridDim.x;
+            if (tn < ntiles)
+                load_tile_async(tiles + (buf ^ 1) * GTILE, phi, x0_of(tn), y0_of(tn), z0_of(tn),
+                                p.n0, p.n1, p.n2);
+        } else {
+            __syncthreads();  // the previous tile's readers are done with shared memory
+            load_tile<T>(tile, phi, x0, y0, z0, p.n0, p.n1, p.n2);
+            __syncthreads();
+        }
+        stage_first_derivatives<T>(tile, dxs, dys, p.w1, p.w2);
+        __syncthreads();
+        const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
+        if (!((x <= p.n0 - 3) && (y <= p.n1 - 3) && (z <= p.n2 - 3))) continue;
         T ph[4], d1[3][4], d2[3][4], dm[3][4], F[4], dens[4], e6 = T(0);
         tile_derivatives<T>(tile, dxs, dys, lx, ly, lz, p, ph, d1, d2, dm);
         site_physics<T, EXT>(ph, d1, d2, dm, p.m2, F, dens, &p.ext, &e6);
-        acc[6] = (double)e6;
         const size_t s = site_index(x, y, z, p.n1, p.n2);
         if (KIND == 0) {
-            T t[4];
+            T tv[4];
             if (p.mode == MODE_GRADIENT) {
 #pragma unroll
-                for (int A = 0; A < 4; ++A) t[A] = ph[A] + p.dt * F[A];
+                for (int A = 0; A < 4; ++A) tv[A] = ph[A] + p.dt * F[A];
             } else {
                 T v[4] = {T(0), T(0), T(0), T(0)};
                 if (!pred) {
@@ -271,22 +342,24 @@ __global__ void __launch_bounds__(GTHREADS) k_tile(FlowParams<T> p, vec4_t<T> *f
 #pragma unroll
                 for (int A = 0; A < 4; ++A) {
                     v[A] = v[A] + p.dt * F[A];
-                    t[A] = ph[A] + p.dt * v[A];
+                    tv[A] = ph[A] + p.dt * v[A];
                 }
                 store4<T>(vel_out + s, make4<T>(v[0], v[1], v[2], v[3]));
             }
-            normalise_store<T>(phi_out + s, t);
+            normalise_store<T>(phi_out + s, tv);
         } else if (KIND == 2) {
             if (fout) store4<T>(fout + s, make4<T>(F[0], F[1], F[2], F[3]));
             if (dout) store4<T>(dout + s, make4<T>(dens[0], dens[1], dens[2], dens[3]));
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] = (double)dens[q];
-        const double f2 = (double)F[0] * F[0] + (double)F[1] * F[1] + (double)F[2] * F[2] +
-                          (double)F[3] * F[3];
-        acc[4] = f2;
-        acc[5] = f2;
+        for (int q = 0; q < 4; ++q) part[q] += dens[q];
+        const T f2 = F[0] * F[0] + F[1] * F[1] + F[2] * F[2] + F[3] * F[3];
+        part[4] += f2;
+        part[5] = part[5] > f2 ? part[5] : f2;
+        part[6] += e6;
+        if (++pending == kFoldTiles) fold();
     }
+    if (pending) fold();
     if (KIND == 2) return;
     reduce_and_finish<T, EXT>(p, acc, KIND == 1, pred);
 }
@@ -418,13 +491,19 @@ cudaError_t launch_until_check(void *ctrl, unsigned long long handle, double tol
 }
 
 // ------------------------------------------------------------- launchers
+// The persistent grid of the tile kernels never exceeds kTileGridCap CTAs
+// (the partial-record space of the scratch holds at least that many).
+constexpr int kTileGridCap = 152 * 8;
+
 TileGeom tile_geometry(const skyrme_lattice &lat)
 {
     TileGeom g;
     const int ix = lat.n[0] - 4, iy = lat.n[1] - 4, iz = lat.n[2] - 4;
-    g.grid = dim3((iz + GTZ - 1) / GTZ, (iy + GTY - 1) / GTY, (ix + GTX - 1) / GTX);
+    const long long ntiles = (long long)((iz + GTZ - 1) / GTZ) * ((iy + GTY - 1) / GTY) *
+                             ((ix + GTX - 1) / GTX);
+    g.nblocks = (int)std::min<long long>(ntiles, kTileGridCap);
+    g.grid = dim3(g.nblocks);
     g.block = dim3(GTZ, GTY, GTX);
-    g.nblocks = (int)(g.grid.x * g.grid.y * g.grid.z);
     g.smem = lat.precision == 64 ? tile_smem_bytes<double>() : tile_smem_bytes<float>();
     return g;
 }
@@ -465,15 +544,24 @@ static cudaError_t launch_tile_model(const skyrme_lattice &lat, const FlowParams
                                      vec4_t<T> *fo, vec4_t<T> *dout, cudaStream_t s)
 {
     const TileGeom g = tile_geometry(lat);
-    static thread_local bool attr_set = false;
-    if (!attr_set) {
+    // resident CTAs of this instantiation on the whole GPU (queried once)
+    static thread_local int resident = 0;
+    if (!resident) {
         cudaError_t e = cudaFuncSetAttribute(k_tile<T, KIND, EXT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)tile_smem_bytes<T>());
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        int dev = 0, sms = 0, per_sm = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile<T, KIND, EXT>, GTHREADS,
+                                                          tile_smem_bytes<T>());
+        if (e != cudaSuccess) return e;
+        resident = std::max(1, sms * std::max(1, per_sm));
     }
-    k_tile<T, KIND, EXT><<<g.grid, g.block, g.smem, s>>>(p, fo, dout);
+    const int grid = std::min(g.nblocks, resident);
+    k_tile<T, KIND, EXT><<<grid, g.block, g.smem, s>>>(p, fo, dout);
     return cudaGetLastError();
 }
 

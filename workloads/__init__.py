@@ -50,6 +50,11 @@ class Workload:
     dt_configured: float
     dt: float = 0.0
     description: str = ""
+    # Section 7.8 extension coefficients (0: the standard model)
+    m_y: float = 0.0
+    m_z: float = 0.0
+    m_w: float = 0.0
+    c6: float = 0.0
 
     def __post_init__(self):
         if not self.dt:
@@ -58,6 +63,10 @@ class Workload:
     @property
     def interior_sites(self) -> int:
         return int(np.prod([max(N - 4, 0) for N in self.n]))
+
+    @property
+    def extended(self) -> bool:
+        return any(v != 0.0 for v in (self.m_y, self.m_z, self.m_w, self.c6))
 
 
 def ball_positions(rng: np.random.Generator, count: int, radius: float) -> np.ndarray:
@@ -103,6 +112,15 @@ def b4_cubic_128() -> Workload:
                                 "FP32 bulk with FP64 reductions")
 
 
+def b4_sextic_128() -> Workload:
+    """The 128^3 B=4 workload with the BPS sextic term switched on at the
+    programme's default coefficient c6 = 1 (Section 7.8)."""
+    return Workload("b4_sextic_128", (128, 128, 128), 0.1, 1.0, 5000, 32,
+                    SeedSpec(kind="rational_map", B=4, profile_scale=2.0), 0.02, c6=1.0,
+                    description="B=4 cubic rational map f=pi exp(-r/2), 128^3, h=0.1, m=1, "
+                                "BPS sextic term c6=1, FP32 bulk with FP64 reductions")
+
+
 def b8_cluster_256() -> Workload:
     return Workload("b8_cluster_256", (256, 256, 256), 0.08, 1.0, 20000, 32,
                     cluster_seed(8, 3.0, 8), 0.016,
@@ -131,6 +149,7 @@ def batched_noise(count: int = 64, steps: int = 5000) -> List[Workload]:
 ALL = {
     "b1_hedgehog_48": b1_hedgehog_48,
     "b4_cubic_128": b4_cubic_128,
+    "b4_sextic_128": b4_sextic_128,
     "b8_cluster_256": b8_cluster_256,
     "b32_cluster_512": b32_cluster_512,
 }
