@@ -42,6 +42,11 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0     # GB/s, used only when the measured peaks file is absent
 FLOPS_PER_SITE = 590      # algorithmic FP operations per site-update (FMA = 2)
 FLOPS_PER_SITE_EXT = 860  # with the Section 7.8 potentials and sextic term
+# FP64 operations (FMA = 2) the diagnostic kernels execute, from ncu op
+# counts (dadd + dmul + 2 dfma) on the 128^3 field; each formula is evaluated
+# once per site and pass, so these are their arithmetic:
+OBS_FP64_FLOPS_PER_SITE = 1032          # Section 5 observables: 124 + 908 per interior site
+RENDER_VOLUME_FP64_FLOPS_PER_SITE = 183  # volume record + normalisation, per lattice site
 GRAPH_CHUNK = 250         # iterations per captured CUDA graph
 
 
@@ -334,6 +339,8 @@ def run_ours(args, ws, rank, local):
         out["e2e"] = run_e2e(sk, torch, dev, wl, K)
         if prec == 32:
             out["fp64_gpu"] = run_fp64_compare(sk, torch, dev, wl, K + W, rep, alu["fp64_tflops"])
+        if not wl.extended:
+            out["diagnostics"] = run_diagnostics(sk, torch, dev, wl, alu["fp64_tflops"])
         out["cpu_baseline"] = run_cpu_baseline(wl, args.cpu_seconds)
     return out
 
@@ -449,6 +456,54 @@ def run_fp64_compare(sk, torch, dev, wl, nsteps, rep32, fp64_tflops):
             "E_fp64": rep["E"],
             "fp32_energy_rel_err": abs(rep32["E"] - rep["E"]) / abs(rep["E"])
             if rep32["steps"] == rep["steps"] else None}
+
+
+def run_diagnostics(sk, torch, dev, wl, fp64_tflops, reps=5):
+    """Timings of the Section 5 observables and the Section 6.2 volume render
+    of the workload's field after 200 flow iterations (standard model)."""
+    lat = lattice_of(sk, wl, wl.precision)
+    st = sk.State(lat, dev)
+    sk.init_field(lat, sk.Seed.from_spec(wl.seed), st)
+    sk.flow_step(lat, wl.dt, 200, sk.ARRESTED, st, report=False)
+    sites, nall = wl.interior_sites, int(np.prod(wl.n))
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / reps
+
+    obs_ms = timed(lambda: sk.observables(lat, st))
+    vol = torch.empty(tuple(wl.n) + (4,), dtype=torch.float64, device=dev)
+    vol_ms = timed(lambda: sk.render_volume(lat, st, out=vol))
+    c, s_ = math.cos(0.6), math.sin(0.6)
+    rp = sk.render_params(1024, 768, view=[[c, 0, s_], [0, 1, 0], [-s_, 0, c]], step=0.005)
+    ray_ms = timed(lambda: sk.render_rays(vol, rp))
+    def fp64_roofline(flops, ms, per):
+        tfl = flops / (ms * 1e-3) / 1e12
+        return {"bound": "alu", "achieved": round(tfl, 4), "peak": fp64_tflops,
+                "unit": "TFLOP/s", "frac": round(tfl / fp64_tflops, 4), "fp64_flops_per": per,
+                "peak_source": "measured FP64 FMA throughput (skyrme_measure_fma_peak)"}
+
+    obs = {"ms": round(obs_ms, 4), "gsites": round(sites / (obs_ms * 1e-3) / 1e9, 4),
+           "what": "skyrme_observables: two FP64 passes over the interior, host read-back",
+           "roofline": fp64_roofline(OBS_FP64_FLOPS_PER_SITE * sites, obs_ms,
+                                     f"{OBS_FP64_FLOPS_PER_SITE} per interior site")}
+    return {"observables": obs,
+            "render_volume": {"ms": round(vol_ms, 4),
+                              "roofline": fp64_roofline(RENDER_VOLUME_FP64_FLOPS_PER_SITE * nall,
+                                                        vol_ms,
+                                                        f"{RENDER_VOLUME_FP64_FLOPS_PER_SITE} per "
+                                                        "lattice site")},
+            "render_rays": {"ms": round(ray_ms, 4), "pixels": 1024 * 768, "step": 0.005,
+                            "mpixels_per_s": round(1024 * 768 / (ray_ms * 1e-3) / 1e6, 2)}}
 
 
 def run_cpu_baseline(wl, seconds):
