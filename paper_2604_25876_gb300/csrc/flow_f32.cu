@@ -6,11 +6,13 @@
 // Eq. "Newton_flow", v += dt F, phi = normalise(phi + dt v); Section 2.1
 // densities), organised for GB300:
 //
-//  * persistent CTAs (as many as fit, normally two per SM) split the
-//    (column, x-plane) work of every lattice in the batch evenly.  A column
-//    is a TY x TZ block of interior (y, z) sites; a CTA marches along x
-//    through contiguous runs of planes, crossing from one lattice into the
-//    next.  Each lattice's energy sums close as soon as the CTAs that
+//  * persistent CTAs (as many as fit: one per SM for a single lattice, with
+//    16 x 32 columns) split the (column, x-plane) work of every lattice in
+//    the batch.  A column is a TY x TZ block of interior (y, z) sites; a CTA
+//    marches along x through contiguous runs of planes, crossing from one
+//    lattice into the next.  A batch is split evenly by units; a single
+//    lattice by streamed planes, a run of r centres streaming r + 4 planes,
+//    so that CTAs whose range spans two columns get fewer centres.  Each lattice's energy sums close as soon as the CTAs that
 //    touched it are done (per-lattice arrival counter, last-CTA finish), so
 //    lattices of different sizes need no global barrier.
 //  * each x-plane of the column tile, with its 2-site halo, is streamed into
@@ -80,7 +82,18 @@ struct InstDesc {
     int mode;
 };
 
+// Unit ranges of the CTAs of a single-lattice launch: CTA b streams units
+// [start[b], start[b + 1]).  n = 0 selects the even split of the units.  The
+// host balances the ranges by their plane count (units plus the pipeline
+// fill of every run) rather than by units.
+constexpr int kSplitMax = 256;
+struct CtaSplit {
+    int n;
+    int start[kSplitMax + 1];
+};
+
 // ------------------------------------------------------------- PTX helpers
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -557,8 +570,8 @@ __device__ __forceinline__ void finish_lattice(const InstDesc &D, Ctrl *c, int c
 // the control blocks are left as they were.
 template <int TY, int TZ, bool BATCHED>
 __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
-    k_step_f32(const __grid_constant__ InstDesc one, const InstDesc *__restrict__ table, int ninst,
-               long long total_units, int dry)
+    k_step_f32(const __grid_constant__ InstDesc one, const __grid_constant__ CtaSplit split,
+               const InstDesc *__restrict__ table, int ninst, long long total_units, int dry)
 {
     constexpr int THREADS = TY * TZ;
     constexpr unsigned PLANE_BYTES = (TY + 4) * (TZ + 4) * 16;
@@ -579,8 +592,10 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
     }
     __syncthreads();
 
-    const long long u0 = total_units * blockIdx.x / gridDim.x;
-    const long long u1 = total_units * (blockIdx.x + 1) / gridDim.x;
+    const bool listed = !BATCHED && split.n > 0;
+    const long long u0 = listed ? split.start[blockIdx.x] : total_units * blockIdx.x / gridDim.x;
+    const long long u1 =
+        listed ? split.start[blockIdx.x + 1] : total_units * (blockIdx.x + 1) / gridDim.x;
     int inst = 0;
     if (BATCHED)
         while (inst + 1 < ninst && table[inst + 1].unit_start <= u0) ++inst;
@@ -871,8 +886,8 @@ template <int TY, int TZ, bool B> static void *kernel_ptr()
 }
 
 template <int TY, int TZ, bool B>
-static cudaError_t launch_shape(const InstDesc &one, const InstDesc *table, int ninst,
-                                long long units, int grid, int dry, cudaStream_t s)
+static cudaError_t launch_shape(const InstDesc &one, const CtaSplit &split, const InstDesc *table,
+                                int ninst, long long units, int grid, int dry, cudaStream_t s)
 {
     static std::mutex mu;
     static bool done[64] = {false};
@@ -888,21 +903,22 @@ static cudaError_t launch_shape(const InstDesc &one, const InstDesc *table, int 
             done[dev] = true;
         }
     }
-    k_step_f32<TY, TZ, B><<<(unsigned)grid, TY * TZ, sizeof(StepSmem<TY, TZ>), s>>>(one, table, ninst,
-                                                                                     units, dry);
+    k_step_f32<TY, TZ, B><<<(unsigned)grid, TY * TZ, sizeof(StepSmem<TY, TZ>), s>>>(
+        one, split, table, ninst, units, dry);
     return cudaGetLastError();
 }
 
 template <bool B>
-static cudaError_t launch_tile(int tile, const InstDesc &one, const InstDesc *table, int ninst,
-                               long long units, int grid, int dry, cudaStream_t s)
+static cudaError_t launch_tile(int tile, const InstDesc &one, const CtaSplit &split,
+                               const InstDesc *table, int ninst, long long units, int grid, int dry,
+                               cudaStream_t s)
 {
     switch (tile) {
-    case 0: return launch_shape<8, 32, B>(one, table, ninst, units, grid, dry, s);
-    case 1: return launch_shape<4, 32, B>(one, table, ninst, units, grid, dry, s);
-    case 2: return launch_shape<16, 16, B>(one, table, ninst, units, grid, dry, s);
-    case 4: return launch_shape<16, 32, B>(one, table, ninst, units, grid, dry, s);
-    default: return launch_shape<8, 16, B>(one, table, ninst, units, grid, dry, s);
+    case 0: return launch_shape<8, 32, B>(one, split, table, ninst, units, grid, dry, s);
+    case 1: return launch_shape<4, 32, B>(one, split, table, ninst, units, grid, dry, s);
+    case 2: return launch_shape<16, 16, B>(one, split, table, ninst, units, grid, dry, s);
+    case 4: return launch_shape<16, 32, B>(one, split, table, ninst, units, grid, dry, s);
+    default: return launch_shape<8, 16, B>(one, split, table, ninst, units, grid, dry, s);
     }
 }
 
@@ -1051,6 +1067,68 @@ cudaError_t launch_fixup_f32_fast(const skyrme_lattice &lat, const FlowArgs &a, 
     return cudaGetLastError();
 }
 
+// The even split (batched launches).
+static const CtaSplit kEvenSplit = {};
+
+// Pipeline fill of a run, in planes: its first centre needs planes x - 2 ..
+// x + 2, so a run of r centres streams r + 4 planes.
+constexpr int kRunFill = 4;
+
+// Greedy cover of `units` (columns of nix planes, one after the other) by CTAs
+// that each stream at most `cap` planes, a run costing its centres plus the
+// fill.  Fills `start` and returns the CTAs used (INT_MAX when more than
+// max_ctas would be needed).
+static int greedy_split(long long units, int nix, double cap, int max_ctas, int *start)
+{
+    long long pos = 0;
+    int b = 0;
+    while (pos < units) {
+        if (b >= max_ctas) return 0x7fffffff;
+        start[b++] = (int)pos;
+        double budget = cap;
+        bool first = true;
+        while (pos < units) {
+            const long long col_end = (pos / nix + 1) * (long long)nix;
+            long long take = (long long)(budget - kRunFill);
+            if (first) take = std::max(take, 1LL);  // every CTA streams at least one centre
+            take = std::min(take, col_end - pos);
+            if (take <= 0) break;
+            pos += take;
+            budget -= (double)(kRunFill + take);
+            first = false;
+            if (pos < col_end) break;  // the budget ran out inside the column
+        }
+    }
+    start[b] = (int)pos;
+    return b;
+}
+
+// Unit ranges for `grid` CTAs whose largest plane count is as small as the
+// greedy cover allows (bisection on the cap); cached for the last geometry.
+static bool balanced_split(long long units, int nix, int grid, CtaSplit &out)
+{
+    static thread_local long long key_units = -1;
+    static thread_local int key_nix = -1, key_grid = -1;
+    static thread_local CtaSplit cached;
+    if (units == key_units && nix == key_nix && grid == key_grid) {
+        out = cached;
+        return out.n > 0;
+    }
+    out.n = 0;
+    if (grid <= 0 || grid > kSplitMax || units > 0x7fffffffLL || units < grid) return false;
+    double lo = (double)units / grid, hi = (double)units / grid + 2.0 * kRunFill + nix;
+    for (int it = 0; it < 48; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (greedy_split(units, nix, mid, grid, out.start) <= grid) hi = mid;
+        else lo = mid;
+    }
+    out.n = greedy_split(units, nix, hi, grid, out.start);
+    if (out.n > grid) out.n = 0;
+    key_units = units, key_nix = nix, key_grid = grid;
+    cached = out;
+    return out.n > 0;
+}
+
 cudaError_t launch_step_f32_fast(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s)
 {
     const int tile = kSingleTile;
@@ -1062,9 +1140,11 @@ cudaError_t launch_step_f32_fast(const skyrme_lattice &lat, const FlowArgs &a, c
     std::vector<InstDesc> ds(1);
     if (!fill_desc(ds[0], lat, st, static_cast<Ctrl *>(a.ctrl), a.dt, a.mode, tile))
         return cudaErrorInvalidValue;
-    const int grid = grid_for(tile, false, ds[0].units);
+    int grid = grid_for(tile, false, ds[0].units);
+    CtaSplit split;
+    if (balanced_split(ds[0].units, ds[0].nix, grid, split)) grid = split.n;
     partition(ds, grid, a.step_parts);
-    return launch_tile<false>(tile, ds[0], nullptr, 1, ds[0].units, grid, 0, s);
+    return launch_tile<false>(tile, ds[0], split, nullptr, 1, ds[0].units, grid, 0, s);
 }
 
 }  // namespace skyrme
@@ -1118,7 +1198,8 @@ static skyrme_status batch_launch(skyrme_batch *b, int nsteps, int dry, cudaStre
     InstDesc dummy;
     memset(&dummy, 0, sizeof(dummy));
     for (int k = 0; k < nsteps; ++k) {
-        if (launch_tile<true>(b->tile, dummy, b->d_table, b->ninst, b->units, b->grid, dry, s) !=
+        if (launch_tile<true>(b->tile, dummy, kEvenSplit, b->d_table, b->ninst, b->units, b->grid,
+                              dry, s) !=
             cudaSuccess)
             return SKYRME_ECUDA;
         if (!dry && b->mode == MODE_ARRESTED) {
