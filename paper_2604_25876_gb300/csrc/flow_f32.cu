@@ -309,6 +309,46 @@ __device__ __forceinline__ void block_reduce_df(DF (&v)[kSums], float amax, DF *
     }
 }
 
+// Block sum of the per-thread double-float sums kept in shared memory
+// (accs: kSums arrays of NT, amaxs: NT) for CTAs of at least kSums + 1 warps:
+// warp q sums quantity q, each lane over two independent chains, then a
+// butterfly; warp kSums takes the max.  Fixed order; thread 0 ends with the
+// totals.  The caller has synchronised after the last write to accs.
+template <int NT>
+__device__ __forceinline__ void block_reduce_df_smem(const DF *accs, const float *amaxs, DF *red,
+                                                     float *mred, DF (&tot)[kSums], float &tmax,
+                                                     int tid)
+{
+    static_assert(NT / 32 > kSums && NT % 64 == 0, "one warp per quantity and two chains");
+    const int lane = tid & 31, warp = tid >> 5;
+    if (warp < kSums) {
+        const DF *a = accs + warp * NT + lane;
+        DF c0 = {0.f, 0.f}, c1 = {0.f, 0.f};
+#pragma unroll 1
+        for (int k = 0; k < NT / 32; k += 2) {
+            c0 = df_add(c0, a[32 * k]);
+            c1 = df_add(c1, a[32 * k + 32]);
+        }
+        DF v = df_add(c0, c1);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
+        if (lane == 0) red[warp] = v;
+    } else if (warp == kSums) {
+        float m = 0.f;
+#pragma unroll 1
+        for (int k = 0; k < NT / 32; ++k) m = fmaxf(m, amaxs[lane + 32 * k]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) *mred = m;
+    }
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < kSums; ++q) tot[q] = red[q];
+        tmax = *mred;
+    }
+}
+
 // Per-plane values of one column kept in the register x-ring.
 struct PlaneVals {
     P4 phi, dy, dz;
@@ -489,7 +529,7 @@ __device__ __forceinline__ void write_record(const InstDesc &D, int slot, const 
 template <int NW, typename Sync>
 __device__ __forceinline__ void finish_lattice(const InstDesc &D, Ctrl *c, int cur, int mode,
                                                int pred, int dry, DF *buf, float *amx, int tid,
-                                               Sync sync)
+                                               Sync sync, DF *accs = nullptr, float *amaxs = nullptr)
 {
     // thread 0 fetches the control fields it needs while the block sums the records
     double E_prev = 0.0;
@@ -518,7 +558,20 @@ __device__ __forceinline__ void finish_lattice(const InstDesc &D, Ctrl *c, int c
     }
     DF t[kSums];
     float tmax = 0.f;
-    block_reduce_df<NW>(v, amax, buf, amx, t, tmax, tid, sync);
+    if constexpr (NW > kSums && (NW * 32) % 64 == 0) {
+        if (accs) {
+            // the CTA's own sums are already in its record: reuse their slots
+#pragma unroll
+            for (int q = 0; q < kSums; ++q) accs[q * NW * 32 + tid] = v[q];
+            amaxs[tid] = amax;
+            sync();
+            block_reduce_df_smem<NW * 32>(accs, amaxs, buf, amx, t, tmax, tid);
+        } else {
+            block_reduce_df<NW>(v, amax, buf, amx, t, tmax, tid, sync);
+        }
+    } else {
+        block_reduce_df<NW>(v, amax, buf, amx, t, tmax, tid, sync);
+    }
     if (tid != 0) return;
     if (dry) {
         c->done = 0;
@@ -701,10 +754,19 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
         if (failed) break;
 
         // ---- this CTA is done with lattice D: block reduction, per-lattice finish
-        DF tot[kSums], mine[kSums];
-        float tmax = 0.f, mmax;
-        load_sums(acc, amax, THREADS, mine, mmax);
-        block_reduce_df<THREADS / 32>(mine, mmax, sm.dfred, sm.mxred, tot, tmax, tid, CtaSync{});
+        DF tot[kSums];
+        float tmax = 0.f;
+        if constexpr (THREADS / 32 > kSums && THREADS % 64 == 0) {
+            // the accumulators were last written before the run's closing barrier
+            block_reduce_df_smem<THREADS>(&sm.accs[0][0], sm.amaxs, sm.dfred, sm.mxred, tot, tmax,
+                                          tid);
+        } else {
+            DF mine[kSums];
+            float mmax;
+            load_sums(acc, amax, THREADS, mine, mmax);
+            block_reduce_df<THREADS / 32>(mine, mmax, sm.dfred, sm.mxred, tot, tmax, tid,
+                                          CtaSync{});
+        }
         if (tid == 0) {
             write_record(D, (int)blockIdx.x - D.cta_first, tot, tmax);
             __threadfence();
@@ -714,7 +776,7 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
         if (sm.last) {
             __threadfence();
             finish_lattice<THREADS / 32>(D, ctrl, cur, mode, pred, dry, sm.dfred, sm.mxred, tid,
-                                         CtaSync{});
+                                         CtaSync{}, &sm.accs[0][0], sm.amaxs);
         }
         __syncthreads();
     }
