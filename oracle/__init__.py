@@ -119,6 +119,9 @@ def _load():
             lib.orc_seed_product.argtypes = [I3, D, ctypes.c_int, P, P, D, ctypes.c_int, P]
             lib.orc_seed_noise.argtypes = [I3, D, D, D, ctypes.c_uint64, P]
             lib.orc_apply_vacuum_boundary.argtypes = [I3, P]
+            lib.orc_rational_map_field.argtypes = [I3, D, ctypes.c_int, D, P, P, P]
+            lib.orc_rational_map_field.restype = ctypes.c_int
+            lib.orc_field_product.argtypes = [I3, P, P, P]
             PM = ctypes.POINTER(_Model)
             lib.orc_site_terms_model.argtypes = [P, P, P, P, PM, P, P, P]
             lib.orc_forces_model.argtypes = [I3, D, PM, P, P, P, P]
@@ -312,6 +315,27 @@ def seed_product(n, h: float, positions, quats, profile_scale: float, symmetrise
     _load().orc_seed_product(_dims(n), h, len(pos), _ptr(pos), _ptr(q), profile_scale,
                              int(bool(symmetrise)), _ptr(phi))
     return phi
+
+
+def rational_map_field(n, h: float, B: int, profile_scale: float, X=(0.0, 0.0, 0.0), R=None):
+    """Rational-map Skyrmion moved to X and rotated by R: U_B(R^T (x - X))
+    (orc_rational_map_field); no vacuum boundary applied."""
+    phi = _field(n)
+    Xa = np.ascontiguousarray(X, dtype=np.float64)
+    Ra = np.ascontiguousarray(np.eye(3) if R is None else R, dtype=np.float64).reshape(9)
+    if _load().orc_rational_map_field(_dims(n), h, B, profile_scale, _ptr(Xa), _ptr(Ra),
+                                      _ptr(phi)) != 0:
+        raise ValueError("rational maps of degree 1 and 4 only")
+    return phi
+
+
+def field_product(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Ordered product ansatz a b, site by site (orc_field_product)."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    out = np.zeros_like(a)
+    _load().orc_field_product(_dims(a.shape[:3]), _ptr(a), _ptr(b), _ptr(out))
+    return out
 
 
 def seed_noise(n, h: float, radius: float, sigma: float, seed: int):

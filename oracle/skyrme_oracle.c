@@ -677,6 +677,36 @@ int orc_seed_rational_map(const int n[3], double h, int B,
     return 0;
 }
 
+/* Section 4.1 with the placement convention of the configuration files
+ * (Section 7.3): the rational-map Skyrmion of degree B moved to X and
+ * rotated by R (row-major, x' = R x), U(x) = U_B(R^T (x - X)). */
+int orc_rational_map_field(const int n[3], double h, int B, double profile_scale,
+                           const double X[3], const double R[9], double *phi)
+{
+    int x;
+    if (B != 1 && B != 4) return -1;
+#pragma omp parallel for schedule(static)
+    for (x = 0; x < n[0]; x++) {
+        int y, z, i;
+        for (y = 0; y < n[1]; y++)
+            for (z = 0; z < n[2]; z++) {
+                const double d[3] = {coord(n, h, 0, x) - X[0], coord(n, h, 1, y) - X[1],
+                                     coord(n, h, 2, z) - X[2]};
+                double q[3], r, f, nh[3];
+                double *p = &phi[4 * site_index(n, x, y, z)];
+                for (i = 0; i < 3; i++) q[i] = R[i] * d[0] + R[3 + i] * d[1] + R[6 + i] * d[2];
+                r = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+                f = M_PI * exp(-r / profile_scale);
+                rational_map_direction(B, q[0], q[1], q[2], r, nh);
+                p[0] = cos(f);
+                p[1] = sin(f) * nh[0];
+                p[2] = sin(f) * nh[1];
+                p[3] = sin(f) * nh[2];
+            }
+    }
+    return 0;
+}
+
 /* Quaternion product in the U = phi^0 + i phi^a tau^a representation:
  * (a0, a)(b0, b) = (a0 b0 - a.b, a0 b + b0 a - a x b), which follows from
  * tau^a tau^b = delta^{ab} + i eps^{abc} tau^c. */
@@ -688,6 +718,16 @@ static void qmul(const double a[4], const double b[4], double out[4])
     r[2] = a[0] * b[2] + b[0] * a[2] - (a[3] * b[1] - a[1] * b[3]);
     r[3] = a[0] * b[3] + b[0] * a[3] - (a[1] * b[2] - a[2] * b[1]);
     memcpy(out, r, sizeof(r));
+}
+
+/* Section 4.2, Eq. "Product ansatz": the ordered product a b of two fields,
+ * site by site. */
+void orc_field_product(const int n[3], const double *a, const double *b, double *out)
+{
+    const long long ns = (long long)n[0] * n[1] * n[2];
+    long long s;
+#pragma omp parallel for schedule(static)
+    for (s = 0; s < ns; s++) qmul(&a[4 * s], &b[4 * s], &out[4 * s]);
 }
 
 void orc_seed_product(const int n[3], double h, int K, const double *pos,

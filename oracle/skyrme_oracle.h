@@ -184,6 +184,16 @@ void orc_seed_noise(const int n[3], double h, double radius, double sigma,
 /* Overwrite the two outer layers with the vacuum. */
 void orc_apply_vacuum_boundary(const int n[3], double *phi);
 
+/* A rational-map Skyrmion (B = 1 or 4, profile pi exp(-r / profile_scale))
+ * moved to X and rotated by the row-major rotation R: U(x) = U_B(R^T (x - X))
+ * at every site, boundary layers included (the configuration-file placement
+ * of Section 7.3).  Returns -1 for another B. */
+int orc_rational_map_field(const int n[3], double h, int B, double profile_scale,
+                           const double X[3], const double R[9], double *phi);
+/* The ordered product ansatz of Section 4.2: out = a b site by site (out may
+ * alias a or b). */
+void orc_field_product(const int n[3], const double *a, const double *b, double *out);
+
 /* SplitMix64 counter stream: value number i of stream `seed`. */
 uint64_t orc_splitmix64(uint64_t seed, uint64_t i);
 /* Standard normal number i of stream `seed` (Box-Muller on two uniforms). */
