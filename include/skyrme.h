@@ -166,8 +166,9 @@ skyrme_status skyrme_graph_destroy(skyrme_graph *g);
  * until it has converged, without returning to the host: a device-side WHILE
  * node repeats `chunk` iterations (as skyrme_flow_step launches them)
  * followed by a check, for as long as
- *   - the last iteration's delta = max over interior sites of |F| (Section 3
- *     and the convergence residual of Section 7.9, reading R6) is above tol,
+ *   - the last iteration's delta = max over interior sites of |F| (the
+ *     convergence residual of Sections 3 and 7.9, taken as the largest
+ *     force) is above tol,
  *   - fewer than max_steps iterations have run since this launch began, and
  *   - no error has been recorded in the state.
  * The flow therefore stops at the first chunk boundary where delta <= tol,

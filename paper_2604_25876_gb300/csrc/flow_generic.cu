@@ -111,7 +111,8 @@ __device__ __forceinline__ vec4_t<T> sd1v(const vec4_t<T> &m2v, const vec4_t<T> 
 // d_x phi on the interior x-planes of the tile over (y, z) widened by 2, then
 // d_y phi on the interior (x, y) rows of the tile over z widened by 2.  The
 // mixed derivatives are first-derivative stencils of these (Section 3,
-// reading R1: d_xy = d_y(d_x phi), d_xz = d_z(d_x phi), d_yz = d_z(d_y phi)),
+// the mixed stencil being the product of two first-derivative stencils:
+// d_xy = d_y(d_x phi), d_xz = d_z(d_x phi), d_yz = d_z(d_y phi)),
 // which costs a quarter of the FP64 operations of the 16-tap sums.
 // FP32 kernels keep two field tiles, the next one arriving by cp.async.
 constexpr int GDX = GTX * GSY * GSZ;  // entries of d_x phi
