@@ -70,7 +70,8 @@ typedef struct {
 
 enum {
     SKYRME_SEED_VACUUM = 0,        /* phi = (1,0,0,0) everywhere */
-    SKYRME_SEED_RATIONAL_MAP = 1,  /* Section 4.1, degree B in {1, 4} (Table 1), centred */
+    SKYRME_SEED_RATIONAL_MAP = 1,  /* Section 4.1, degree B in {1, 2, 3, 4} (Table 1; the
+                                      degree-3 constant a = i, tetrahedral), centred */
     SKYRME_SEED_PRODUCT = 2,       /* Section 4.2, Eq. "Product ansatz" of B isorotated hedgehogs */
     SKYRME_SEED_NOISE = 3          /* vacuum + Gaussian-smoothed N(0,1) noise in a ball, normalised */
 };

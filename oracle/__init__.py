@@ -303,7 +303,7 @@ def seed_vacuum(n):
 def seed_rational_map(n, h: float, B: int, profile_scale: float):
     phi = _field(n)
     if _load().orc_seed_rational_map(_dims(n), h, B, profile_scale, _ptr(phi)) != 0:
-        raise ValueError("rational maps of degree 1 and 4 only")
+        raise ValueError("rational maps of degree 1 to 4 only")
     return phi
 
 
@@ -325,7 +325,7 @@ def rational_map_field(n, h: float, B: int, profile_scale: float, X=(0.0, 0.0, 0
     Ra = np.ascontiguousarray(np.eye(3) if R is None else R, dtype=np.float64).reshape(9)
     if _load().orc_rational_map_field(_dims(n), h, B, profile_scale, _ptr(Xa), _ptr(Ra),
                                       _ptr(phi)) != 0:
-        raise ValueError("rational maps of degree 1 and 4 only")
+        raise ValueError("rational maps of degree 1 to 4 only")
     return phi
 
 

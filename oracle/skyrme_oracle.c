@@ -16,7 +16,9 @@
  *   Section 3,   Eq. "Sigma model EL equations"  dE/dphi^A
  *   Section 3,   first/second-derivative 4th-order stencils
  *   Section 3,   arrest rule, normalisation after each update, vacuum box
- *   Section 4.1  rational-map ansatz, Table 1 (B = 1 and B = 4 maps)
+ *   Section 4.1  rational-map ansatz, Table 1 (the B = 1 to 4 maps; the
+ *                degree-3 constant a, given by reference only, is i: the
+ *                tetrahedral map)
  *   Section 4.2  product ansatz, Eq. "Product ansatz"
  *   Section 5.6  virial V = integral of T_kk
  *   Section 7.8  extension models: the modified-pion, loosely and lightly
@@ -629,6 +631,18 @@ static void rational_map_direction(int B, double x, double y, double z3,
     if (B == 1) { /* R(z) = z */
         P = Z1;
         Q = Z0;
+    } else if (B == 2) { /* R(z) = z^2 */
+        P = cmul(Z1, Z1);
+        Q = cmul(Z0, Z0);
+    } else if (B == 3) { /* R(z) = (sqrt3 a z^2 - 1) / (z (z^2 - sqrt3 a)), a = i (tetrahedral) */
+        cplx Z1s = cmul(Z1, Z1), Z0s = cmul(Z0, Z0);
+        cplx c = {0.0, sqrt(3.0)};
+        cplx t = cmul(c, Z1s);             /* sqrt3 i z1^2 */
+        cplx u = cmul(c, Z0s);             /* sqrt3 i z0^2 */
+        P.re = cmul(t, Z0).re - cmul(Z0s, Z0).re;  /* z0 (sqrt3 i z1^2 - z0^2) */
+        P.im = cmul(t, Z0).im - cmul(Z0s, Z0).im;
+        Q.re = cmul(Z1, cadd(Z1s, (cplx){-u.re, -u.im})).re;  /* z1 (z1^2 - sqrt3 i z0^2) */
+        Q.im = cmul(Z1, cadd(Z1s, (cplx){-u.re, -u.im})).im;
     } else { /* B = 4: R(z) = (z^4 + 2 sqrt3 i z^2 + 1)/(z^4 - 2 sqrt3 i z^2 + 1) */
         cplx Z1s = cmul(Z1, Z1), Z0s = cmul(Z0, Z0);
         cplx Z14 = cmul(Z1s, Z1s), Z04 = cmul(Z0s, Z0s);
@@ -653,7 +667,7 @@ int orc_seed_rational_map(const int n[3], double h, int B,
                           double profile_scale, double *phi)
 {
     int x;
-    if (B != 1 && B != 4) return -1;
+    if (B < 1 || B > 4) return -1;
 #pragma omp parallel for schedule(static)
     for (x = 0; x < n[0]; x++) {
         int y, z;
@@ -684,7 +698,7 @@ int orc_rational_map_field(const int n[3], double h, int B, double profile_scale
                            const double X[3], const double R[9], double *phi)
 {
     int x;
-    if (B != 1 && B != 4) return -1;
+    if (B < 1 || B > 4) return -1;
 #pragma omp parallel for schedule(static)
     for (x = 0; x < n[0]; x++) {
         int y, z, i;

@@ -165,7 +165,8 @@ long long orc_flow_model(const int n[3], double h, const orc_model *md, double d
 
 void orc_seed_vacuum(const int n[3], double *phi);
 /* phi = (cos f, sin f n_R(z)) with f(r) = pi exp(-r/profile_scale) and the
- * rational map of degree B (1: R=z; 4: the cubic map of Table 1), centred at
+ * rational map of degree B (Table 1: 1: R=z; 2: z^2; 3: the tetrahedral map
+ * with a = i; 4: the cubic map), centred at
  * the origin. */
 int orc_seed_rational_map(const int n[3], double h, int B,
                           double profile_scale, double *phi);
@@ -184,7 +185,7 @@ void orc_seed_noise(const int n[3], double h, double radius, double sigma,
 /* Overwrite the two outer layers with the vacuum. */
 void orc_apply_vacuum_boundary(const int n[3], double *phi);
 
-/* A rational-map Skyrmion (B = 1 or 4, profile pi exp(-r / profile_scale))
+/* A rational-map Skyrmion (B = 1 to 4, profile pi exp(-r / profile_scale))
  * moved to X and rotated by the row-major rotation R: U(x) = U_B(R^T (x - X))
  * at every site, boundary layers included (the configuration-file placement
  * of Section 7.3).  Returns -1 for another B. */

@@ -209,7 +209,7 @@ skyrme_status skyrme_init_field(const skyrme_lattice *lat, const skyrme_seed *se
     switch (seed->kind) {
     case SKYRME_SEED_VACUUM: break;
     case SKYRME_SEED_RATIONAL_MAP:
-        if ((seed->B != 1 && seed->B != 4) || !(seed->profile_scale > 0.0)) return SKYRME_EINVAL;
+        if (seed->B < 1 || seed->B > 4 || !(seed->profile_scale > 0.0)) return SKYRME_EINVAL;
         break;
     case SKYRME_SEED_PRODUCT:
         if (seed->B < 1 || seed->B > max_constituents() || !seed->positions || !seed->quaternions ||

@@ -1,5 +1,5 @@
 // init_fields.cu -- initial fields of Section 4 built on the device:
-// rational-map Skyrmions (Section 4.1, Table 1 degrees 1 and 4), the product
+// rational-map Skyrmions (Section 4.1, Table 1 degrees 1 to 4), the product
 // ansatz of isorotated 1-Skyrmions (Section 4.2, Eq. "Product ansatz",
 // optionally symmetrised by renormalising U_1..U_K + U_K..U_1), and a
 // smoothed-noise start (vacuum plus Gaussian-smoothed N(0,1) noise inside a
@@ -65,7 +65,20 @@ __device__ void rm_direction(int B, double x, double y, double z3, double r, dou
     else { z1r = r - z3; z1i = 0.0; z0r = x; z0i = -y; }
     double pr, pi, qr, qi;
     if (B == 1) { pr = z1r; pi = z1i; qr = z0r; qi = z0i; }
-    else {
+    else if (B == 2) {  // R = z^2
+        pr = z1r * z1r - z1i * z1i; pi = 2 * z1r * z1i;
+        qr = z0r * z0r - z0i * z0i; qi = 2 * z0r * z0i;
+    } else if (B == 3) {
+        // R = (sqrt3 i z^2 - 1) / (z (z^2 - sqrt3 i)):
+        // P = z0 (sqrt3 i z1^2 - z0^2), Q = z1 (z1^2 - sqrt3 i z0^2)
+        const double c = sqrt(3.0);
+        const double a2r = z1r * z1r - z1i * z1i, a2i = 2 * z1r * z1i;
+        const double b2r = z0r * z0r - z0i * z0i, b2i = 2 * z0r * z0i;
+        const double ar = -c * a2i - b2r, ai = c * a2r - b2i;
+        const double cr = a2r + c * b2i, ci = a2i - c * b2r;
+        pr = z0r * ar - z0i * ai; pi = z0r * ai + z0i * ar;
+        qr = z1r * cr - z1i * ci; qi = z1r * ci + z1i * cr;
+    } else {
         // z1^2, z0^2, z1^4, z0^4, z1^2 z0^2
         const double a2r = z1r * z1r - z1i * z1i, a2i = 2 * z1r * z1i;
         const double b2r = z0r * z0r - z0i * z0i, b2i = 2 * z0r * z0i;

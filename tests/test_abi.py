@@ -70,7 +70,7 @@ def test_invalid_arguments_are_rejected_without_cuda():
     assert lib.skyrme_flow_step(ctypes.byref(lat), 0.01, 1, 7, ctypes.byref(st), None, None) == 1
     assert lib.skyrme_flow_step(ctypes.byref(lat), 0.01, -1, 1, ctypes.byref(st), None, None) == 1
     # bad seeds
-    for seed in (sk.Seed(sk.SEED_RATIONAL_MAP, B=3, profile_scale=1.0),
+    for seed in (sk.Seed(sk.SEED_RATIONAL_MAP, B=5, profile_scale=1.0),
                  sk.Seed(sk.SEED_RATIONAL_MAP, B=4, profile_scale=0.0),
                  sk.Seed(sk.SEED_PRODUCT, B=2),  # no arrays
                  sk.Seed(sk.SEED_NOISE, radius=3.0, sigma=100.0, seed=1),  # too wide

@@ -1,18 +1,21 @@
-"""End-to-end pins against values the paper prints: the relaxed B=8a and
-B=12a Skyrmions of its "Neat examples" section (tests/golden/
+"""End-to-end pins against values the paper prints: the relaxed B=3, B=8a
+and B=12a Skyrmions of its "Neat examples" section (tests/golden/
 paper_neat_examples.txt).
 
-The seeds follow the printed configuration files: B=4 rational-map
+The seeds follow the printed recipes: the B=3 rational map of Table 1; and
+for B=8a and B=12a the printed configuration files, B=4 rational-map
 constituents placed and rotated (Euler angles about z, y, z) and combined
-with the ordered product ansatz, built by the oracle.  The FP64 flow relaxes
+with the ordered product ansatz.  The oracle builds them.  The FP64 flow relaxes
 them on the GPU on the programme's default lattice (151^3, half-width 8,
 m = 1) until max |F| <= 1e-3.  The constituent profile pi exp(-r) differs
 from the paper's fitted profile; the relaxed Skyrmion does not depend on it.
+B=3 checks the sign and size of the mixed inertia tensor W, which vanishes
+for the two chains.
 
-The D-term is not compared.  It follows the formula the paper prints
-(Section 5, Eq. "D-term").  The printed D(0) values are about 1.21e-3 times
-that formula evaluated on these same fields (1.2137e-3 for B=8a, 1.2082e-3
-for B=12a), while every other observable agrees to about 0.1%.
+The D-term follows the formula the paper prints (Section 5, Eq. "D-term").
+The printed D(0) values equal that formula times one more lattice cell
+volume h^3 (to 1e-4 for B=3 and B=8a, 0.45% for B=12a), as if the volume
+element had been applied twice; the test compares D h^3 with them at 1%.
 """
 import math
 import os
@@ -58,6 +61,8 @@ def printed():
 def seed(name):
     n = (N, N, N)
     R = euler_zyz(*ALPHA)
+    if name == "b3":
+        return oracle.seed_rational_map(n, H, 3, 1.3)
     if name == "b8a":
         parts = [oracle.rational_map_field(n, H, 4, 1.0, X=(-1.5, 0, 0)),
                  oracle.rational_map_field(n, H, 4, 1.0, X=(1.5, 0, 0), R=R)]
@@ -71,7 +76,7 @@ def seed(name):
     return oracle.apply_vacuum_boundary(phi)
 
 
-@pytest.mark.parametrize("name", ["b8a", "b12a"])
+@pytest.mark.parametrize("name", ["b3", "b8a", "b12a"])
 def test_relaxed_multi_skyrmion_matches_the_printed_observables(name):
     ref = printed()[name]
     lat = sk.Lattice((N, N, N), H, M, 64)
@@ -89,6 +94,8 @@ def test_relaxed_multi_skyrmion_matches_the_printed_observables(name):
         scale = np.max(np.abs(want))
         # printed to two decimals; the relaxed tensors agree to ~0.1%
         assert np.max(np.abs(got - want)) <= 2e-3 * scale + 0.1, (key, got, want)
-    assert np.max(np.abs(np.array(o["W"]))) < 1e-3 * np.max(np.abs(ref["V"]))
-    # the D-term as printed in Section 5 (see the module docstring)
-    assert o["D"] < 0
+    W = np.array(o["W"])
+    assert np.max(np.abs(W - ref["W"])) <= 2e-3 * np.max(np.abs(ref["V"])) + 0.1, (W, ref["W"])
+    # the D-term of the printed formula, times the extra cell volume of the
+    # printed values (see the module docstring)
+    assert o["D"] * H ** 3 == pytest.approx(ref["D"], rel=1e-2)

@@ -87,6 +87,8 @@ def seeds_for(n, h):
     wl = workloads.cluster_seed(5, 1.5, 8)
     return [
         ("rational_map_1", sk.Seed.rational_map(1, 1.0), oracle.seed_rational_map(n, h, 1, 1.0)),
+        ("rational_map_2", sk.Seed.rational_map(2, 1.5), oracle.seed_rational_map(n, h, 2, 1.5)),
+        ("rational_map_3", sk.Seed.rational_map(3, 1.5), oracle.seed_rational_map(n, h, 3, 1.5)),
         ("rational_map_4", sk.Seed.rational_map(4, 2.0), oracle.seed_rational_map(n, h, 4, 2.0)),
         ("product_sym", sk.Seed.product(wl.positions, wl.quaternions, 1.0, True),
          oracle.seed_product(n, h, wl.positions, wl.quaternions, 1.0, True)),
