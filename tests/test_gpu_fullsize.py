@@ -91,3 +91,62 @@ def test_full_size_fp32_energy_tracks_fp64_gpu_flow(name):
     assert reps[32]["E"] == pytest.approx(reps[64]["E"], rel=1e-5)
     assert reps[32]["B"] == pytest.approx(reps[64]["B"], rel=1e-5)
     assert reps[32]["arrests"] == reps[64]["arrests"]
+
+
+# Size extremes of the lattice the ABI accepts: a 1024^3 cube (1.07e9 sites,
+# four 17 GB buffers), the longest axis (4096 sites) and the smallest
+# lattices (one interior site; a ragged near-minimal box).
+EXTREMES = {
+    "cube_1024": ((1024, 1024, 1024), 0.02, 4, 2.0),
+    "axis_4096": ((4096, 36, 40), 0.25, 1, 1.0),
+}
+
+
+@pytest.mark.parametrize("name", list(EXTREMES))
+def test_extreme_sizes_step_matches_oracle_site_by_site(name):
+    n, h, B, scale = EXTREMES[name]
+    m, dt = 1.0, 0.05 * h
+    lat = sk.Lattice(n, h, m, 32)
+    st = sk.State(lat, DEV)
+    sk.init_field(lat, sk.Seed.rational_map(B, scale), st)
+    rng = np.random.default_rng(11)
+    sites = sample_sites(n, 40, rng)
+    blocks = {s: np.ascontiguousarray(neighbourhood(st.field(), *s)) for s in sites}
+    rep = sk.flow_step(lat, dt, 1, sk.ARRESTED, st)
+    assert rep["steps"] == 1 and rep["status"] == 0
+    assert rep["B"] == pytest.approx(B, abs=0.05 * B)
+    phi1 = st.field()
+    errs, scale_f = [], 0.0
+    for s, blk in blocks.items():
+        d1, d2, dm = oracle.site_derivatives(blk, h, 2, 2, 2)
+        _, F, _ = oracle.site_terms(blk[2, 2, 2], d1, d2, dm, m)
+        t = blk[2, 2, 2] + dt * (dt * F)
+        want = t / np.linalg.norm(t)
+        errs.append(np.max(np.abs(phi1[s].double().cpu().numpy() - want)))
+        scale_f = max(scale_f, dt * dt * np.max(np.abs(F)))
+    assert max(errs) < 2e-7 + 1e-5 * scale_f, (max(errs), scale_f)
+    del st
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("prec,tol", [(64, 1e-12), (32, 2e-6)])
+@pytest.mark.parametrize("n", [(5, 5, 5), (6, 7, 5), (5, 9, 6)])
+def test_smallest_lattices_match_oracle(n, prec, tol):
+    h, m, dt = 0.3, 1.0, 0.015
+    rng = np.random.default_rng(sum(n))
+    phi = rng.normal(size=tuple(n) + (4,))
+    phi[..., 0] += 2.0
+    phi /= np.linalg.norm(phi, axis=-1, keepdims=True)
+    phi = oracle.apply_vacuum_boundary(np.ascontiguousarray(phi))
+    if prec == 32:
+        phi = phi.astype(np.float32).astype(np.float64)
+    ost = oracle.new_state(phi)
+    oreps = oracle.flow(ost, h, m, dt, 3, reports=True)
+    lat = sk.Lattice(n, h, m, prec)
+    st = sk.State(lat, DEV)
+    sk.load_field(lat, st, phi)
+    rep = sk.flow_step(lat, dt, 3, sk.ARRESTED, st)
+    got = st.field().double().cpu().numpy()
+    assert np.max(np.abs(got - ost.phi)) <= tol * 10
+    assert rep["E"] == pytest.approx(oreps[-1]["E"], rel=tol * 10)
+    assert rep["arrests"] == sum(r["arrested"] for r in oreps)
