@@ -14,8 +14,8 @@ namespace skyrme {
 int max_constituents();
 int max_smoothing_half_width();
 bool f32_fast_path_available(const skyrme_lattice &lat);
-cudaError_t launch_step_f32_fast(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s);
-cudaError_t launch_fixup_f32_fast(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s);
+cudaError_t launch_iterations_f32_fast(const skyrme_lattice &lat, const FlowArgs &a, int nsteps,
+                                       cudaStream_t s);
 int f32_fast_blocks(const skyrme_lattice &lat);
 }  // namespace skyrme
 
@@ -250,13 +250,13 @@ static skyrme_status launch_iterations(const skyrme_lattice &lat, const FlowArgs
 {
     // the streaming FP32 kernel implements the standard model only
     const bool fast = lat.precision == 32 && !lattice_extended(lat) && f32_fast_path_available(lat);
+    if (fast) {
+        CK(launch_iterations_f32_fast(lat, a, nsteps, s), "step and fix-up kernels (fp32)");
+        return SKYRME_OK;
+    }
     for (int k = 0; k < nsteps; ++k) {
-        if (fast) CK(launch_step_f32_fast(lat, a, s), "step kernel (fp32)");
-        else CK(launch_step(lat, a, s), "step kernel");
-        if (a.mode == SKYRME_ARRESTED) {
-            if (fast) CK(launch_fixup_f32_fast(lat, a, s), "fix-up kernel (fp32)");
-            else CK(launch_fixup(lat, a, s), "fix-up kernel");
-        }
+        CK(launch_step(lat, a, s), "step kernel");
+        if (a.mode == SKYRME_ARRESTED) CK(launch_fixup(lat, a, s), "fix-up kernel");
     }
     return SKYRME_OK;
 }

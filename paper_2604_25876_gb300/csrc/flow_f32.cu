@@ -1111,24 +1111,6 @@ int f32_fast_blocks(const skyrme_lattice &lat)
     return kMaxGrid;
 }
 
-cudaError_t launch_fixup_f32_fast(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s)
-{
-    FixDesc d;
-    for (int i = 0; i < 2; ++i) {
-        d.phi[i] = static_cast<float4 *>(a.phi[i]);
-        d.vel[i] = static_cast<float4 *>(a.vel[i]);
-    }
-    d.ctrl = static_cast<Ctrl *>(a.ctrl);
-    d.n0 = lat.n[0];
-    d.n1 = lat.n[1];
-    d.n2 = lat.n[2];
-    d.dt = (float)a.dt;
-    const long long rows = (long long)(lat.n[0] - 4) * (lat.n[1] - 4);
-    const int blocks = (int)std::max(1LL, std::min((long long)sm_count() * 2, (rows + 15) / 16));
-    k_fixup_one<<<blocks, 512, 0, s>>>(d);
-    return cudaGetLastError();
-}
-
 // The even split (batched launches).
 static const CtaSplit kEvenSplit = {};
 
@@ -1191,8 +1173,14 @@ static bool balanced_split(long long units, int nix, int grid, CtaSplit &out)
     return out.n > 0;
 }
 
-cudaError_t launch_step_f32_fast(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s)
+// nsteps iterations of a single lattice: the step kernel and, in ARRESTED
+// mode, the fix-up check.  The tensor maps, the work split and the fix-up
+// descriptor are the same for every iteration, so they are prepared once per
+// call; the loop only launches.
+cudaError_t launch_iterations_f32_fast(const skyrme_lattice &lat, const FlowArgs &a, int nsteps,
+                                       cudaStream_t s)
 {
+    if (nsteps <= 0) return cudaSuccess;
     const int tile = kSingleTile;
     skyrme_state st;
     for (int i = 0; i < 2; ++i) {
@@ -1206,7 +1194,29 @@ cudaError_t launch_step_f32_fast(const skyrme_lattice &lat, const FlowArgs &a, c
     CtaSplit split;
     if (balanced_split(ds[0].units, ds[0].nix, grid, split)) grid = split.n;
     partition(ds, grid, a.step_parts);
-    return launch_tile<false>(tile, ds[0], split, nullptr, 1, ds[0].units, grid, 0, s);
+
+    FixDesc fx;
+    for (int i = 0; i < 2; ++i) {
+        fx.phi[i] = static_cast<float4 *>(a.phi[i]);
+        fx.vel[i] = static_cast<float4 *>(a.vel[i]);
+    }
+    fx.ctrl = static_cast<Ctrl *>(a.ctrl);
+    fx.n0 = lat.n[0];
+    fx.n1 = lat.n[1];
+    fx.n2 = lat.n[2];
+    fx.dt = (float)a.dt;
+    const long long rows = (long long)(lat.n[0] - 4) * (lat.n[1] - 4);
+    const int fix_blocks = (int)std::max(1LL, std::min((long long)sm_count() * 2, (rows + 15) / 16));
+
+    for (int k = 0; k < nsteps; ++k) {
+        cudaError_t e = launch_tile<false>(tile, ds[0], split, nullptr, 1, ds[0].units, grid, 0, s);
+        if (e != cudaSuccess) return e;
+        if (a.mode == SKYRME_ARRESTED) {
+            k_fixup_one<<<fix_blocks, 512, 0, s>>>(fx);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
 }
 
 }  // namespace skyrme
