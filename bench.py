@@ -341,6 +341,8 @@ def run_ours(args, ws, rank, local):
             out["fp64_gpu"] = run_fp64_compare(sk, torch, dev, wl, K + W, rep, alu["fp64_tflops"])
         if not wl.extended:
             out["diagnostics"] = run_diagnostics(sk, torch, dev, wl, alu["fp64_tflops"])
+            if prec == 32:
+                out["variants"] = run_variants(sk, torch, dev, wl, hbm)
         out["cpu_baseline"] = run_cpu_baseline(wl, args.cpu_seconds)
     return out
 
@@ -456,6 +458,73 @@ def run_fp64_compare(sk, torch, dev, wl, nsteps, rep32, fp64_tflops):
             "E_fp64": rep["E"],
             "fp32_energy_rel_err": abs(rep32["E"] - rep["E"]) / abs(rep["E"])
             if rep32["steps"] == rep["steps"] else None}
+
+
+def run_variants(sk, torch, dev, wl, hbm, tol=1e-3, chunk=250, iters=1000):
+    """The other flow modes and the run-to-tolerance driver (Section 3,
+    Section 7.9): Newton and gradient flow throughput from graph replays of
+    the same step kernel, and the time to relax the workload's seed to
+    max |F| <= tol in one launch of a WHILE-node graph, in FP32 and in FP64."""
+    out = {}
+    for name, mode, bps in (("newton", sk.NEWTON, BYTES_PER_SITE_F32),
+                            ("gradient", sk.GRADIENT, BYTES_PER_SITE_F32 // 2)):
+        lat = lattice_of(sk, wl, 32)
+        st = sk.State(lat, dev)
+        sk.init_field(lat, sk.Seed.from_spec(wl.seed), st)
+        g = sk.FlowGraph(lat, st, wl.dt, chunk, mode)
+        g.launch()  # warm-up
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(g.stream)
+        for _ in range(iters // chunk):
+            g.launch()
+        b.record(g.stream)
+        g.stream.synchronize()
+        g.close()
+        ms = a.elapsed_time(b) / (iters // chunk * chunk)
+        rep = sk.read_report(lat, st)
+        gbs = bps * wl.interior_sites / (ms * 1e-3) / 1e9
+        out[name] = {"value": round(wl.interior_sites / (ms * 1e-3) / 1e9, 4), "unit": UNIT,
+                     "steps": iters // chunk * chunk, "status": int(rep["status"]),
+                     "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm,
+                                  "unit": "GB/s", "frac": round(gbs / hbm, 4),
+                                  "algorithmic_bytes_per_site": bps}}
+    until = {"tol": tol, "chunk": chunk}
+    for prec in (32, 64):
+        lat = lattice_of(sk, wl, prec)
+        st = sk.State(lat, dev)
+        sk.init_field(lat, sk.Seed.from_spec(wl.seed), st)
+        g = sk.FlowGraph(lat, st, wl.dt, chunk, sk.ARRESTED, until=(tol, 200000))
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(g.stream)
+        g.launch()
+        b.record(g.stream)
+        g.stream.synchronize()
+        g.close()
+        ms = a.elapsed_time(b)
+        rep = sk.read_report(lat, st)
+        r = {"steps": rep["steps"], "ms": round(ms, 3), "E": rep["E"], "delta": rep["delta"],
+             "status": int(rep["status"]),
+             "gsites": round(wl.interior_sites * rep["steps"] / (ms * 1e-3) / 1e9, 4)}
+        if prec == 32 and rep["steps"] % chunk == 0:
+            # the same iterations from the same seed as plain graph replays:
+            # the cost of the device-side stop test
+            sk.init_field(lat, sk.Seed.from_spec(wl.seed), st)
+            g = sk.FlowGraph(lat, st, wl.dt, chunk, sk.ARRESTED)
+            torch.cuda.synchronize(dev)
+            a.record(g.stream)
+            for _ in range(rep["steps"] // chunk):
+                g.launch()
+            b.record(g.stream)
+            g.stream.synchronize()
+            g.close()
+            r["plain_graphs_ms"] = round(a.elapsed_time(b), 3)
+            r["until_overhead"] = round(ms / a.elapsed_time(b) - 1.0, 4)
+        until["fp%d" % prec] = r
+    until["energy_rel_diff"] = abs(until["fp32"]["E"] - until["fp64"]["E"]) / abs(until["fp64"]["E"])
+    until["time_ratio_fp64_over_fp32"] = round(until["fp64"]["ms"] / until["fp32"]["ms"], 2)
+    out["until"] = until
+    return out
 
 
 def run_diagnostics(sk, torch, dev, wl, fp64_tflops, reps=5):
