@@ -89,11 +89,11 @@ __global__ void __launch_bounds__(256) k_energy_static(const vec4_t<T> *__restri
                       (r0[2] * r1[3] - r1[2] * r0[3]) * (r2[0] * r3[1] - r3[0] * r2[1]);
         acc[0] += (double)tra;
         acc[1] += (double)(T(0.5) * (tra * tra - sq));
-        T e0 = T(2) * m2 * (T(1) - c.x);
+        const T u = one_minus_phi0<T>(ph);
+        T e0 = T(2) * m2 * u;
         if (extended) {
             // Section 7.8 potentials and the sextic term c6 4 pi^4 (B0)^2 = c6 det^2
-            const T u = T(1) - c.x;
-            e0 += ext.my2 * (T(1) - c.x * c.x) + ext.mz2 * u * u + T(0.5) * ext.mw2 * u * u * u * u;
+            e0 += ext.my2 * one_minus_phi0_sq<T>(ph, u) + ext.mz2 * u * u + T(0.5) * ext.mw2 * u * u * u * u;
             acc[4] += (double)(ext.c6 * det * det);
         }
         acc[2] += (double)e0;

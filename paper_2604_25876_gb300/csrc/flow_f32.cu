@@ -503,7 +503,10 @@ __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &
         if (mode != MODE_GRADIENT) __stcs(vout + si, st4(vnew));
         a32.e2 += tra;
         a32.e4 += e4;
-        a32.e0 += 1.f - ph.a.x;
+        // 1 - phi^0 from the pion components where it cancels (phi^0 >= 0)
+        const float2 pq = __fmul2_rn(ph.b, ph.b);
+        const float pi2 = fmaf(ph.a.y, ph.a.y, pq.x + pq.y);
+        a32.e0 += ph.a.x >= 0.f ? __fdividef(pi2, 1.f + ph.a.x) : 1.f - ph.a.x;
         a32.b += det;
         a32.f2 += f2;
         a32.fmax2 = fmaxf(a32.fmax2, f2);

@@ -105,6 +105,32 @@ __device__ __forceinline__ T fd2(T m2v, T m1v, T c, T p1v, T p2v)
     return W<T>::s1 * (p1v + m1v) + W<T>::s2 * (p2v + m2v) + W<T>::s0 * c;
 }
 
+// ------------------------------------------------------ 1 - phi^0
+// 1 - phi^0 of a unit 4-vector, the variable of the pion-mass potential
+// (Eq. "SkyrmeEnergy_phi") and of the Section 7.8 potentials.  Near the
+// vacuum phi^0 -> 1 and the difference cancels: an FP32 phi^0 holds it only to
+// its spacing of 6e-8 next to 1, and over a large near-vacuum lattice those
+// per-site errors add up to a bias of the potential energy (2e-4 of E ~ 10 on
+// a 112^3 lattice with h = 0.15).  In FP32 it is therefore taken, for
+// phi^0 >= 0, as |pi|^2 / (1 + phi^0) with pi = (phi^1, phi^2, phi^3), which
+// FP32 holds to full relative precision; for phi^0 < 0 there is no
+// cancellation.  FP64 uses the difference as written.
+template <typename T> __device__ __forceinline__ T one_minus_phi0(const T phi[4])
+{
+    if constexpr (sizeof(T) == 4) {
+        const T pi2 = phi[1] * phi[1] + phi[2] * phi[2] + phi[3] * phi[3];
+        return phi[0] >= T(0) ? __fdividef(pi2, T(1) + phi[0]) : T(1) - phi[0];
+    } else {
+        return T(1) - phi[0];
+    }
+}
+// 1 - (phi^0)^2 = u (2 - u) with u = 1 - phi^0 (same reasoning)
+template <typename T> __device__ __forceinline__ T one_minus_phi0_sq(const T phi[4], T u)
+{
+    if constexpr (sizeof(T) == 4) return u * (T(2) - u);
+    else return T(1) - phi[0] * phi[0];
+}
+
 // ------------------------------------------------------ extension models
 // Section 7.8 options beyond the standard pion mass: squared masses of the
 // modified pion, loosely and lightly bound potentials and the sextic
@@ -127,8 +153,8 @@ __device__ __forceinline__ void cross3(const T a[4], const T b[4], const T c[4],
 }
 
 // Adds the extension terms to the Euler-Lagrange gradient G (before the
-// tangent projection); returns their potential density in e0x and the sextic
-// density in e6.
+// tangent projection); returns their potential density in e0x, the sextic
+// density in e6 and 1 - phi^0 in u.
 //   potentials: d/dphi^0 of m_y^2 (1 - phi0^2) + m_z^2 u^2 + m_w^2 u^4 / 2, u = 1 - phi0;
 //   sextic, with D = det[phi, u, v, w] (u, v, w = d_x, d_y, d_z phi) and
 //   e6 = c6 4 pi^4 (B0)^2 = c6 D^2: the Euler-Lagrange operator of c6 D^2 is
@@ -139,12 +165,12 @@ __device__ __forceinline__ void cross3(const T a[4], const T b[4], const T c[4],
 template <typename T>
 __device__ __forceinline__ void extension_terms(const T phi[4], const T d1[3][4], const T d2[3][4],
                                                 const T dm[3][4], const ExtModel<T> &x, T G[4],
-                                                T &e0x, T &e6)
+                                                T &e0x, T &e6, T &u)
 {
-    const T u = T(1) - phi[0];
+    u = one_minus_phi0<T>(phi);
     const T u2 = u * u;
     G[0] -= T(2) * (x.my2 * phi[0] + x.mz2 * u + x.mw2 * u2 * u);
-    e0x = x.my2 * (T(1) - phi[0] * phi[0]) + x.mz2 * u2 + T(0.5) * x.mw2 * u2 * u2;
+    e0x = x.my2 * one_minus_phi0_sq<T>(phi, u) + x.mz2 * u2 + T(0.5) * x.mw2 * u2 * u2;
     T P[4], Q0[4], Q1[4], Q2[4];
     cross3<T>(d1[0], d1[1], d1[2], P);
     cross3<T>(phi, d1[1], d1[2], Q0);
@@ -201,8 +227,8 @@ __device__ __forceinline__ void site_physics(const T phi[4], const T d1[3][4], c
         G[A] = T(-2) * brace;
     }
     G[0] -= T(2) * m2;
-    T e0x = T(0);
-    if constexpr (EXT) extension_terms<T>(phi, d1, d2, dm, *ext, G, e0x, *e6);
+    T e0x = T(0), u0 = T(0);
+    if constexpr (EXT) extension_terms<T>(phi, d1, d2, dm, *ext, G, e0x, *e6, u0);
     const T Gphi = G[0] * phi[0] + G[1] * phi[1] + G[2] * phi[2] + G[3] * phi[3];
 #pragma unroll
     for (int A = 0; A < 4; ++A) F[A] = Gphi * phi[A] - G[A];
@@ -210,8 +236,8 @@ __device__ __forceinline__ void site_physics(const T phi[4], const T d1[3][4], c
     dens[0] = tra;
     const T sq = a00 * a00 + a11 * a11 + a22 * a22 + T(2) * (a01 * a01 + a02 * a02 + a12 * a12);
     dens[1] = T(0.5) * (tra * tra - sq);
-    dens[2] = T(2) * m2 * (T(1) - phi[0]);
-    if constexpr (EXT) dens[2] += e0x;
+    if constexpr (EXT) dens[2] = T(2) * m2 * u0 + e0x;
+    else dens[2] = T(2) * m2 * one_minus_phi0<T>(phi);
     // b = -(1/2 pi^2) det[phi, d_x phi, d_y phi, d_z phi] (Laplace expansion in 2x2 minors)
     const T *r0 = phi, *r1 = d1[0], *r2 = d1[1], *r3 = d1[2];
     const T s0 = r0[0] * r1[1] - r1[0] * r0[1];

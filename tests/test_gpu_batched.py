@@ -128,3 +128,32 @@ def test_batched_noise_workload_shapes():
     for r, e in zip(b.reports(), e0):
         assert r["status"] == 0 and np.isfinite(r["E"]) and r["E"] < e
     b.close()
+
+
+def test_batched_workload_tracks_fp64_flows():
+    """Four lattices of the 64-lattice workload at their full sizes, flowed
+    200 iterations in one FP32 batch, against each lattice's FP64 flow alone:
+    energies and charges agree to 1e-5 relative, arrests are the same."""
+    wls = workloads.batched_noise(count=64, steps=200)[:4]
+    lats, states = [], []
+    for w in wls:
+        lat = sk.Lattice(w.n, w.h, w.m, 32)
+        st = sk.State(lat, DEV)
+        sk.init_field(lat, sk.Seed.from_spec(w.seed), st)
+        lats.append(lat)
+        states.append(st)
+    b = sk.Batch(lats, states, [w.dt for w in wls])
+    b.step(200)
+    torch.cuda.synchronize()
+    for w, lat, st in zip(wls, lats, states):
+        r32 = sk.read_report(lat, st)
+        l64 = sk.Lattice(w.n, w.h, w.m, 64)
+        s64 = sk.State(l64, DEV)
+        sk.init_field(l64, sk.Seed.from_spec(w.seed), s64)
+        r64 = sk.flow_step(l64, w.dt, 200, sk.ARRESTED, s64)
+        assert r32["status"] == 0 and r64["status"] == 0
+        assert r32["steps"] == r64["steps"] == 200
+        assert r32["E"] == pytest.approx(r64["E"], rel=1e-5), w.n
+        assert r32["B"] == pytest.approx(r64["B"], rel=1e-5, abs=1e-6), w.n
+        assert r32["arrests"] == r64["arrests"], w.n
+    b.close()
