@@ -506,7 +506,7 @@ __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &
         // 1 - phi^0 from the pion components where it cancels (phi^0 >= 0)
         const float2 pq = __fmul2_rn(ph.b, ph.b);
         const float pi2 = fmaf(ph.a.y, ph.a.y, pq.x + pq.y);
-        a32.e0 += ph.a.x >= 0.f ? __fdividef(pi2, 1.f + ph.a.x) : 1.f - ph.a.x;
+        a32.e0 += ph.a.x >= 0.f ? pi2 * rcp_approx(1.f + ph.a.x) : 1.f - ph.a.x;
         a32.b += det;
         a32.f2 += f2;
         a32.fmax2 = fmaxf(a32.fmax2, f2);

@@ -115,11 +115,19 @@ __device__ __forceinline__ T fd2(T m2v, T m1v, T c, T p1v, T p2v)
 // phi^0 >= 0, as |pi|^2 / (1 + phi^0) with pi = (phi^1, phi^2, phi^3), which
 // FP32 holds to full relative precision; for phi^0 < 0 there is no
 // cancellation.  FP64 uses the difference as written.
+// Reciprocal on the special-function unit (at most 1 ulp from 1/x for
+// normal x); the denominators it gets here lie in [1, 2].
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 template <typename T> __device__ __forceinline__ T one_minus_phi0(const T phi[4])
 {
     if constexpr (sizeof(T) == 4) {
         const T pi2 = phi[1] * phi[1] + phi[2] * phi[2] + phi[3] * phi[3];
-        return phi[0] >= T(0) ? __fdividef(pi2, T(1) + phi[0]) : T(1) - phi[0];
+        return phi[0] >= T(0) ? pi2 * rcp_approx(T(1) + phi[0]) : T(1) - phi[0];
     } else {
         return T(1) - phi[0];
     }
