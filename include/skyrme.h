@@ -145,7 +145,11 @@ skyrme_status skyrme_load_field(const skyrme_lattice *lat, skyrme_state *st, voi
  * velocity is zeroed when E_n > E_{n-1}; then v += dt F, phi = (phi + dt v)/|.|
  * at interior sites.  `report` (nullable, host) receives the latest
  * iteration's results, which synchronises the stream.  Returns
- * SKYRME_ENONFINITE (sticky) once a non-finite value has appeared. */
+ * SKYRME_ENONFINITE (sticky) once a non-finite value has appeared.
+ * From 256 iterations on, on a stream that is not being captured, the call
+ * captures 128 iterations into a CUDA graph on a stream of its own and
+ * replays it on `stream` (fewer GPU cycles per launch); the graph and that
+ * stream are host and driver resources released before the call returns. */
 skyrme_status skyrme_flow_step(const skyrme_lattice *lat, double dt, int nsteps, int mode,
                                skyrme_state *st, skyrme_report *report, void *stream);
 /* ---- the flow as a CUDA graph ----

@@ -248,6 +248,49 @@ def test_graph_replay_equals_flow_step():
         assert torch.equal(a.field(), b.field()) and torch.equal(a.velocity(), b.velocity())
 
 
+@pytest.mark.parametrize("prec", [32, 64])
+def test_long_flow_step_call_equals_short_calls(prec):
+    """A call of 300 iterations runs as replays of a captured 128-iteration
+    graph plus 44 direct iterations; it must reproduce three calls of 100
+    (launched directly) bit for bit, in every mode."""
+    n, h, m = (28, 30, 32), 0.2, 1.0
+    for mode in (sk.ARRESTED, sk.NEWTON, sk.GRADIENT):
+        lat = sk.Lattice(n, h, m, prec)
+        a, b = sk.State(lat, DEV), sk.State(lat, DEV)
+        for st in (a, b):
+            sk.init_field(lat, sk.Seed.rational_map(4, 1.5), st)
+        ra = sk.flow_step(lat, 0.01, 300, mode, a)
+        for _ in range(3):
+            rb = sk.flow_step(lat, 0.01, 100, mode, b)
+        assert ra["steps"] == rb["steps"] == 300
+        assert ra["E"] == rb["E"] and ra["arrests"] == rb["arrests"], mode
+        assert torch.equal(a.field(), b.field()) and torch.equal(a.velocity(), b.velocity())
+
+
+def test_long_flow_step_call_inside_a_user_capture_launches_directly():
+    """flow_step on a stream that the caller is capturing (here a torch CUDA
+    graph) must not start a capture of its own: its launches go into the
+    caller's graph, whose replay then equals the same call made directly."""
+    n, h, m = (28, 30, 32), 0.2, 1.0
+    lat = sk.Lattice(n, h, m, 32)
+    a, b = sk.State(lat, DEV), sk.State(lat, DEV)
+    for st in (a, b):
+        sk.init_field(lat, sk.Seed.rational_map(4, 1.5), st)
+    sk.flow_step(lat, 0.01, 1, sk.ARRESTED, a)
+    sk.flow_step(lat, 0.01, 1, sk.ARRESTED, b)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream(DEV)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        sk.flow_step(lat, 0.01, 300, sk.ARRESTED, b, report=False, stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    ra = sk.flow_step(lat, 0.01, 300, sk.ARRESTED, a)
+    rb = sk.read_report(lat, b)
+    assert rb["steps"] == ra["steps"] == 301 and rb["E"] == ra["E"]
+    assert torch.equal(a.field(), b.field())
+
+
 def load_golden(name):
     import os
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
