@@ -354,6 +354,19 @@ skyrme_status skyrme_energy_static(const skyrme_lattice *lat, const void *phi, d
 typedef enum { SKYRME_PEAK_FP32 = 0, SKYRME_PEAK_FP64 = 1 } skyrme_peak_kind;
 skyrme_status skyrme_measure_fma_peak(int kind, double *tflops, void *stream);
 
+/* ---- failure detection ----
+ * skyrme_selftest_wait: exercises the bounded device-side wait that the step
+ * kernels use on their TMA plane copies.  One thread waits on a shared-memory
+ * mbarrier that nothing completes, gives up after limit_seconds
+ * (0 < limit_seconds <= 10, else SKYRME_EINVAL) and records the timeout in
+ * the state's control block, as a step kernel does when a copy never lands.
+ * Synchronises `stream` and returns the recorded status: SKYRME_ETIMEOUT.
+ * The status is sticky in the state (flow calls and skyrme_read_report see
+ * it) until skyrme_init_field or skyrme_load_field resets the control block;
+ * the CUDA context stays usable. */
+skyrme_status skyrme_selftest_wait(const skyrme_lattice *lat, skyrme_state *st,
+                                   double limit_seconds, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -132,6 +132,8 @@ _SIGNATURES = {
     "skyrme_graph_create": (ctypes.c_int, [ctypes.POINTER(c_lattice), ctypes.c_double,
                                            ctypes.c_int, ctypes.c_int, ctypes.POINTER(c_state), _P,
                                            ctypes.POINTER(ctypes.c_void_p)]),
+    "skyrme_selftest_wait": (ctypes.c_int, [ctypes.POINTER(c_lattice), ctypes.POINTER(c_state),
+                                            ctypes.c_double, _P]),
     "skyrme_graph_launch": (ctypes.c_int, [_P, _P]),
     "skyrme_graph_destroy": (ctypes.c_int, [_P]),
 }
@@ -494,6 +496,15 @@ def measure_fma_peak(kind: int, stream=None) -> float:
     _check(load().skyrme_measure_fma_peak(int(kind), ctypes.byref(out), _stream_ptr(stream)),
            "skyrme_measure_fma_peak")
     return out.value
+
+
+def selftest_wait(lat: Lattice, st: State, limit_seconds: float = 0.05, stream=None) -> int:
+    """Run the bounded-wait self-test (skyrme_selftest_wait) on the state's
+    control block and return its status code (5, SKYRME_ETIMEOUT, when the
+    wait gave up as it should)."""
+    cl, cs = lat.c(), st.c()
+    return int(load().skyrme_selftest_wait(ctypes.byref(cl), ctypes.byref(cs),
+                                           float(limit_seconds), _stream_ptr(stream, st.device)))
 
 
 class FlowGraph:

@@ -14,6 +14,7 @@ namespace skyrme {
 int max_constituents();
 int max_smoothing_half_width();
 bool f32_fast_path_available(const skyrme_lattice &lat);
+cudaError_t launch_wait_selftest(void *ctrl, unsigned long long limit_ns, cudaStream_t s);
 cudaError_t launch_iterations_f32_fast(const skyrme_lattice &lat, const FlowArgs &a, int nsteps,
                                        cudaStream_t s);
 int f32_fast_blocks(const skyrme_lattice &lat);
@@ -453,6 +454,21 @@ skyrme_status skyrme_graph_destroy(skyrme_graph *g)
     if (g->graph) cudaGraphDestroy(g->graph);
     delete g;
     return SKYRME_OK;
+}
+
+skyrme_status skyrme_selftest_wait(const skyrme_lattice *lat, skyrme_state *st,
+                                   double limit_seconds, void *stream)
+{
+    skyrme_status rc = check_state(lat, st);
+    if (rc != SKYRME_OK) return rc;
+    if (!(limit_seconds > 0.0) || !(limit_seconds <= 10.0)) return SKYRME_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(launch_wait_selftest(st->scratch, (unsigned long long)(limit_seconds * 1e9), s),
+       "wait self-test kernel");
+    Ctrl c;
+    rc = copy_ctrl(*st, &c, s);
+    if (rc != SKYRME_OK) return rc;
+    return static_cast<skyrme_status>(c.status);
 }
 
 skyrme_status skyrme_read_report(const skyrme_lattice *lat, const skyrme_state *st,

@@ -1176,6 +1176,28 @@ static bool balanced_split(long long units, int nix, int grid, CtaSplit &out)
     return out.n > 0;
 }
 
+// Self-test of the bounded wait the step kernels use on their TMA copies:
+// thread 0 waits on a shared-memory mbarrier that nothing ever completes,
+// gives up after limit_ns, and records SKYRME_ETIMEOUT in the control block,
+// as a step kernel does when a plane copy never lands.  Nothing faults or
+// hangs: the kernel returns after the limit.
+__global__ void k_wait_selftest(Ctrl *c, unsigned long long limit_ns)
+{
+    __shared__ unsigned long long bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait(&bar, 0, limit_ns)) atomicExch(&c->status, (int)DEV_TIMEOUT);
+}
+
+cudaError_t launch_wait_selftest(void *ctrl, unsigned long long limit_ns, cudaStream_t s)
+{
+    k_wait_selftest<<<1, 32, 0, s>>>(static_cast<Ctrl *>(ctrl), limit_ns);
+    return cudaGetLastError();
+}
+
 // nsteps iterations of a single lattice: the step kernel and, in ARRESTED
 // mode, the fix-up check.  The tensor maps, the work split and the fix-up
 // descriptor are the same for every iteration, so they are prepared once per

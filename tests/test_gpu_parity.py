@@ -227,6 +227,27 @@ def test_nonfinite_input_is_reported():
         sk.energy(lat, st)
 
 
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    """The bounded wait of the step kernels, run out on purpose on an
+    mbarrier that nothing completes: the kernel returns after the limit with
+    SKYRME_ETIMEOUT recorded, flow calls report it until the state is reset,
+    and the device keeps working."""
+    import time
+    lat = sk.Lattice((20, 20, 20), 0.2, 1.0, 32)
+    st = sk.State(lat, DEV)
+    sk.init_field(lat, sk.Seed.rational_map(1, 1.0), st)
+    t0 = time.perf_counter()
+    assert sk.selftest_wait(lat, st, 0.05) == 5
+    assert 0.04 < time.perf_counter() - t0 < 5.0
+    assert sk.read_report(lat, st)["status"] == 5
+    with pytest.raises(sk.SkyrmeError) as ei:
+        sk.flow_step(lat, 0.01, 2, sk.ARRESTED, st)
+    assert ei.value.status == 5
+    sk.init_field(lat, sk.Seed.rational_map(1, 1.0), st)  # resets the control block
+    rep = sk.flow_step(lat, 0.01, 2, sk.ARRESTED, st)
+    assert rep["status"] == 0 and rep["steps"] == 2 and math.isfinite(rep["E"])
+
+
 def test_graph_replay_equals_flow_step():
     """A captured graph of K iterations replayed twice reproduces 2K calls of
     skyrme_flow_step bit for bit (the flow state lives on the device)."""
