@@ -42,6 +42,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0     # GB/s, used only when the measured peaks file is absent
 FLOPS_PER_SITE = 590      # algorithmic FP operations per site-update (FMA = 2)
 FLOPS_PER_SITE_EXT = 860  # with the Section 7.8 potentials and sextic term
+FLOPS_PER_SITE_POT = 607  # with the Section 7.8 potentials only
 # FP64 operations (FMA = 2) the diagnostic kernels execute, from ncu op
 # counts (dadd + dmul + 2 dfma) on the 128^3 field; each formula is evaluated
 # once per site and pass, so these are their arithmetic:
@@ -106,14 +107,16 @@ def oracle_mass(oracle, wl):
 
 
 def flops_per_site(wl):
-    return FLOPS_PER_SITE_EXT if wl.extended else FLOPS_PER_SITE
+    if not wl.extended:
+        return FLOPS_PER_SITE
+    return FLOPS_PER_SITE_EXT if wl.c6 != 0.0 else FLOPS_PER_SITE_POT
 
 
 def step_kernel_key(wl, prec):
     """Name of the step kernel a workload runs on (the traffic record key):
-    the FP32 streaming kernel for the standard model, the tile kernels for
-    FP64 and for extended models."""
-    if prec == 32 and not wl.extended:
+    the FP32 streaming kernel for the standard model and the potentials, the
+    tile kernels for FP64 and for the sextic term."""
+    if prec == 32 and wl.streaming:
         return f"step_f32_{wl.name}"
     return f"step_tile_f{prec}_{wl.name}" if wl.extended else f"step_f64_{wl.name}"
 

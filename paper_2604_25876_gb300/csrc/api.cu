@@ -249,8 +249,9 @@ skyrme_status skyrme_load_field(const skyrme_lattice *lat, skyrme_state *st, voi
 static skyrme_status launch_iterations(const skyrme_lattice &lat, const FlowArgs &a, int nsteps,
                                        cudaStream_t s)
 {
-    // the streaming FP32 kernel implements the standard model only
-    const bool fast = lat.precision == 32 && !lattice_extended(lat) && f32_fast_path_available(lat);
+    // the streaming FP32 kernel implements the standard model and the
+    // Section 7.8 potentials; the sextic term runs on the tile kernels
+    const bool fast = lat.precision == 32 && lat.c6 == 0.0 && f32_fast_path_available(lat);
     if (fast) {
         CK(launch_iterations_f32_fast(lat, a, nsteps, s), "step and fix-up kernels (fp32)");
         return SKYRME_OK;

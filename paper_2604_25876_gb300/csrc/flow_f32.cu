@@ -78,6 +78,10 @@ struct InstDesc {
     float2 s1, s2, s0;     // second-derivative weights / h^2
     float2 dt, dt2;        // dt and 2 dt
     float m2;
+    // Section 7.8 potentials (the POT kernels): squared masses of the
+    // modified-pion, loosely and lightly bound terms
+    float my2, mz2, mw2;
+    float e0_scale;        // E0 = h^3 e0_scale sum(e0 slot): 2 m^2 (standard) or 1 (POT)
     float h3_hi, h3_lo;    // h^3 as an unevaluated float sum
     int mode;
 };
@@ -436,7 +440,7 @@ __device__ __forceinline__ void plane_record(const float4 (*DY)[TZ + 4], const I
 // Euler-Lagrange force of Eq. (3.3) projected on the tangent space, the
 // symplectic update with renormalisation, and the energy, charge and force
 // densities into a32 (valid sites only).
-template <int TY, int TZ>
+template <int TY, int TZ, bool POT = false>
 __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &M2,
                                             const PlaneVals &M1, const PlaneVals &C,
                                             const PlaneVals &Q1, const PlaneVals &Q2, float2 xc1,
@@ -472,6 +476,19 @@ __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &
     // brace of the Euler-Lagrange equation; G = -2 (brace + m^2 e_0)
     P4 br = fma(bc(ccz), dzc, fma(bc(ccy), dyc, fma(bc(ccx), dx, fma(bc(1.f + tra), L, mul(bc(-1.f), Ha)))));
     br.a.x += D.m2;
+    // 1 - phi^0 from the pion components where it cancels (phi^0 >= 0)
+    auto one_minus_phi0 = [&]() {
+        const float2 pq = __fmul2_rn(ph.b, ph.b);
+        const float pi2 = fmaf(ph.a.y, ph.a.y, pq.x + pq.y);
+        return ph.a.x >= 0.f ? pi2 * rcp_approx(1.f + ph.a.x) : 1.f - ph.a.x;
+    };
+    float u = 0.f;
+    if constexpr (POT) {
+        // d/dphi^0 of the Section 7.8 potentials m_y^2 (1 - phi0^2) + m_z^2 u^2
+        // + m_w^2 u^4 / 2, u = 1 - phi^0, in the brace (G = -2 brace)
+        u = one_minus_phi0();
+        br.a.x += fmaf(D.my2, ph.a.x, u * fmaf(D.mw2 * u, u, D.mz2));
+    }
     // F = -G + (G.phi) phi = 2 (br - (br.phi) phi)
     const float bp = dot(br, ph);
     const P4 Fh = fma(bc(-bp), ph, br);
@@ -503,10 +520,13 @@ __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &
         if (mode != MODE_GRADIENT) __stcs(vout + si, st4(vnew));
         a32.e2 += tra;
         a32.e4 += e4;
-        // 1 - phi^0 from the pion components where it cancels (phi^0 >= 0)
-        const float2 pq = __fmul2_rn(ph.b, ph.b);
-        const float pi2 = fmaf(ph.a.y, ph.a.y, pq.x + pq.y);
-        a32.e0 += ph.a.x >= 0.f ? pi2 * rcp_approx(1.f + ph.a.x) : 1.f - ph.a.x;
+        if constexpr (POT) {
+            // the whole potential: 2 m^2 u + m_y^2 u (2 - u) + m_z^2 u^2 + m_w^2 u^4 / 2
+            const float u2 = u * u;
+            a32.e0 += fmaf(2.f * D.m2, u, fmaf(D.my2, u * (2.f - u), u2 * fmaf(0.5f * D.mw2, u2, D.mz2)));
+        } else {
+            a32.e0 += one_minus_phi0();
+        }
         a32.b += det;
         a32.f2 += f2;
         a32.fmax2 = fmaxf(a32.fmax2, f2);
@@ -584,7 +604,7 @@ __device__ __forceinline__ void finish_lattice(const InstDesc &D, Ctrl *c, int c
     const DF bfac = {(float)kB, (float)(kB - (double)(float)kB)};
     const DF h3 = {D.h3_hi, D.h3_lo};
     const DF E2 = df_mul(h3, t[0]), E4 = df_mul(h3, t[1]);
-    const DF E0 = df_mul(h3, df_mul(DF{2.f * D.m2, 0.f}, t[2]));  // e0 = 2 m^2 (1 - phi^0)
+    const DF E0 = df_mul(h3, df_mul(DF{D.e0_scale, 0.f}, t[2]));  // 2 m^2 sum(1 - phi^0), or the potentials' sum
     const DF E = df_add(df_add(E2, E4), E0);
     const DF B = df_mul(h3, df_mul(bfac, t[3]));
     const DF V = df_add(df_add(df_neg(E2), E4), df_mul(DF{-3.f, 0.f}, E0));
@@ -624,7 +644,7 @@ __device__ __forceinline__ void finish_lattice(const InstDesc &D, Ctrl *c, int c
 // lattices come from `table` (ninst entries, ordered by unit_start); otherwise
 // from `one`.  dry != 0 (autotuning): outputs land in the inactive buffers and
 // the control blocks are left as they were.
-template <int TY, int TZ, bool BATCHED>
+template <int TY, int TZ, bool BATCHED, bool POT = false>
 __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
     k_step_f32(const __grid_constant__ InstDesc one, const __grid_constant__ CtaSplit split,
                const InstDesc *__restrict__ table, int ninst, long long total_units, int dry)
@@ -718,7 +738,7 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
                     const uint32_t g3n = g3 == 2 ? 0 : g3 + 1;  // (g + 1) % 3 == (g - 2) % 3
                     const int x = pp - 2;
                     if (x >= xs)
-                        centre_site<TY, TZ>(D, ring[(k + 1) % 5], ring[(k + 2) % 5], ring[(k + 3) % 5],
+                        centre_site<TY, TZ, POT>(D, ring[(k + 1) % 5], ring[(k + 2) % 5], ring[(k + 3) % 5],
                                             ring[(k + 4) % 5], ring[k], D.c1, D.c2,
                                             &sm.inpl[g3n][0][tid], &sm.inyz[g3n][tid],
                                             &sm.vpl[s][ty][tz], use_v,
@@ -1051,6 +1071,10 @@ static bool fill_desc(InstDesc &d, const skyrme_lattice &lat, const skyrme_state
     d.s2 = pair(-1.0 / 12.0 * ih2);
     d.s0 = pair(-2.5 * ih2);
     d.m2 = (float)(lat.m * lat.m);
+    d.my2 = (float)(lat.m_y * lat.m_y);
+    d.mz2 = (float)(lat.m_z * lat.m_z);
+    d.mw2 = (float)(lat.m_w * lat.m_w);
+    d.e0_scale = lattice_potentials(lat) ? 1.f : 2.f * d.m2;
     d.dt = make_float2((float)dt, (float)dt);
     d.dt2 = make_float2(2.f * (float)dt, 2.f * (float)dt);
     const double h3 = lat.h * lat.h * lat.h;
@@ -1233,8 +1257,31 @@ cudaError_t launch_iterations_f32_fast(const skyrme_lattice &lat, const FlowArgs
     const long long rows = (long long)(lat.n[0] - 4) * (lat.n[1] - 4);
     const int fix_blocks = (int)std::max(1LL, std::min((long long)sm_count() * 2, (rows + 15) / 16));
 
+    const bool pot = lattice_potentials(lat);
+    if (pot) {
+        // the potentials variant of the single-lattice kernel
+        static std::mutex mu;
+        static bool done[64] = {false};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        std::lock_guard<std::mutex> lock(mu);
+        if (dev < 64 && !done[dev]) {
+            cudaError_t e = cudaFuncSetAttribute(k_step_f32<16, 32, false, true>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)sizeof(StepSmem<16, 32>));
+            if (e != cudaSuccess) return e;
+            done[dev] = true;
+        }
+    }
     for (int k = 0; k < nsteps; ++k) {
-        cudaError_t e = launch_tile<false>(tile, ds[0], split, nullptr, 1, ds[0].units, grid, 0, s);
+        cudaError_t e;
+        if (pot) {
+            k_step_f32<16, 32, false, true><<<(unsigned)grid, 16 * 32, sizeof(StepSmem<16, 32>), s>>>(
+                ds[0], split, nullptr, 1, ds[0].units, 0);
+            e = cudaGetLastError();
+        } else {
+            e = launch_tile<false>(tile, ds[0], split, nullptr, 1, ds[0].units, grid, 0, s);
+        }
         if (e != cudaSuccess) return e;
         if (a.mode == SKYRME_ARRESTED) {
             k_fixup_one<<<fix_blocks, 512, 0, s>>>(fx);

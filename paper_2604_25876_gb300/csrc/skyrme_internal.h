@@ -48,6 +48,12 @@ inline bool lattice_extended(const skyrme_lattice &lat)
     return lat.m_y != 0.0 || lat.m_z != 0.0 || lat.m_w != 0.0 || lat.c6 != 0.0;
 }
 
+// A lattice with a Section 7.8 potential switched on (m_y, m_z or m_w).
+inline bool lattice_potentials(const skyrme_lattice &lat)
+{
+    return lat.m_y != 0.0 || lat.m_z != 0.0 || lat.m_w != 0.0;
+}
+
 // Kernels (asynchronous, return the launch error)
 cudaError_t launch_step(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s);
 cudaError_t launch_fixup(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s);

@@ -119,6 +119,35 @@ def test_fp32_trajectory_tracks_fp64_oracle():
     assert rep["E6"] == pytest.approx(oreps[-1]["E6"], rel=1e-5)
 
 
+POTENTIALS = [dict(m_y=0.9, m_z=0.0, m_w=0.0), dict(m_y=0.0, m_z=0.6, m_w=0.0),
+              dict(m_y=0.0, m_z=0.0, m_w=1.1), dict(m_y=0.9, m_z=0.6, m_w=1.1)]
+
+
+@pytest.mark.parametrize("pot", range(len(POTENTIALS)))
+def test_fp32_potentials_flow_on_the_streaming_kernel_tracks_the_oracle(pot):
+    """With the potentials on and no sextic term the FP32 flow runs on the
+    streaming kernel.  Its first energy equals the tile kernel's evaluation of
+    the same field, and 50 arrested iterations follow the FP64 oracle: field
+    within 1e-4, energy and virial within 1e-5, the same arrests."""
+    kw = dict(POTENTIALS[pot], c6=0.0)
+    n, h = (40, 40, 40), 0.2
+    phi = oracle.seed_rational_map(n, h, 4, 2.0)
+    ost = oracle.new_state(phi)
+    oreps = oracle.flow(ost, h, model(**kw), 0.05 * h, 50, reports=True)
+    lat, st = on_gpu(phi, h, 32, **kw)
+    e_tile = sk.energy(lat, st)
+    r1 = sk.flow_step(lat, 0.05 * h, 1, sk.ARRESTED, st)
+    assert r1["E"] == pytest.approx(e_tile["E"], rel=2e-6)
+    assert r1["E0"] == pytest.approx(e_tile["E0"], rel=2e-6)
+    rep = sk.flow_step(lat, 0.05 * h, 49, sk.ARRESTED, st)
+    assert rep["status"] == 0 and rep["steps"] == 50 and rep["E6"] == 0.0
+    assert np.max(np.abs(st.field().double().cpu().numpy() - ost.phi)) < 1e-4
+    assert rep["E"] == pytest.approx(oreps[-1]["E"], rel=1e-5)
+    assert rep["E0"] == pytest.approx(oreps[-1]["E0"], rel=1e-5)
+    assert rep["virial"] == pytest.approx(oreps[-1]["virial"], rel=1e-4, abs=1e-5 * rep["E"])
+    assert rep["arrests"] == sum(r["arrested"] for r in oreps)
+
+
 def test_standard_model_report_has_no_sextic_part_and_vacuum_stays_fixed():
     for prec in (32, 64):
         lat = sk.Lattice((20, 21, 22), 0.2, 1.0, prec)

@@ -71,6 +71,12 @@ class Workload:
     def extended(self) -> bool:
         return any(v != 0.0 for v in (self.m_y, self.m_z, self.m_w, self.c6))
 
+    @property
+    def streaming(self) -> bool:
+        """True where the FP32 flow runs on the streaming kernel: the
+        standard model and the potentials without the sextic term."""
+        return self.c6 == 0.0
+
 
 def ball_positions(rng: np.random.Generator, count: int, radius: float) -> np.ndarray:
     """Uniform points in a ball, by rejection from the enclosing cube."""
@@ -124,6 +130,16 @@ def b4_sextic_128() -> Workload:
                                 "BPS sextic term c6=1, FP32 bulk with FP64 reductions")
 
 
+def b4_lightly_bound_128() -> Workload:
+    """The 128^3 B=4 workload with the lightly bound potential m_w^2 (1 - phi^0)^4 / 2
+    of Section 7.8 added to the pion mass (m_w = 1, a synthetic choice) and no
+    sextic term: an extended model that the FP32 streaming kernel runs."""
+    return Workload("b4_lightly_bound_128", (128, 128, 128), 0.1, 1.0, 5000, 32,
+                    SeedSpec(kind="rational_map", B=4, profile_scale=2.0), 0.02, m_w=1.0,
+                    description="B=4 cubic rational map f=pi exp(-r/2), 128^3, h=0.1, m=1, "
+                                "lightly bound potential m_w=1, FP32 bulk with FP64 reductions")
+
+
 def b8_cluster_256() -> Workload:
     return Workload("b8_cluster_256", (256, 256, 256), 0.08, 1.0, 20000, 32,
                     cluster_seed(8, 3.0, 8), 0.016,
@@ -153,6 +169,7 @@ ALL = {
     "b1_hedgehog_48": b1_hedgehog_48,
     "b4_cubic_128": b4_cubic_128,
     "b4_sextic_128": b4_sextic_128,
+    "b4_lightly_bound_128": b4_lightly_bound_128,
     "b8_cluster_256": b8_cluster_256,
     "b32_cluster_512": b32_cluster_512,
 }
