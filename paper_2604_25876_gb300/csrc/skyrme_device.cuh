@@ -179,6 +179,11 @@ __device__ __forceinline__ void extension_terms(const T phi[4], const T d1[3][4]
     const T u2 = u * u;
     G[0] -= T(2) * (x.my2 * phi[0] + x.mz2 * u + x.mw2 * u2 * u);
     e0x = x.my2 * one_minus_phi0_sq<T>(phi, u) + x.mz2 * u2 + T(0.5) * x.mw2 * u2 * u2;
+    e6 = T(0);
+    // potentials only (a uniform branch): the FP64 kernels skip the sextic
+    // arithmetic; FP32 flows without the sextic term run on the streaming kernel
+    if constexpr (sizeof(T) == 8)
+        if (x.c6 == T(0)) return;
     T P[4], Q0[4], Q1[4], Q2[4];
     cross3<T>(d1[0], d1[1], d1[2], P);
     cross3<T>(phi, d1[1], d1[2], Q0);
