@@ -4,7 +4,6 @@ lookup of recorded DRAM traffic, and the bounds that keep the bench short."""
 import json
 import os
 
-import numpy as np
 import pytest
 
 import bench
