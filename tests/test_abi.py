@@ -195,3 +195,17 @@ def test_extension_coefficients_are_validated_and_gated_without_cuda():
     assert not out.value
     # a null result pointer
     assert lib.skyrme_sextic_energy(ctypes.byref(c), ctypes.byref(st), None, None) == 1
+
+
+def test_wait_selftest_rejects_bad_arguments_without_cuda():
+    lib = sk.load()
+    lat = sk.Lattice((16, 16, 16), 0.2, 1.0, 32).c()
+    # fake, well-formed device addresses: the checks run before any CUDA call
+    st = sk.c_state((ctypes.c_void_p * 2)(0x10000, 0x20000), (ctypes.c_void_p * 2)(0x30000, 0x40000),
+                    ctypes.c_void_p(0x50000), ctypes.c_size_t(1 << 30))
+    for limit in (0.0, -1.0, 10.5, float("nan"), float("inf")):
+        assert lib.skyrme_selftest_wait(ctypes.byref(lat), ctypes.byref(st), limit, None) == 1
+    assert lib.skyrme_selftest_wait(ctypes.byref(lat), None, 0.05, None) == 1
+    small = sk.c_state((ctypes.c_void_p * 2)(0x10000, 0x20000), (ctypes.c_void_p * 2)(0x30000, 0x40000),
+                       ctypes.c_void_p(0x50000), ctypes.c_size_t(16))
+    assert lib.skyrme_selftest_wait(ctypes.byref(lat), ctypes.byref(small), 0.05, None) == 2
