@@ -118,6 +118,8 @@ def _load():
             lib.orc_seed_rational_map.restype = ctypes.c_int
             lib.orc_seed_product.argtypes = [I3, D, ctypes.c_int, P, P, D, ctypes.c_int, P]
             lib.orc_seed_noise.argtypes = [I3, D, D, D, ctypes.c_uint64, P]
+            lib.orc_noise_components.argtypes = [I3, D, D, D, ctypes.c_uint64, P]
+            lib.orc_gaussian_smooth.argtypes = [I3, D, D, P, P]
             lib.orc_apply_vacuum_boundary.argtypes = [I3, P]
             lib.orc_rational_map_field.argtypes = [I3, D, ctypes.c_int, D, P, P, P]
             lib.orc_rational_map_field.restype = ctypes.c_int
@@ -342,6 +344,21 @@ def seed_noise(n, h: float, radius: float, sigma: float, seed: int):
     phi = _field(n)
     _load().orc_seed_noise(_dims(n), h, radius, sigma, int(seed), _ptr(phi))
     return phi
+
+
+def noise_components(n, h: float, radius: float, sigma: float, seed: int):
+    """The smoothed-noise seed's noise field before it is added to the vacuum."""
+    out = _field(n)
+    _load().orc_noise_components(_dims(n), h, radius, sigma, int(seed), _ptr(out))
+    return out
+
+
+def gaussian_smooth(field: np.ndarray, h: float, sigma: float):
+    """The noise seed's separable Gaussian smoothing applied to a 4-component field."""
+    a = np.ascontiguousarray(field, dtype=np.float64)
+    out = np.zeros_like(a)
+    _load().orc_gaussian_smooth(_dims(a.shape[:3]), h, sigma, _ptr(a), _ptr(out))
+    return out
 
 
 def apply_vacuum_boundary(phi: np.ndarray):

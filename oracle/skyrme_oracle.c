@@ -824,41 +824,27 @@ double orc_normal(uint64_t seed, uint64_t i)
     return sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
 }
 
-void orc_seed_noise(const int n[3], double h, double radius, double sigma,
-                    uint64_t seed, double *phi)
+/* Separable discrete Gaussian smoothing of a 4-component field (the noise
+ * recipe's smoothing step): weights exp(-(k h)^2 / (2 sigma^2)) for
+ * |k| <= K = ceil(4 sigma / h), divided by their sum; applied along x, then
+ * y, then z, with sites outside the box contributing zero. */
+void orc_gaussian_smooth(const int n[3], double h, double sigma, const double *in,
+                         double *out)
 {
-    size_t ns = (size_t)n[0] * n[1] * n[2], s;
-    int K = (int)ceil(4.0 * sigma / h), k, axis, x, q;
+    size_t ns = (size_t)n[0] * n[1] * n[2];
+    int K = (int)ceil(4.0 * sigma / h), k, axis, x;
     double *w = (double *)malloc((size_t)(2 * K + 1) * sizeof(double));
-    double *a = (double *)calloc(4 * ns, sizeof(double));
+    double *a = (double *)malloc(4 * ns * sizeof(double));
     double *b = (double *)calloc(4 * ns, sizeof(double));
     double wsum = 0.0;
-    nsum mean[4], var[4];
-    double count = 0.0;
 
-    /* i.i.d. N(0,1) per component inside the ball */
-#pragma omp parallel for schedule(static)
-    for (x = 0; x < n[0]; x++) {
-        int y, z, c;
-        for (y = 0; y < n[1]; y++)
-            for (z = 0; z < n[2]; z++) {
-                double cx = coord(n, h, 0, x), cy = coord(n, h, 1, y),
-                       cz = coord(n, h, 2, z);
-                size_t si = site_index(n, x, y, z);
-                if (cx * cx + cy * cy + cz * cz <= radius * radius)
-                    for (c = 0; c < 4; c++)
-                        a[4 * si + c] = orc_normal(seed, 4 * (uint64_t)si + c);
-            }
-    }
-
-    /* Gaussian weights on the lattice, truncated at 4 sigma, summing to one */
+    memcpy(a, in, 4 * ns * sizeof(double));
     for (k = -K; k <= K; k++) {
         w[k + K] = exp(-(k * h) * (k * h) / (2.0 * sigma * sigma));
         wsum += w[k + K];
     }
     for (k = 0; k <= 2 * K; k++) w[k] /= wsum;
 
-    /* separable convolution along x, then y, then z; zero outside the box */
     for (axis = 0; axis < 3; axis++) {
 #pragma omp parallel for schedule(static)
         for (x = 0; x < n[0]; x++) {
@@ -884,6 +870,43 @@ void orc_seed_noise(const int n[3], double h, double radius, double sigma,
         }
         memcpy(a, b, 4 * ns * sizeof(double));
     }
+    memcpy(out, a, 4 * ns * sizeof(double));
+    free(w);
+    free(a);
+    free(b);
+}
+
+/* The noise 4-vector field of the smoothed-noise seed before it is added to
+ * the vacuum: i.i.d. N(0,1) components (orc_normal with counter 4 s + c at
+ * site s) at sites within `radius` of the origin and 0 elsewhere, smoothed
+ * by orc_gaussian_smooth, then each component divided by its standard
+ * deviation over the ball sites. */
+void orc_noise_components(const int n[3], double h, double radius, double sigma,
+                          uint64_t seed, double *a)
+{
+    size_t ns = (size_t)n[0] * n[1] * n[2], s;
+    int x, q;
+    double *raw = (double *)calloc(4 * ns, sizeof(double));
+    nsum mean[4], var[4];
+    double count = 0.0;
+
+    /* i.i.d. N(0,1) per component inside the ball */
+#pragma omp parallel for schedule(static)
+    for (x = 0; x < n[0]; x++) {
+        int y, z, c;
+        for (y = 0; y < n[1]; y++)
+            for (z = 0; z < n[2]; z++) {
+                double cx = coord(n, h, 0, x), cy = coord(n, h, 1, y),
+                       cz = coord(n, h, 2, z);
+                size_t si = site_index(n, x, y, z);
+                if (cx * cx + cy * cy + cz * cz <= radius * radius)
+                    for (c = 0; c < 4; c++)
+                        raw[4 * si + c] = orc_normal(seed, 4 * (uint64_t)si + c);
+            }
+    }
+
+    orc_gaussian_smooth(n, h, sigma, raw, a);
+    free(raw);
 
     /* unit standard deviation per component over the ball sites */
     memset(mean, 0, sizeof(mean));
@@ -916,6 +939,15 @@ void orc_seed_noise(const int n[3], double h, double radius, double sigma,
         if (sd > 0.0)
             for (s = 0; s < ns; s++) a[4 * s + q] /= sd;
     }
+}
+
+void orc_seed_noise(const int n[3], double h, double radius, double sigma,
+                    uint64_t seed, double *phi)
+{
+    size_t ns = (size_t)n[0] * n[1] * n[2], s;
+    double *a = (double *)malloc(4 * ns * sizeof(double));
+
+    orc_noise_components(n, h, radius, sigma, seed, a);
 
     /* phi = normalise(vacuum + noise) */
     for (s = 0; s < ns; s++) {
@@ -929,13 +961,12 @@ void orc_seed_noise(const int n[3], double h, double radius, double sigma,
             phi[4 * s] = 1.0;
             phi[4 * s + 1] = phi[4 * s + 2] = phi[4 * s + 3] = 0.0;
         } else {
+            int q;
             for (q = 0; q < 4; q++) phi[4 * s + q] = t[q] / nrm;
         }
     }
     orc_apply_vacuum_boundary(n, phi);
-    free(w);
     free(a);
-    free(b);
 }
 
 /* ------------------------------------------------------------------------

@@ -182,6 +182,15 @@ void orc_seed_product(const int n[3], double h, int K, const double *pos,
  * sites, phi = normalise((1,0,0,0) + noise). */
 void orc_seed_noise(const int n[3], double h, double radius, double sigma,
                     uint64_t seed, double *phi);
+/* The seed's noise before it is added to the vacuum (4 components per
+ * site): the ball's i.i.d. normals, smoothed, rescaled per component. */
+void orc_noise_components(const int n[3], double h, double radius, double sigma,
+                          uint64_t seed, double *noise);
+/* The seed's smoothing step on any 4-component field: separable Gaussian
+ * weights exp(-(k h)^2 / 2 sigma^2), |k| <= ceil(4 sigma / h), normalised to
+ * sum 1, along x then y then z, zero outside the box. */
+void orc_gaussian_smooth(const int n[3], double h, double sigma, const double *in,
+                         double *out);
 /* Overwrite the two outer layers with the vacuum. */
 void orc_apply_vacuum_boundary(const int n[3], double *phi);
 
