@@ -10,6 +10,11 @@
  * (a report or an energy) is requested.  Errors are status codes; nothing is
  * thrown across the ABI and nothing aborts the process.
  *
+ * Device: every call works on the current CUDA device.  Device buffers passed
+ * to it must live on that device (or be managed or mapped host memory that it
+ * can address); a buffer of another GPU, or plain host memory, is rejected
+ * with SKYRME_EINVAL after the other argument checks and before any launch.
+ *
  * Lattice layout (Section 7.5.1, the text/binary file formats): site (x,y,z)
  * of an n[0] x n[1] x n[2] lattice has index ((x*n[1])+y)*n[2]+z, z fastest.
  * Each site holds the 4 components (phi^0, phi^1, phi^2, phi^3) contiguously:
@@ -28,7 +33,7 @@
 extern "C" {
 #endif
 
-#define SKYRME_ABI_VERSION 2
+#define SKYRME_ABI_VERSION 3
 
 typedef enum {
     SKYRME_OK = 0,
@@ -153,6 +158,68 @@ skyrme_status skyrme_load_field(const skyrme_lattice *lat, skyrme_state *st, voi
  * stream are host and driver resources released before the call returns. */
 skyrme_status skyrme_flow_step(const skyrme_lattice *lat, double dt, int nsteps, int mode,
                                skyrme_state *st, skyrme_report *report, void *stream);
+/* ---- x-slab decomposition of one lattice ----
+ * The step is a radius-2 stencil (Section 3: the 4th-order first, second and
+ * mixed differences reach two sites along each axis), and the arrest rule
+ * (Section 3) compares the static energy of the WHOLE lattice with the
+ * previous iteration's.  A lattice of N sites along x can therefore be cut
+ * into slabs of whole interior x-planes, each held by its own skyrme_state
+ * (on its own GPU or not), if every iteration
+ *   1. steps each slab with the prediction of the arrest decision that all
+ *      slabs share, leaving an 8-double record of the slab's sums instead of
+ *      deciding (skyrme_slab_step),
+ *   2. gives every slab the records of all slabs, in slab order (an
+ *      all-gather between ranks),
+ *   3. makes the decision over the whole lattice in every slab and applies
+ *      the arrest fix-up (skyrme_slab_finish), and
+ *   4. exchanges halos: each slab's two ghost planes on a side shared with a
+ *      neighbour receive that neighbour's two nearest interior planes of the
+ *      new field (the buffer the state's `cur` now names: after k iterations
+ *      from a load or seed, cur = k mod 2).
+ * A slab's lattice is the slab's p interior planes plus two ghost planes on
+ * each side: n = {p + 4, N1, N2}, with h, m, precision and the model of the
+ * whole lattice.  On a side that is the whole lattice's boundary the ghost
+ * planes are its two vacuum layers and never change.  The per-site results
+ * are those of the whole-lattice flow (the same kernels and per-site
+ * arithmetic); the energy sums differ only by summation order.  Load each
+ * slab with skyrme_load_field (which writes the vacuum into all outer
+ * layers), then run step 4 once before the first iteration.
+ *   skyrme_slab_step: one iteration of the slab as in skyrme_flow_step, up to
+ *     the decision.  `record` (device, 8-byte aligned, 8 doubles) receives
+ *     {sum e2, sum e4, sum e0, sum b, sum |F|^2, max |F|^2, interior sites,
+ *     sum e6} over the slab's interior sites (e0 holding the whole
+ *     potential density, b the baryon density).  Asynchronous.
+ *   skyrme_slab_finish: sums `nslabs` records (device, 8 doubles each, slab
+ *     order; 1 <= nslabs <= 4096) in that order, forms E_n, B, the virial and
+ *     delta of the whole lattice, makes the arrest decision and the report's
+ *     bookkeeping in the slab's control block, and (ARRESTED mode) corrects
+ *     a mispredicted decision at the slab's sites.  dt and mode must be
+ *     those of the skyrme_slab_step call.  Asynchronous.
+ * Both return SKYRME_EINVAL for bad arguments, as skyrme_flow_step does. */
+skyrme_status skyrme_slab_step(const skyrme_lattice *slab, double dt, int mode, skyrme_state *st,
+                               double *record, void *stream);
+skyrme_status skyrme_slab_finish(const skyrme_lattice *slab, double dt, int mode, skyrme_state *st,
+                                 const double *records, int nslabs, void *stream);
+
+/* ---- reduction diagnostic (FP32 streaming path) ----
+ * skyrme_step_densities: one iteration exactly as skyrme_flow_step runs it
+ * (the FP32 streaming kernel: precision 32 and c6 = 0, else
+ * SKYRME_EUNSUPPORTED), which also writes, for every interior site, the FP32
+ * per-site values that this iteration's energy and charge sums add up, as a
+ * float4 in the site layout: {e2, e4, u, det} with e2 = tr a, e4 of
+ * Eq. "SkyrmeEnergy_phi", det = det[phi, d_x phi, d_y phi, d_z phi] (the
+ * baryon density is -det / 2 pi^2, Eq. "B0_components") and u the potential
+ * term (1 - phi^0 for the standard model, whose density is 2 m^2 u; the whole
+ * potential density with the Section 7.8 potentials).  Other sites of `dens`
+ * (device, 16-byte aligned, n[0]*n[1]*n[2] float4) are not written.  With
+ * them a test can compare the iteration's reported E_n, B and virial with an
+ * exact sum of the very values the kernel summed, which isolates the error
+ * of the reduction.  `report` as for skyrme_flow_step.  The paper has no
+ * counterpart. */
+skyrme_status skyrme_step_densities(const skyrme_lattice *lat, double dt, int mode,
+                                    skyrme_state *st, void *dens, skyrme_report *report,
+                                    void *stream);
+
 /* ---- the flow as a CUDA graph ----
  * skyrme_graph_create captures `nsteps` iterations exactly as
  * skyrme_flow_step launches them (the step kernel and, in ARRESTED mode, the
@@ -333,8 +400,10 @@ skyrme_status skyrme_forces(const skyrme_lattice *lat, skyrme_state *st, void *f
  *   - Lattices with more than 2048 interior x-planes (n[0] - 4 > 2048) do not
  *     fit the array and are rejected with SKYRME_EINVAL, as are misaligned or
  *     null pointers.
- *   - The first call on each device looks up the array's device address with
- *     that device current; make that first call before any stream capture.
+ *   - `phi` must be on the current device (SKYRME_EINVAL otherwise).  Every
+ *     call looks up the array's device address in the current context (a
+ *     host-side lookup that allocates nothing), so a context that was reset
+ *     or replaced under the same device never receives a stale address.
  *   - Every call on a device shares the array and leaves its contents behind;
  *     each call clears what must start at zero.  Calls that overlap on the
  *     GPU (on other streams or host threads) race, so the caller serialises

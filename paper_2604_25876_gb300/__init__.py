@@ -136,6 +136,14 @@ _SIGNATURES = {
                                             ctypes.c_double, _P]),
     "skyrme_graph_launch": (ctypes.c_int, [_P, _P]),
     "skyrme_graph_destroy": (ctypes.c_int, [_P]),
+    "skyrme_slab_step": (ctypes.c_int, [ctypes.POINTER(c_lattice), ctypes.c_double, ctypes.c_int,
+                                        ctypes.POINTER(c_state), _P, _P]),
+    "skyrme_slab_finish": (ctypes.c_int, [ctypes.POINTER(c_lattice), ctypes.c_double,
+                                          ctypes.c_int, ctypes.POINTER(c_state), _P,
+                                          ctypes.c_int, _P]),
+    "skyrme_step_densities": (ctypes.c_int, [ctypes.POINTER(c_lattice), ctypes.c_double,
+                                             ctypes.c_int, ctypes.POINTER(c_state), _P,
+                                             ctypes.POINTER(c_report), _P]),
 }
 
 _lib = None
@@ -170,6 +178,28 @@ def _check(rc: int, where: str):
 def _torch():
     import torch
     return torch
+
+
+class _On:
+    """The library's functions, each called with ``device`` as the current
+    CUDA device: the C entry points run on the current device and reject
+    buffers of another one."""
+
+    def __init__(self, device):
+        self.device = device
+
+    def __getattr__(self, name):
+        fn = getattr(load(), name)
+        dev = self.device
+
+        def call(*args):
+            with _torch().cuda.device(dev):
+                return fn(*args)
+        return call
+
+
+def _on(device) -> _On:
+    return _On(device)
 
 
 def _stream_ptr(stream=None, device=None):
@@ -310,7 +340,7 @@ def _rep_dict(r: c_report) -> dict:
 def init_field(lat: Lattice, seed: Seed, st: State, stream=None):
     cl, cs = lat.c(), st.c()
     sd, keep = seed.c()
-    _check(load().skyrme_init_field(ctypes.byref(cl), ctypes.byref(sd), ctypes.byref(cs),
+    _check(_on(st.device).skyrme_init_field(ctypes.byref(cl), ctypes.byref(sd), ctypes.byref(cs),
                                     _stream_ptr(stream, st.device)), "skyrme_init_field")
     del keep
 
@@ -322,7 +352,7 @@ def load_field(lat: Lattice, st: State, phi, stream=None):
     t = torch.as_tensor(np.asarray(phi) if not isinstance(phi, torch.Tensor) else phi)
     st.phi[0].copy_(t.to(device=st.device, dtype=lat.dtype))
     cl, cs = lat.c(), st.c()
-    _check(load().skyrme_load_field(ctypes.byref(cl), ctypes.byref(cs),
+    _check(_on(st.device).skyrme_load_field(ctypes.byref(cl), ctypes.byref(cs),
                                     _stream_ptr(stream, st.device)), "skyrme_load_field")
 
 
@@ -330,17 +360,57 @@ def flow_step(lat: Lattice, dt: float, nsteps: int, mode: int, st: State, report
               stream=None):
     cl, cs = lat.c(), st.c()
     rep = c_report()
-    rc = load().skyrme_flow_step(ctypes.byref(cl), float(dt), int(nsteps), int(mode),
+    rc = _on(st.device).skyrme_flow_step(ctypes.byref(cl), float(dt), int(nsteps), int(mode),
                                  ctypes.byref(cs), ctypes.byref(rep) if report else None,
                                  _stream_ptr(stream, st.device))
     _check(rc, "skyrme_flow_step")
     return _rep_dict(rep) if report else None
 
 
+def step_densities(lat: Lattice, dt: float, mode: int, st: State, stream=None):
+    """One iteration of an FP32 streaming-kernel flow (skyrme_step_densities)
+    that also returns, as a float32 device tensor (Nx, Ny, Nz, 4), the
+    per-site values {e2, e4, u, det} its energy and charge sums added up
+    (interior sites; the rest is zero), with the iteration's report."""
+    torch = _torch()
+    dens = torch.zeros(tuple(int(v) for v in lat.n) + (4,), dtype=torch.float32,
+                       device=st.device)
+    cl, cs = lat.c(), st.c()
+    rep = c_report()
+    _check(_on(st.device).skyrme_step_densities(ctypes.byref(cl), float(dt), int(mode),
+                                                ctypes.byref(cs), ctypes.c_void_p(dens.data_ptr()),
+                                                ctypes.byref(rep), _stream_ptr(stream, st.device)),
+           "skyrme_step_densities")
+    return dens, _rep_dict(rep)
+
+
+def slab_step(lat: Lattice, dt: float, mode: int, st: State, record, stream=None):
+    """skyrme_slab_step: one iteration of an x-slab up to the arrest decision;
+    ``record`` is a float64 device tensor of 8 values that receives the slab's
+    sums."""
+    cl, cs = lat.c(), st.c()
+    _check(_on(st.device).skyrme_slab_step(ctypes.byref(cl), float(dt), int(mode),
+                                           ctypes.byref(cs), ctypes.c_void_p(record.data_ptr()),
+                                           _stream_ptr(stream, st.device)), "skyrme_slab_step")
+
+
+def slab_finish(lat: Lattice, dt: float, mode: int, st: State, records, stream=None):
+    """skyrme_slab_finish: the decision over all slabs from ``records`` (a
+    float64 device tensor of shape (nslabs, 8), slab order) and the fix-up."""
+    if records.dtype != _torch().float64 or records.dim() != 2 or records.shape[1] != 8 or \
+            not records.is_contiguous():
+        raise ValueError("records must be a contiguous float64 tensor of shape (nslabs, 8)")
+    cl, cs = lat.c(), st.c()
+    _check(_on(st.device).skyrme_slab_finish(ctypes.byref(cl), float(dt), int(mode),
+                                             ctypes.byref(cs), ctypes.c_void_p(records.data_ptr()),
+                                             int(records.shape[0]), _stream_ptr(stream, st.device)),
+           "skyrme_slab_finish")
+
+
 def read_report(lat: Lattice, st: State, stream=None) -> dict:
     cl, cs = lat.c(), st.c()
     rep = c_report()
-    _check(load().skyrme_read_report(ctypes.byref(cl), ctypes.byref(cs), ctypes.byref(rep),
+    _check(_on(st.device).skyrme_read_report(ctypes.byref(cl), ctypes.byref(cs), ctypes.byref(rep),
                                      _stream_ptr(stream, st.device)), "skyrme_read_report")
     return _rep_dict(rep)
 
@@ -348,7 +418,7 @@ def read_report(lat: Lattice, st: State, stream=None) -> dict:
 def energy(lat: Lattice, st: State, stream=None) -> dict:
     cl, cs = lat.c(), st.c()
     out = (ctypes.c_double * 6)()
-    _check(load().skyrme_energy(ctypes.byref(cl), ctypes.byref(cs), out,
+    _check(_on(st.device).skyrme_energy(ctypes.byref(cl), ctypes.byref(cs), out,
                                 _stream_ptr(stream, st.device)), "skyrme_energy")
     return dict(zip(("E", "E2", "E4", "E0", "B", "virial"), list(out)))
 
@@ -356,7 +426,7 @@ def energy(lat: Lattice, st: State, stream=None) -> dict:
 def baryon_number(lat: Lattice, st: State, stream=None) -> float:
     cl, cs = lat.c(), st.c()
     out = ctypes.c_double()
-    _check(load().skyrme_baryon_number(ctypes.byref(cl), ctypes.byref(cs), ctypes.byref(out),
+    _check(_on(st.device).skyrme_baryon_number(ctypes.byref(cl), ctypes.byref(cs), ctypes.byref(out),
                                        _stream_ptr(stream, st.device)), "skyrme_baryon_number")
     return out.value
 
@@ -364,7 +434,7 @@ def baryon_number(lat: Lattice, st: State, stream=None) -> float:
 def virial(lat: Lattice, st: State, stream=None) -> float:
     cl, cs = lat.c(), st.c()
     out = ctypes.c_double()
-    _check(load().skyrme_virial(ctypes.byref(cl), ctypes.byref(cs), ctypes.byref(out),
+    _check(_on(st.device).skyrme_virial(ctypes.byref(cl), ctypes.byref(cs), ctypes.byref(out),
                                 _stream_ptr(stream, st.device)), "skyrme_virial")
     return out.value
 
@@ -377,7 +447,7 @@ def energy_static(lat: Lattice, phi, stream=None) -> dict:
         raise ValueError("phi must be a contiguous (Nx, Ny, Nz, 4) tensor of the lattice dtype")
     cl = lat.c()
     out = (ctypes.c_double * 6)()
-    _check(load().skyrme_energy_static(ctypes.byref(cl), ctypes.c_void_p(phi.data_ptr()), out,
+    _check(_on(phi.device).skyrme_energy_static(ctypes.byref(cl), ctypes.c_void_p(phi.data_ptr()), out,
                                        _stream_ptr(stream, phi.device)), "skyrme_energy_static")
     return dict(zip(("E", "E2", "E4", "E0", "B", "virial"), list(out)))
 
@@ -386,7 +456,7 @@ def sextic_energy(lat: Lattice, st: State, stream=None) -> float:
     """E6 = h^3 sum of c6 4 pi^4 (B0)^2 of the current field (skyrme_sextic_energy)."""
     cl, cs = lat.c(), st.c()
     out = ctypes.c_double()
-    _check(load().skyrme_sextic_energy(ctypes.byref(cl), ctypes.byref(cs), ctypes.byref(out),
+    _check(_on(st.device).skyrme_sextic_energy(ctypes.byref(cl), ctypes.byref(cs), ctypes.byref(out),
                                        _stream_ptr(stream, st.device)), "skyrme_sextic_energy")
     return out.value
 
@@ -397,7 +467,7 @@ def observables(lat: Lattice, st: State, stream=None) -> dict:
     (3x3 lists; W[i][j] with i isospin, j space), D-term D and energy E."""
     o = c_observables()
     cl, cs = lat.c(), st.c()
-    _check(load().skyrme_observables(ctypes.byref(cl), ctypes.byref(cs), ctypes.byref(o),
+    _check(_on(st.device).skyrme_observables(ctypes.byref(cl), ctypes.byref(cs), ctypes.byref(o),
                                      _stream_ptr(stream, st.device)), "skyrme_observables")
     mat = lambda a: [list(a[0:3]), list(a[3:6]), list(a[6:9])]
     return {"B": o.B, "X": list(o.X), "R": o.R, "Q": mat(o.Q), "U": mat(o.U), "V": mat(o.V),
@@ -411,7 +481,7 @@ def forces(lat: Lattice, st: State, want_dens: bool = True, stream=None):
     F = torch.empty(shape, dtype=lat.dtype, device=st.device)
     D = torch.empty(shape, dtype=lat.dtype, device=st.device) if want_dens else None
     cl, cs = lat.c(), st.c()
-    _check(load().skyrme_forces(ctypes.byref(cl), ctypes.byref(cs), ctypes.c_void_p(F.data_ptr()),
+    _check(_on(st.device).skyrme_forces(ctypes.byref(cl), ctypes.byref(cs), ctypes.c_void_p(F.data_ptr()),
                                 ctypes.c_void_p(D.data_ptr()) if D is not None else None,
                                 _stream_ptr(stream, st.device)), "skyrme_forces")
     return F, D
@@ -438,7 +508,7 @@ def render_volume(lat: Lattice, st: State, out=None, stream=None):
     shape = tuple(int(v) for v in lat.n) + (4,)
     vol = out if out is not None else torch.empty(shape, dtype=torch.float64, device=st.device)
     cl, cs = lat.c(), st.c()
-    _check(load().skyrme_render_volume(ctypes.byref(cl), ctypes.byref(cs),
+    _check(_on(st.device).skyrme_render_volume(ctypes.byref(cl), ctypes.byref(cs),
                                        ctypes.c_void_p(vol.data_ptr()),
                                        ctypes.c_size_t(vol.numel() * vol.element_size()),
                                        _stream_ptr(stream, st.device)), "skyrme_render_volume")
@@ -453,7 +523,7 @@ def render_rays(vol, params: c_render_params, stream=None):
         raise ValueError("vol must be a contiguous float64 tensor of shape (Nx, Ny, Nz, 4)")
     rgba = torch.empty((params.height, params.width, 4), dtype=torch.float32, device=vol.device)
     n = (ctypes.c_int * 3)(*[int(v) for v in vol.shape[:3]])
-    _check(load().skyrme_render_rays(n, ctypes.c_void_p(vol.data_ptr()), ctypes.byref(params),
+    _check(_on(vol.device).skyrme_render_rays(n, ctypes.c_void_p(vol.data_ptr()), ctypes.byref(params),
                                      ctypes.c_void_p(rgba.data_ptr()),
                                      _stream_ptr(stream, vol.device)), "skyrme_render_rays")
     return rgba
@@ -468,7 +538,7 @@ def render(lat: Lattice, st: State, params: c_render_params, work=None, stream=N
                            dtype=torch.uint8, device=st.device)
     rgba = torch.empty((params.height, params.width, 4), dtype=torch.float32, device=st.device)
     cl, cs = lat.c(), st.c()
-    _check(load().skyrme_render(ctypes.byref(cl), ctypes.byref(cs), ctypes.byref(params),
+    _check(_on(st.device).skyrme_render(ctypes.byref(cl), ctypes.byref(cs), ctypes.byref(params),
                                 ctypes.c_void_p(work.data_ptr()),
                                 ctypes.c_size_t(work.numel() * work.element_size()),
                                 ctypes.c_void_p(rgba.data_ptr()), _stream_ptr(stream, st.device)),
@@ -503,7 +573,7 @@ def selftest_wait(lat: Lattice, st: State, limit_seconds: float = 0.05, stream=N
     control block and return its status code (5, SKYRME_ETIMEOUT, when the
     wait gave up as it should)."""
     cl, cs = lat.c(), st.c()
-    return int(load().skyrme_selftest_wait(ctypes.byref(cl), ctypes.byref(cs),
+    return int(_on(st.device).skyrme_selftest_wait(ctypes.byref(cl), ctypes.byref(cs),
                                            float(limit_seconds), _stream_ptr(stream, st.device)))
 
 
@@ -524,26 +594,37 @@ class FlowGraph:
         h = ctypes.c_void_p()
         sp = ctypes.c_void_p(self.stream.cuda_stream)
         if batch is not None:
-            _check(load().skyrme_batch_graph_create(batch._h, self.nsteps, sp, ctypes.byref(h)),
+            _check(_on(dev).skyrme_batch_graph_create(batch._h, self.nsteps, sp, ctypes.byref(h)),
                    "skyrme_batch_graph_create")
         elif until is not None:
             tol, max_steps = until
             cl, cs = lat.c(), st.c()
-            _check(load().skyrme_graph_create_until(ctypes.byref(cl), float(dt), int(mode),
+            _check(_on(dev).skyrme_graph_create_until(ctypes.byref(cl), float(dt), int(mode),
                                                     float(tol), int(max_steps), self.nsteps,
                                                     ctypes.byref(cs), sp, ctypes.byref(h)),
                    "skyrme_graph_create_until")
         else:
             cl, cs = lat.c(), st.c()
-            _check(load().skyrme_graph_create(ctypes.byref(cl), float(dt), self.nsteps, int(mode),
+            _check(_on(dev).skyrme_graph_create(ctypes.byref(cl), float(dt), self.nsteps, int(mode),
                                               ctypes.byref(cs), sp, ctypes.byref(h)),
                    "skyrme_graph_create")
         self._h = h
 
     def launch(self, stream=None):
+        """Launch the graph on ``stream`` (default: the graph's own stream).
+        The launch is ordered after the work already queued on the caller's
+        current stream (the state may just have been seeded there), and the
+        current stream's later work after the launch, as if the graph ran on
+        the current stream."""
+        torch = _torch()
         s = stream if stream is not None else self.stream
+        cur = torch.cuda.current_stream(s.device)
+        if cur != s:
+            s.wait_stream(cur)
         _check(load().skyrme_graph_launch(self._h, ctypes.c_void_p(s.cuda_stream)),
                "skyrme_graph_launch")
+        if cur != s:
+            cur.wait_stream(s)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -590,26 +671,26 @@ class Batch:
         nbytes = int(load().skyrme_batch_scratch_bytes(n, self._cl))
         self.scratch = torch.zeros(nbytes, dtype=torch.uint8, device=self.states[0].device)
         h = ctypes.c_void_p()
-        _check(load().skyrme_batch_create(n, self._cl, self._cs, self._dt, int(mode),
+        _check(_on(self.states[0].device).skyrme_batch_create(n, self._cl, self._cs, self._dt, int(mode),
                                           ctypes.c_void_p(self.scratch.data_ptr()), nbytes,
                                           ctypes.byref(h)), "skyrme_batch_create")
         self._h = h
 
     def step(self, nsteps: int, stream=None):
-        _check(load().skyrme_batch_step(self._h, int(nsteps),
+        _check(_on(self.states[0].device).skyrme_batch_step(self._h, int(nsteps),
                                         _stream_ptr(stream, self.states[0].device)),
                "skyrme_batch_step")
 
     def autotune(self, trials: int = 3, stream=None):
         t, ms = ctypes.c_int(), ctypes.c_double()
-        _check(load().skyrme_batch_autotune(self._h, int(trials),
+        _check(_on(self.states[0].device).skyrme_batch_autotune(self._h, int(trials),
                                             _stream_ptr(stream, self.states[0].device),
                                             ctypes.byref(t), ctypes.byref(ms)),
                "skyrme_batch_autotune")
         return t.value, ms.value
 
     def set_tile(self, tile: int):
-        _check(load().skyrme_batch_set_tile(self._h, int(tile)), "skyrme_batch_set_tile")
+        _check(_on(self.states[0].device).skyrme_batch_set_tile(self._h, int(tile)), "skyrme_batch_set_tile")
 
     def tile(self):
         t, ty, tz, g = (ctypes.c_int() for _ in range(4))

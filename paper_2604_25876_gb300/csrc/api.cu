@@ -42,7 +42,8 @@ static skyrme_status cuda_fail(cudaError_t e, const char *what)
         if (_e != cudaSuccess) return cuda_fail(_e, what); \
     } while (0)
 
-static bool lattice_ok(const skyrme_lattice *lat)
+namespace skyrme {
+bool lattice_ok(const skyrme_lattice *lat)
 {
     if (!lat) return false;
     for (int i = 0; i < 3; ++i)
@@ -55,6 +56,37 @@ static bool lattice_ok(const skyrme_lattice *lat)
     const double sites = (double)lat->n[0] * lat->n[1] * lat->n[2];
     return sites < 4.0e9;
 }
+
+// Device buffers must live on the current device: the kernels are launched
+// there, and a buffer of another GPU would be read across devices (a fault
+// when peer access is off).  Host memory the device cannot address is
+// rejected too.  Managed and mapped host memory pass.
+skyrme_status on_current_device(const void *const *ptrs, int n)
+{
+    int dev = -1;
+    CK(cudaGetDevice(&dev), "current device");
+    for (int i = 0; i < n; ++i) {
+        if (!ptrs[i]) continue;
+        cudaPointerAttributes at;
+        CK(cudaPointerGetAttributes(&at, ptrs[i]), "pointer attributes");
+        if (at.type == cudaMemoryTypeUnregistered) return SKYRME_EINVAL;
+        if (at.type == cudaMemoryTypeDevice && at.device != dev) return SKYRME_EINVAL;
+    }
+    return SKYRME_OK;
+}
+}  // namespace skyrme
+
+static skyrme_status state_on_device(const skyrme_state *st)
+{
+    const void *p[5] = {st->phi[0], st->phi[1], st->vel[0], st->vel[1], st->scratch};
+    return on_current_device(p, 5);
+}
+
+#define CKDEV(expr)                          \
+    do {                                     \
+        skyrme_status _r = (expr);           \
+        if (_r != SKYRME_OK) return _r;      \
+    } while (0)
 
 static size_t site_bytes(const skyrme_lattice &lat) { return lat.precision == 64 ? 32 : 16; }
 
@@ -227,6 +259,7 @@ skyrme_status skyrme_init_field(const skyrme_lattice *lat, const skyrme_seed *se
         break;
     default: return SKYRME_EINVAL;
     }
+    CKDEV(state_on_device(st));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     FlowArgs a = make_args(*lat, *st, 0.0, MODE_ARRESTED);
     CK(launch_reset_ctrl(a.ctrl, s), "reset control block");
@@ -239,6 +272,7 @@ skyrme_status skyrme_load_field(const skyrme_lattice *lat, skyrme_state *st, voi
 {
     skyrme_status rc = check_state(lat, st);
     if (rc != SKYRME_OK) return rc;
+    CKDEV(state_on_device(st));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     FlowArgs a = make_args(*lat, *st, 0.0, MODE_ARRESTED);
     CK(launch_reset_ctrl(a.ctrl, s), "reset control block");
@@ -246,22 +280,29 @@ skyrme_status skyrme_load_field(const skyrme_lattice *lat, skyrme_state *st, voi
     return SKYRME_OK;
 }
 
+// FP32 flows without the sextic term run on the streaming kernel
+static bool fp32_streaming(const skyrme_lattice &lat)
+{
+    return lat.precision == 32 && lat.c6 == 0.0 && f32_fast_path_available(lat);
+}
+
 static skyrme_status launch_iterations(const skyrme_lattice &lat, const FlowArgs &a, int nsteps,
                                        cudaStream_t s)
 {
     // the streaming FP32 kernel implements the standard model and the
     // Section 7.8 potentials; the sextic term runs on the tile kernels
-    const bool fast = lat.precision == 32 && lat.c6 == 0.0 && f32_fast_path_available(lat);
-    if (fast) {
+    if (fp32_streaming(lat)) {
         CK(launch_iterations_f32_fast(lat, a, nsteps, s), "step and fix-up kernels (fp32)");
         return SKYRME_OK;
     }
     for (int k = 0; k < nsteps; ++k) {
         CK(launch_step(lat, a, s), "step kernel");
-        if (a.mode == SKYRME_ARRESTED) CK(launch_fixup(lat, a, s), "fix-up kernel");
+        // an x-slab's fix-up follows the decision over all slabs
+        if (a.mode == SKYRME_ARRESTED && !a.slab_rec) CK(launch_fixup(lat, a, s), "fix-up kernel");
     }
     return SKYRME_OK;
 }
+
 
 // skyrme_flow_step's iterations.  A stream launch costs the GPU about 2.5 us
 // and a kernel node of a graph about 0.8 us, and every iteration is two
@@ -319,6 +360,7 @@ skyrme_status skyrme_flow_step(const skyrme_lattice *lat, double dt, int nsteps,
     if (rc != SKYRME_OK) return rc;
     if (!(dt > 0.0) || !isfinite(dt) || nsteps < 0) return SKYRME_EINVAL;
     if (!mode_ok(mode)) return SKYRME_EINVAL;
+    CKDEV(state_on_device(st));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     FlowArgs a = make_args(*lat, *st, dt, mode);
     rc = run_iterations(*lat, a, nsteps, s);
@@ -333,6 +375,76 @@ skyrme_status skyrme_flow_step(const skyrme_lattice *lat, double dt, int nsteps,
     return SKYRME_OK;
 }
 
+skyrme_status skyrme_step_densities(const skyrme_lattice *lat, double dt, int mode,
+                                    skyrme_state *st, void *dens, skyrme_report *report,
+                                    void *stream)
+{
+    skyrme_status rc = check_state(lat, st);
+    if (rc != SKYRME_OK) return rc;
+    if (!(dt > 0.0) || !isfinite(dt) || !mode_ok(mode)) return SKYRME_EINVAL;
+    if (!dens || ((uintptr_t)dens % 16)) return SKYRME_EINVAL;
+    if (!fp32_streaming(*lat)) return SKYRME_EUNSUPPORTED;
+    CKDEV(state_on_device(st));
+    {
+        const void *p = dens;
+        CKDEV(on_current_device(&p, 1));
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    FlowArgs a = make_args(*lat, *st, dt, mode);
+    a.dump = dens;
+    rc = launch_iterations(*lat, a, 1, s);
+    if (rc != SKYRME_OK) return rc;
+    if (report) {
+        Ctrl c;
+        rc = copy_ctrl(*st, &c, s);
+        if (rc != SKYRME_OK) return rc;
+        fill_report(c, report);
+        if (c.status) return static_cast<skyrme_status>(c.status);
+    }
+    return SKYRME_OK;
+}
+
+skyrme_status skyrme_slab_step(const skyrme_lattice *slab, double dt, int mode, skyrme_state *st,
+                               double *record, void *stream)
+{
+    skyrme_status rc = check_state(slab, st);
+    if (rc != SKYRME_OK) return rc;
+    if (!(dt > 0.0) || !isfinite(dt) || !mode_ok(mode)) return SKYRME_EINVAL;
+    if (!record || ((uintptr_t)record % 8)) return SKYRME_EINVAL;
+    CKDEV(state_on_device(st));
+    {
+        const void *p = record;
+        CKDEV(on_current_device(&p, 1));
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    FlowArgs a = make_args(*slab, *st, dt, mode);
+    a.slab_rec = record;
+    return launch_iterations(*slab, a, 1, s);
+}
+
+skyrme_status skyrme_slab_finish(const skyrme_lattice *slab, double dt, int mode, skyrme_state *st,
+                                 const double *records, int nslabs, void *stream)
+{
+    skyrme_status rc = check_state(slab, st);
+    if (rc != SKYRME_OK) return rc;
+    if (!(dt > 0.0) || !isfinite(dt) || !mode_ok(mode)) return SKYRME_EINVAL;
+    if (!records || ((uintptr_t)records % 8) || nslabs < 1 || nslabs > 4096) return SKYRME_EINVAL;
+    CKDEV(state_on_device(st));
+    {
+        const void *p = records;
+        CKDEV(on_current_device(&p, 1));
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    FlowArgs a = make_args(*slab, *st, dt, mode);
+    CK(launch_slab_decide(a.ctrl, records, nslabs, slab->h * slab->h * slab->h, mode, s),
+       "slab decision kernel");
+    if (mode == SKYRME_ARRESTED) {
+        if (fp32_streaming(*slab)) CK(launch_fixup_f32_fast(*slab, a, s), "fix-up kernel (fp32)");
+        else CK(launch_fixup(*slab, a, s), "fix-up kernel");
+    }
+    return SKYRME_OK;
+}
+
 skyrme_status skyrme_graph_create(const skyrme_lattice *lat, double dt, int nsteps, int mode,
                                   skyrme_state *st, void *stream, skyrme_graph **out)
 {
@@ -341,6 +453,7 @@ skyrme_status skyrme_graph_create(const skyrme_lattice *lat, double dt, int nste
     skyrme_status rc = check_state(lat, st);
     if (rc != SKYRME_OK) return rc;
     if (!(dt > 0.0) || !isfinite(dt) || nsteps < 1 || !mode_ok(mode)) return SKYRME_EINVAL;
+    CKDEV(state_on_device(st));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     FlowArgs a = make_args(*lat, *st, dt, mode);
     skyrme_graph *g = new skyrme_graph();
@@ -380,6 +493,7 @@ skyrme_status skyrme_graph_create_until(const skyrme_lattice *lat, double dt, in
     if (!(dt > 0.0) || !isfinite(dt) || !mode_ok(mode) || !(tol >= 0.0) || !isfinite(tol) ||
         max_steps < 1 || chunk < 1)
         return SKYRME_EINVAL;
+    CKDEV(state_on_device(st));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     FlowArgs a = make_args(*lat, *st, dt, mode);
     cudaStream_t body = nullptr;
@@ -463,6 +577,7 @@ skyrme_status skyrme_selftest_wait(const skyrme_lattice *lat, skyrme_state *st,
     skyrme_status rc = check_state(lat, st);
     if (rc != SKYRME_OK) return rc;
     if (!(limit_seconds > 0.0) || !(limit_seconds <= 10.0)) return SKYRME_EINVAL;
+    CKDEV(state_on_device(st));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     CK(launch_wait_selftest(st->scratch, (unsigned long long)(limit_seconds * 1e9), s),
        "wait self-test kernel");
@@ -478,6 +593,7 @@ skyrme_status skyrme_read_report(const skyrme_lattice *lat, const skyrme_state *
     skyrme_status rc = check_state(lat, st);
     if (rc != SKYRME_OK) return rc;
     if (!report) return SKYRME_EINVAL;
+    CKDEV(state_on_device(st));
     Ctrl c;
     rc = copy_ctrl(*st, &c, static_cast<cudaStream_t>(stream));
     if (rc != SKYRME_OK) return rc;
@@ -491,6 +607,7 @@ skyrme_status skyrme_energy(const skyrme_lattice *lat, skyrme_state *st, double 
     skyrme_status rc = check_state(lat, st);
     if (rc != SKYRME_OK) return rc;
     if (!out6) return SKYRME_EINVAL;
+    CKDEV(state_on_device(st));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     FlowArgs a = make_args(*lat, *st, 0.0, MODE_ARRESTED);
     CK(launch_energy(*lat, a, s), "energy kernel");
@@ -527,6 +644,7 @@ skyrme_status skyrme_sextic_energy(const skyrme_lattice *lat, skyrme_state *st, 
     if (!E6) return SKYRME_EINVAL;
     skyrme_status rc = check_state(lat, st);
     if (rc != SKYRME_OK) return rc;
+    CKDEV(state_on_device(st));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     FlowArgs a = make_args(*lat, *st, 0.0, MODE_ARRESTED);
     CK(launch_energy(*lat, a, s), "energy kernel");
@@ -547,6 +665,7 @@ skyrme_status skyrme_observables(const skyrme_lattice *lat, skyrme_state *st,
     if (lattice_extended(*lat)) return SKYRME_EUNSUPPORTED;
     const ScratchLayout L = scratch_layout(*lat);
     if (L.total - L.energy_off < observables_parts_bytes()) return SKYRME_ENOMEM;
+    CKDEV(state_on_device(st));
     FlowArgs a = make_args(*lat, *st, 0.0, MODE_ARRESTED);
     return compute_observables(*lat, a, out, static_cast<cudaStream_t>(stream));
 }
@@ -558,6 +677,11 @@ skyrme_status skyrme_forces(const skyrme_lattice *lat, skyrme_state *st, void *f
     if (rc != SKYRME_OK) return rc;
     const size_t align = site_bytes(*lat);
     if (((uintptr_t)force % align) || ((uintptr_t)dens % align)) return SKYRME_EINVAL;
+    CKDEV(state_on_device(st));
+    {
+        const void *p[2] = {force, dens};
+        CKDEV(on_current_device(p, 2));
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     FlowArgs a = make_args(*lat, *st, 0.0, MODE_ARRESTED);
     const size_t bytes = (size_t)lat->n[0] * lat->n[1] * lat->n[2] * site_bytes(*lat);
@@ -580,6 +704,8 @@ skyrme_status skyrme_render_volume(const skyrme_lattice *lat, skyrme_state *st, 
     if (rc != SKYRME_OK) return rc;
     if (!vol || ((uintptr_t)vol % 32)) return SKYRME_EINVAL;
     if (vol_bytes < skyrme_render_volume_bytes(lat)) return SKYRME_ENOMEM;
+    CKDEV(state_on_device(st));
+    CKDEV(on_current_device(&vol, 1));
     const ScratchLayout L = scratch_layout(*lat);
     FlowArgs a = make_args(*lat, *st, 0.0, MODE_ARRESTED);
     void *bmax = static_cast<char *>(st->scratch) + L.energy_off;
@@ -595,6 +721,10 @@ skyrme_status skyrme_render_rays(const int n[3], const void *vol,
     for (int i = 0; i < 3; ++i)
         if (n[i] < 2 || n[i] > (1 << 20)) return SKYRME_EINVAL;
     if (!render_params_valid(*params)) return SKYRME_EINVAL;
+    {
+        const void *p[2] = {vol, rgba};
+        CKDEV(on_current_device(p, 2));
+    }
     CK(launch_render_rays(n, vol, *params, rgba, static_cast<cudaStream_t>(stream)), "render rays");
     return SKYRME_OK;
 }

@@ -16,8 +16,6 @@
 #include <math.h>
 #include <stddef.h>
 
-#include <mutex>
-
 #include "skyrme_device.cuh"
 #include "skyrme_internal.h"
 
@@ -125,25 +123,16 @@ __global__ void __launch_bounds__(256) k_energy_static(const vec4_t<T> *__restri
     hdr->counter = 0;
 }
 
-// Device address of the static scratch, looked up once per device with that
-// device current.
-static void *static_scratch_address(int dev, cudaError_t *err)
+// Device address of the static scratch in the current context.  Module
+// symbols belong to a context, and a context can be replaced under the same
+// device ordinal (cudaDeviceReset, or a host application that binds its own
+// context), so the address is looked up on every call rather than cached:
+// the lookup is host-side and allocates nothing.
+static void *static_scratch_address(cudaError_t *err)
 {
-    static std::mutex mu;
-    static void *addr[256] = {nullptr};
-    std::lock_guard<std::mutex> lock(mu);
-    if (dev < 0 || dev >= 256) {
-        *err = cudaErrorInvalidDevice;
-        return nullptr;
-    }
-    if (!addr[dev]) {
-        void *p = nullptr;
-        *err = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (*err != cudaSuccess) return nullptr;
-        addr[dev] = p;
-    }
-    *err = cudaSuccess;
-    return addr[dev];
+    void *p = nullptr;
+    *err = cudaGetSymbolAddress(&p, g_static_scratch);
+    return *err == cudaSuccess ? p : nullptr;
 }
 
 }  // namespace skyrme
@@ -153,21 +142,17 @@ using namespace skyrme;
 extern "C" skyrme_status skyrme_energy_static(const skyrme_lattice *lat, const void *phi,
                                               double out6[6], void *stream)
 {
-    if (!lat || !phi || !out6) return SKYRME_EINVAL;
-    for (int i = 0; i < 3; ++i)
-        if (lat->n[i] < 5 || lat->n[i] > 4096) return SKYRME_EINVAL;
-    if (!(lat->h > 0.0) || (lat->precision != 32 && lat->precision != 64)) return SKYRME_EINVAL;
-    const double coef[5] = {lat->m, lat->m_y, lat->m_z, lat->m_w, lat->c6};
-    for (double v : coef)
-        if (!isfinite(v) || v < 0.0) return SKYRME_EINVAL;
+    if (!lattice_ok(lat) || !phi || !out6) return SKYRME_EINVAL;
     // one partial record per interior x-plane must fit the static scratch
     if (lat->n[0] - 4 > kStaticMaxPlanes) return SKYRME_EINVAL;
     const size_t align = lat->precision == 64 ? 32 : 16;
     if ((uintptr_t)phi % align) return SKYRME_EINVAL;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return SKYRME_ECUDA;
-    void *scratch = static_scratch_address(dev, &e);
+    // the field must be on the current device, where the scratch is looked up
+    // and the kernel runs
+    skyrme_status rc = on_current_device(&phi, 1);
+    if (rc != SKYRME_OK) return rc;
+    cudaError_t e;
+    void *scratch = static_scratch_address(&e);
     if (!scratch) return SKYRME_ECUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // the arrival counter and the results must start from zero on every call

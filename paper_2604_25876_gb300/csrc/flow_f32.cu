@@ -33,10 +33,12 @@
 //  * 4-vector arithmetic uses the packed FP32 pair instructions of sm_100+
 //    (__ffma2_rn / __fadd2_rn / __fmul2_rn): two components per instruction;
 //    stencil weights are stored as (w, w) pairs.
-//  * per-site densities are summed in FP32 over at most 40 consecutive
-//    planes, then in double-float (hi, lo) pairs kept in shared memory; block
-//    and per-lattice reductions are double-float in a fixed order, and the
-//    arrest comparison is made in FP64 on the rounded totals.
+//  * per-site energy and charge densities enter compensated FP32 sums
+//    (Knuth's error-free two-sum at every addition, the rounding errors summed
+//    exactly beside them), folded every 40 planes into double-float (hi, lo)
+//    pairs kept in shared memory; block and per-lattice reductions are
+//    double-float in a fixed order, and the arrest comparison is made in FP64
+//    on the rounded totals.
 //  * the tile shape (TY, TZ) is a template parameter; the batch autotuner
 //    times the candidates on the actual lattices and keeps the fastest.
 #include <cuda.h>
@@ -84,6 +86,8 @@ struct InstDesc {
     float e0_scale;        // E0 = h^3 e0_scale sum(e0 slot): 2 m^2 (standard) or 1 (POT)
     float h3_hi, h3_lo;    // h^3 as an unevaluated float sum
     int mode;
+    double *slab_rec;      // x-slab of a larger lattice: record out, no decision (else null)
+    float4 *dump;          // DUMP kernels: per-site densities the step sums
 };
 
 // Unit ranges of the CTAs of a single-lattice launch: CTA b streams units
@@ -246,21 +250,43 @@ __device__ __forceinline__ DF df_shfl_xor(DF a, int o)
 // the five sums of a step: e2, e4, (1 - phi^0), det, |F|^2; plus max |F|^2
 constexpr int kSums = 5;
 
+// A thread's running sums between two flushes.  The energy and charge
+// densities are added with Knuth's error-free two-sum, two quantities per
+// packed instruction: s holds the FP32 sums of (e2, e4) and (e0, det), c the
+// exact sums of the rounding errors of every addition into s (each error is
+// itself exact, so s + c is the exact sum up to the rounding of the few
+// additions into c).  The per-site sums therefore carry no FP32 reduction
+// error into the energy of the arrest test or the baryon number.  |F|^2 is a
+// plain FP32 sum (it feeds only the reported residual).
 struct Acc {
-    float e2, e4, e0, b, f2, fmax2;
+    float2 s24, c24;  // (e2, e4) and their compensation
+    float2 s0b, c0b;  // (e0, det) and their compensation
+    float f2, fmax2;
 };
 
-// Fold a thread's FP32 partial sums into its double-float sums, which live
-// in shared memory (acc: kSums arrays of stride nthreads, at this thread's slot).
+// s + x with the rounding error of the addition added to c (two quantities)
+__device__ __forceinline__ void two_sum_acc(float2 &s, float2 &c, float2 x)
+{
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const float2 t = __fadd2_rn(s, x);
+    const float2 bb = __ffma2_rn(s, m1, t);                      // t - s
+    const float2 ea = __ffma2_rn(__ffma2_rn(bb, m1, t), m1, s);  // s - (t - bb)
+    const float2 eb = __ffma2_rn(bb, m1, x);                     // x - bb
+    c = __fadd2_rn(c, __fadd2_rn(ea, eb));
+    s = t;
+}
+
+// Fold a thread's running sums into its double-float sums, which live in
+// shared memory (acc: kSums arrays of stride nthreads, at this thread's slot).
 __device__ __forceinline__ void flush(DF *acc, float *amax, int nthreads, Acc &a)
 {
-    acc[0] = df_add(acc[0], a.e2);
-    acc[nthreads] = df_add(acc[nthreads], a.e4);
-    acc[2 * nthreads] = df_add(acc[2 * nthreads], a.e0);
-    acc[3 * nthreads] = df_add(acc[3 * nthreads], a.b);
+    acc[0] = df_add(df_add(acc[0], a.s24.x), a.c24.x);
+    acc[nthreads] = df_add(df_add(acc[nthreads], a.s24.y), a.c24.y);
+    acc[2 * nthreads] = df_add(df_add(acc[2 * nthreads], a.s0b.x), a.c0b.x);
+    acc[3 * nthreads] = df_add(df_add(acc[3 * nthreads], a.s0b.y), a.c0b.y);
     acc[4 * nthreads] = df_add(acc[4 * nthreads], a.f2);
     *amax = fmaxf(*amax, a.fmax2);
-    a = {0, 0, 0, 0, 0, 0};
+    a = Acc{};
 }
 
 __device__ __forceinline__ void zero_sums(DF *acc, float *amax, int nthreads)
@@ -440,7 +466,7 @@ __device__ __forceinline__ void plane_record(const float4 (*DY)[TZ + 4], const I
 // Euler-Lagrange force of Eq. (3.3) projected on the tangent space, the
 // symplectic update with renormalisation, and the energy, charge and force
 // densities into a32 (valid sites only).
-template <int TY, int TZ, bool POT = false>
+template <int TY, int TZ, bool POT = false, bool DUMP = false>
 __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &M2,
                                             const PlaneVals &M1, const PlaneVals &C,
                                             const PlaneVals &Q1, const PlaneVals &Q2, float2 xc1,
@@ -518,16 +544,17 @@ __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &
     if (valid) {
         __stcs(phiout + si, st4(pn));
         if (mode != MODE_GRADIENT) __stcs(vout + si, st4(vnew));
-        a32.e2 += tra;
-        a32.e4 += e4;
+        float e0v;
         if constexpr (POT) {
             // the whole potential: 2 m^2 u + m_y^2 u (2 - u) + m_z^2 u^2 + m_w^2 u^4 / 2
             const float u2 = u * u;
-            a32.e0 += fmaf(2.f * D.m2, u, fmaf(D.my2, u * (2.f - u), u2 * fmaf(0.5f * D.mw2, u2, D.mz2)));
+            e0v = fmaf(2.f * D.m2, u, fmaf(D.my2, u * (2.f - u), u2 * fmaf(0.5f * D.mw2, u2, D.mz2)));
         } else {
-            a32.e0 += one_minus_phi0();
+            e0v = one_minus_phi0();
         }
-        a32.b += det;
+        if constexpr (DUMP) __stcs(D.dump + si, make_float4(tra, e4, e0v, det));
+        two_sum_acc(a32.s24, a32.c24, make_float2(tra, e4));
+        two_sum_acc(a32.s0b, a32.c0b, make_float2(e0v, det));
         a32.f2 += f2;
         a32.fmax2 = fmaxf(a32.fmax2, f2);
     }
@@ -602,6 +629,21 @@ __device__ __forceinline__ void finish_lattice(const InstDesc &D, Ctrl *c, int c
     }
     constexpr double kB = -0.050660591821168885;  // b = -det / (2 pi^2)
     const DF bfac = {(float)kB, (float)(kB - (double)(float)kB)};
+    if (D.slab_rec) {
+        // one x-slab of a larger lattice: leave this slab's record for the
+        // decision over all slabs, {e2, e4, e0, b, |F|^2, max |F|^2, sites, e6}
+        double *r = D.slab_rec;
+        r[0] = df_value(t[0]);
+        r[1] = df_value(t[1]);
+        r[2] = df_value(df_mul(DF{D.e0_scale, 0.f}, t[2]));
+        r[3] = df_value(df_mul(bfac, t[3]));
+        r[4] = df_value(t[4]);
+        r[5] = (double)tmax;
+        r[6] = (double)(D.n0 - 4) * (double)(D.n1 - 4) * (double)(D.n2 - 4);
+        r[7] = 0.0;
+        c->done = 0;
+        return;
+    }
     const DF h3 = {D.h3_hi, D.h3_lo};
     const DF E2 = df_mul(h3, t[0]), E4 = df_mul(h3, t[1]);
     const DF E0 = df_mul(h3, df_mul(DF{D.e0_scale, 0.f}, t[2]));  // 2 m^2 sum(1 - phi^0), or the potentials' sum
@@ -627,15 +669,15 @@ __device__ __forceinline__ void finish_lattice(const InstDesc &D, Ctrl *c, int c
     c->E_prev = Ed;
     c->steps = steps + 1;
     c->cur = cur ^ 1;
-    const float nsites = (float)(D.n0 - 4) * (float)(D.n1 - 4) * (float)(D.n2 - 4);
+    const double nsites = (double)(D.n0 - 4) * (double)(D.n1 - 4) * (double)(D.n2 - 4);
     c->last[0] = Ed;
     c->last[1] = df_value(E2);
     c->last[2] = df_value(E4);
     c->last[3] = df_value(E0);
     c->last[4] = df_value(B);
     c->last[5] = df_value(V);
-    c->last[6] = (double)sqrtf(tmax);
-    c->last[7] = (double)sqrtf(t[4].hi / nsites);
+    c->last[6] = sqrt((double)tmax);
+    c->last[7] = sqrt(df_value(t[4]) / (double)nsites);
     if (!(isfinite(Ed) && isfinite(B.hi) && isfinite(t[4].hi))) c->status = DEV_NONFINITE;
     c->done = 0;
 }
@@ -644,7 +686,7 @@ __device__ __forceinline__ void finish_lattice(const InstDesc &D, Ctrl *c, int c
 // lattices come from `table` (ninst entries, ordered by unit_start); otherwise
 // from `one`.  dry != 0 (autotuning): outputs land in the inactive buffers and
 // the control blocks are left as they were.
-template <int TY, int TZ, bool BATCHED, bool POT = false>
+template <int TY, int TZ, bool BATCHED, bool POT = false, bool DUMP = false>
 __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
     k_step_f32(const __grid_constant__ InstDesc one, const __grid_constant__ CtaSplit split,
                const InstDesc *__restrict__ table, int ninst, long long total_units, int dry)
@@ -698,7 +740,7 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
         DF *acc = &sm.accs[0][tid];
         float *amax = &sm.amaxs[tid];
         zero_sums(acc, amax, THREADS);
-        Acc a32 = {0, 0, 0, 0, 0, 0};
+        Acc a32 = {};
 
         while (us < seg_hi && !failed) {
             const long long local = us - D.unit_start;
@@ -719,8 +761,13 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
                 tma_plane(&sm.plane[slot][0][0], map, &sm.bar[slot], 4 * (z0 - 2), y0 - 2, q);
                 if (wv) tma_plane(&sm.vpl[slot][0][0], vmap, &sm.bar[slot], 4 * z0, y0, q - 2);
             };
-            if (tid == 0)
+            if (tid == 0) {
+                // the slots were last read through the generic proxy (the run
+                // before this one, ordered by the closing barrier): order those
+                // reads before the copies' async-proxy writes
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 for (int q = 0; q < NSLOT && pf + q <= pl; ++q) issue(pf + q, (g + q) % NSLOT);
+            }
             PlaneVals ring[5];
             int nouter = 0;
             for (int base = pf; base <= pl && !failed; base += 5) {
@@ -738,7 +785,7 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
                     const uint32_t g3n = g3 == 2 ? 0 : g3 + 1;  // (g + 1) % 3 == (g - 2) % 3
                     const int x = pp - 2;
                     if (x >= xs)
-                        centre_site<TY, TZ, POT>(D, ring[(k + 1) % 5], ring[(k + 2) % 5], ring[(k + 3) % 5],
+                        centre_site<TY, TZ, POT, DUMP>(D, ring[(k + 1) % 5], ring[(k + 2) % 5], ring[(k + 3) % 5],
                                             ring[(k + 4) % 5], ring[k], D.c1, D.c2,
                                             &sm.inpl[g3n][0][tid], &sm.inyz[g3n][tid],
                                             &sm.vpl[s][ty][tz], use_v,
@@ -965,9 +1012,9 @@ constexpr int kNumTiles = 5;
 // faster than two 8 x 32 CTAs per SM on 128^3, 256^3 and 512^3)
 constexpr int kSingleTile = 4;
 
-template <int TY, int TZ, bool B> static void *kernel_ptr()
+template <int TY, int TZ, bool B, bool POT = false, bool DUMP = false> static void *kernel_ptr()
 {
-    return reinterpret_cast<void *>(&k_step_f32<TY, TZ, B>);
+    return reinterpret_cast<void *>(&k_step_f32<TY, TZ, B, POT, DUMP>);
 }
 
 template <int TY, int TZ, bool B>
@@ -1257,38 +1304,71 @@ cudaError_t launch_iterations_f32_fast(const skyrme_lattice &lat, const FlowArgs
     const long long rows = (long long)(lat.n[0] - 4) * (lat.n[1] - 4);
     const int fix_blocks = (int)std::max(1LL, std::min((long long)sm_count() * 2, (rows + 15) / 16));
 
+    ds[0].slab_rec = a.slab_rec;
+    ds[0].dump = static_cast<float4 *>(a.dump);
     const bool pot = lattice_potentials(lat);
-    if (pot) {
-        // the potentials variant of the single-lattice kernel
+    const bool dump = a.dump != nullptr;
+    // the single-lattice instantiations besides the tile table: the
+    // potentials variant and the density-dump variants
+    void *kern = nullptr;
+    if (pot) kern = dump ? kernel_ptr<16, 32, false, true, true>() : kernel_ptr<16, 32, false, true>();
+    else if (dump) kern = kernel_ptr<16, 32, false, false, true>();
+    if (kern) {
         static std::mutex mu;
-        static bool done[64] = {false};
+        static bool done[3][64] = {{false}};
+        const int which = pot ? (dump ? 2 : 1) : 0;
         int dev = 0;
         cudaGetDevice(&dev);
         std::lock_guard<std::mutex> lock(mu);
-        if (dev < 64 && !done[dev]) {
-            cudaError_t e = cudaFuncSetAttribute(k_step_f32<16, 32, false, true>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (dev < 64 && !done[which][dev]) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)sizeof(StepSmem<16, 32>));
             if (e != cudaSuccess) return e;
-            done[dev] = true;
+            done[which][dev] = true;
         }
     }
     for (int k = 0; k < nsteps; ++k) {
         cudaError_t e;
-        if (pot) {
-            k_step_f32<16, 32, false, true><<<(unsigned)grid, 16 * 32, sizeof(StepSmem<16, 32>), s>>>(
-                ds[0], split, nullptr, 1, ds[0].units, 0);
-            e = cudaGetLastError();
+        if (kern) {
+            void *args[] = {(void *)&ds[0], (void *)&split, nullptr, nullptr, nullptr, nullptr};
+            const InstDesc *tab = nullptr;
+            int ninst = 1, dry = 0;
+            long long units = ds[0].units;
+            args[2] = &tab;
+            args[3] = &ninst;
+            args[4] = &units;
+            args[5] = &dry;
+            e = cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(16 * 32), args,
+                                 sizeof(StepSmem<16, 32>), s);
         } else {
             e = launch_tile<false>(tile, ds[0], split, nullptr, 1, ds[0].units, grid, 0, s);
         }
         if (e != cudaSuccess) return e;
-        if (a.mode == SKYRME_ARRESTED) {
+        // an x-slab's fix-up follows the decision over all slabs
+        if (a.mode == SKYRME_ARRESTED && !a.slab_rec) {
             k_fixup_one<<<fix_blocks, 512, 0, s>>>(fx);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_fixup_f32_fast(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s)
+{
+    FixDesc fx;
+    for (int i = 0; i < 2; ++i) {
+        fx.phi[i] = static_cast<float4 *>(a.phi[i]);
+        fx.vel[i] = static_cast<float4 *>(a.vel[i]);
+    }
+    fx.ctrl = static_cast<Ctrl *>(a.ctrl);
+    fx.n0 = lat.n[0];
+    fx.n1 = lat.n[1];
+    fx.n2 = lat.n[2];
+    fx.dt = (float)a.dt;
+    const long long rows = (long long)(lat.n[0] - 4) * (lat.n[1] - 4);
+    const int fix_blocks = (int)std::max(1LL, std::min((long long)sm_count() * 2, (rows + 15) / 16));
+    k_fixup_one<<<fix_blocks, 512, 0, s>>>(fx);
+    return cudaGetLastError();
 }
 
 }  // namespace skyrme
@@ -1387,6 +1467,17 @@ skyrme_status skyrme_batch_create(int ninst, const skyrme_lattice *lats, skyrme_
     for (int i = 0; i < ninst; ++i)
         if (lattice_extended(lats[i])) return SKYRME_EUNSUPPORTED;
     if (!f32_fast_path_available(lats[0])) return SKYRME_EUNSUPPORTED;
+    {
+        const void *p = scratch;
+        skyrme_status rc = on_current_device(&p, 1);
+        if (rc != SKYRME_OK) return rc;
+    }
+    for (int i = 0; i < ninst; ++i) {
+        const void *p[5] = {states[i].phi[0], states[i].phi[1], states[i].vel[0], states[i].vel[1],
+                            states[i].scratch};
+        skyrme_status rc = on_current_device(p, 5);
+        if (rc != SKYRME_OK) return rc;
+    }
     skyrme_batch *b = new skyrme_batch();
     b->ninst = ninst;
     b->mode = mode;

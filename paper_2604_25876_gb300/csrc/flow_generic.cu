@@ -40,6 +40,7 @@ template <typename T> struct FlowParams {
     T v1, v2, v0;  // second-derivative weights / h^2
     double h3;
     int mode;
+    double *slab_rec;  // x-slab: the step's record goes here, the decision is made later
 };
 
 template <typename T> __device__ __forceinline__ T comp(const vec4_t<T> &v, int A)
@@ -245,6 +246,12 @@ __device__ __forceinline__ void reduce_and_finish(const FlowParams<T> &p, double
             c->energy[7] = sqrt(tot[4] / nsites);
             if (!(isfinite(c->energy[0]) && isfinite(c->energy[4]))) c->status = DEV_NONFINITE;
             c->edone = 0;
+        } else if (p.slab_rec) {
+            // one x-slab of a larger lattice: the arrest decision needs every
+            // slab's sums, so this step only leaves its record
+#pragma unroll
+            for (int q = 0; q < kPartialDoubles; ++q) p.slab_rec[q] = tot[q];
+            p.ctrl->done = 0;
         } else {
             finish_step(p.ctrl, tot, p.h3, p.mode, pred);
         }
@@ -283,16 +290,32 @@ __global__ void __launch_bounds__(GTHREADS, kTileMinBlocks<T, EXT>) k_tile(FlowP
     // add in FP32 over at most kFoldTiles tiles and then fold into FP64, so
     // that the FP64 pipe (1/64 of the FP32 rate) does a few operations per
     // thread instead of seven per site; FP64 kernels add in FP64 directly.
+    // In FP32 the energy, charge and sextic sums are compensated: each
+    // addition's rounding error (Knuth's two-sum, exact) is added to comp[],
+    // so part + comp carries no FP32 reduction error into the FP64 totals.
     constexpr int kFoldTiles = sizeof(T) == 4 ? 32 : 1;
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
     T part[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+    T comp[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
     int pending = 0;
+    auto add = [&](int q, T x) {
+        if constexpr (sizeof(T) == 4) {
+            const T t = __fadd_rn(part[q], x);
+            const T bb = __fsub_rn(t, part[q]);
+            comp[q] = __fadd_rn(comp[q], __fadd_rn(__fsub_rn(part[q], __fsub_rn(t, bb)),
+                                                   __fsub_rn(x, bb)));
+            part[q] = t;
+        } else {
+            part[q] += x;
+        }
+    };
     auto fold = [&]() {
 #pragma unroll
         for (int q = 0; q < 7; ++q)
-            acc[q] = (q == 5) ? fmax(acc[q], (double)part[q]) : acc[q] + (double)part[q];
+            acc[q] = (q == 5) ? fmax(acc[q], (double)part[q])
+                              : acc[q] + (double)part[q] + (double)comp[q];
 #pragma unroll
-        for (int q = 0; q < 7; ++q) part[q] = T(0);
+        for (int q = 0; q < 7; ++q) part[q] = T(0), comp[q] = T(0);
         pending = 0;
     };
     auto x0_of = [&](int t) { return 2 + (t / (nz * ny)) * GTX; };
@@ -353,11 +376,11 @@ __global__ void __launch_bounds__(GTHREADS, kTileMinBlocks<T, EXT>) k_tile(FlowP
             if (dout) store4<T>(dout + s, make4<T>(dens[0], dens[1], dens[2], dens[3]));
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) part[q] += dens[q];
+        for (int q = 0; q < 4; ++q) add(q, dens[q]);
         const T f2 = F[0] * F[0] + F[1] * F[1] + F[2] * F[2] + F[3] * F[3];
         part[4] += f2;
         part[5] = part[5] > f2 ? part[5] : f2;
-        part[6] += e6;
+        if constexpr (EXT) add(6, e6);
         if (++pending == kFoldTiles) fold();
     }
     if (pending) fold();
@@ -537,6 +560,7 @@ template <typename T> static FlowParams<T> make_params(const FlowArgs &a, double
     p.dt = T(a.dt);
     p.h3 = a.h * a.h * a.h;
     p.mode = a.mode;
+    p.slab_rec = a.slab_rec;
     return p;
 }
 
@@ -631,6 +655,35 @@ cudaError_t launch_load_finish(const skyrme_lattice &lat, const FlowArgs &a, cud
 cudaError_t launch_reset_ctrl(void *ctrl, cudaStream_t s)
 {
     k_reset_ctrl<<<1, 32, 0, s>>>(static_cast<Ctrl *>(ctrl));
+    return cudaGetLastError();
+}
+
+// The arrest decision of a lattice cut into x-slabs (Section 3 arrest rule on
+// the whole lattice's energy): the slabs' records {e2, e4, e0, b, |F|^2,
+// max |F|^2, sites, e6} are combined in slab order, so every slab (every rank)
+// that combines the same records reaches the same decision, predictor state
+// and report; then the end-of-step bookkeeping of a whole lattice runs.
+__global__ void k_slab_decide(Ctrl *c, const double *__restrict__ recs, int nslabs, double h3,
+                              int mode)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double tot[kPartialDoubles];
+#pragma unroll
+    for (int q = 0; q < kPartialDoubles; ++q) tot[q] = 0.0;
+    for (int sl = 0; sl < nslabs; ++sl)
+#pragma unroll
+        for (int q = 0; q < kPartialDoubles; ++q) {
+            const double v = recs[(size_t)sl * kPartialDoubles + q];
+            tot[q] = (q == 5) ? fmax(tot[q], v) : tot[q] + v;
+        }
+    const int pred = (mode == MODE_ARRESTED) ? c->pred : 0;
+    finish_step(c, tot, h3, mode, pred);
+}
+
+cudaError_t launch_slab_decide(void *ctrl, const double *records, int nslabs, double h3, int mode,
+                               cudaStream_t s)
+{
+    k_slab_decide<<<1, 32, 0, s>>>(static_cast<Ctrl *>(ctrl), records, nslabs, h3, mode);
     return cudaGetLastError();
 }
 

@@ -369,8 +369,10 @@ __device__ __forceinline__ void reduce_partials(const double *parts, int nparts,
     }
 }
 
-// End-of-step bookkeeping, run by thread 0 of the last CTA to arrive.
-// tot = {sum e2, sum e4, sum e0, sum b, sum |F|^2, max |F|^2, n_sites, -}.
+// End-of-step bookkeeping, run by thread 0 of the last CTA to arrive (or,
+// for a lattice split into x-slabs, by the one-thread kernel that combines the
+// slabs' records).
+// tot = {sum e2, sum e4, sum e0, sum b, sum |F|^2, max |F|^2, n_sites, sum e6}.
 __device__ __forceinline__ void finish_step(Ctrl *c, const double (&tot)[kPartialDoubles],
                                             double h3, int mode, int pred)
 {

@@ -40,6 +40,12 @@ struct FlowArgs {
     double h, m, dt;
     double my, mz, mw, c6;  // Section 7.8 extension coefficients
     int mode;
+    // x-slab of a larger lattice: the step writes its 8-double record here and
+    // leaves the arrest decision to launch_slab_decide (null: a whole lattice)
+    double *slab_rec = nullptr;
+    // FP32 streaming step only: per-site densities the step summed (float4
+    // per site, null: none)
+    void *dump = nullptr;
 };
 
 // A lattice with any Section 7.8 extension term switched on.
@@ -54,6 +60,11 @@ inline bool lattice_potentials(const skyrme_lattice &lat)
     return lat.m_y != 0.0 || lat.m_z != 0.0 || lat.m_w != 0.0;
 }
 
+// Argument checks shared by the entry points (api.cu): lattice sizes, spacing
+// and coefficients; every non-null pointer on the current device.
+bool lattice_ok(const skyrme_lattice *lat);
+skyrme_status on_current_device(const void *const *ptrs, int n);
+
 // Kernels (asynchronous, return the launch error)
 cudaError_t launch_step(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s);
 cudaError_t launch_fixup(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s);
@@ -62,6 +73,12 @@ cudaError_t launch_forces(const skyrme_lattice &lat, const FlowArgs &a, void *fo
                           cudaStream_t s);
 cudaError_t launch_load_finish(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s);
 cudaError_t launch_reset_ctrl(void *ctrl, cudaStream_t s);
+// Sum nslabs slab records (8 doubles each, slab order) and run the lattice's
+// end-of-step bookkeeping: arrest decision, predictor, fix flag, buffer flip.
+cudaError_t launch_slab_decide(void *ctrl, const double *records, int nslabs, double h3, int mode,
+                               cudaStream_t s);
+// The FP32 streaming path's arrest fix-up (the whole-lattice flow's own).
+cudaError_t launch_fixup_f32_fast(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s);
 cudaError_t launch_until_arm(void *ctrl, unsigned long long handle, cudaStream_t s);
 cudaError_t launch_until_check(void *ctrl, unsigned long long handle, double tol,
                                long long max_steps, cudaStream_t s);

@@ -61,3 +61,18 @@ def test_static_energy_rejects_lattices_beyond_its_array():
     assert rc == 1  # SKYRME_EINVAL: 2049 interior x-planes > 2048
     rc, _ = call_static(lib, sk.Lattice((20, 20, 20), 0.1, 1.0, 32), phi.data_ptr() + 4)
     assert rc == 1  # misaligned field pointer
+
+
+def test_static_energy_rejects_a_field_in_host_memory():
+    """The kernel runs on the current device, so a field it cannot address is
+    refused before any launch, and the next call works as before."""
+    lib = sk.load()
+    n = (20, 20, 20)
+    lat = sk.Lattice(n, 0.1, 1.0, 32)
+    host = np.zeros(n + (4,), dtype=np.float32)
+    rc, _ = call_static(lib, lat, host.ctypes.data)
+    assert rc == 1  # SKYRME_EINVAL
+    phi = torch.zeros(n + (4,), dtype=torch.float32, device="cuda:0")
+    phi[..., 0] = 1.0
+    rc, got = call_static(lib, lat, phi.data_ptr())
+    assert rc == 0 and got[0] == 0.0
