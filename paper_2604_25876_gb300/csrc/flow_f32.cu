@@ -21,15 +21,17 @@
 //    instead of hanging.  Warps consume the planes independently: the last
 //    warp to be done with a slot (a shared-memory counter) streams the next
 //    plane into it, so the only CTA-wide barriers are at the ends of runs.
+//  * the in-plane values a plane contributes to its own centre two planes
+//    later (13 per site) wait in tensor memory: each warp keeps a 3-slot ring
+//    of them in its TMEM lanes (tcgen05.st / tcgen05.ld), which takes them
+//    off the shared-memory pipe and out of shared memory.
 //  * in-plane derivatives (d_y, d_z, d_yy, d_zz) come from the staged plane;
 //    d_yz = d_z(d_y phi) uses a per-warp shared-memory exchange of d_y phi
 //    (each warp computes the 4 z-halo columns of its own rows); d_x, d_xx,
 //    d_xy = d_x(d_y phi), d_xz = d_x(d_z phi) come from a 5-plane register
 //    ring of (phi, d_y phi, d_z phi) that the x-loop cycles through (unrolled
-//    by 5 so no register is ever moved).  The in-plane contractions a plane
-//    contributes to its own centre two planes later wait in a per-thread
-//    shared-memory ring, and the velocity of each centre plane arrives by TMA
-//    together with the field plane two planes ahead.
+//    by 5 so no register is ever moved).  The velocity of each centre plane
+//    arrives by TMA together with the field plane two planes ahead.
 //  * 4-vector arithmetic uses the packed FP32 pair instructions of sm_100+
 //    (__ffma2_rn / __fadd2_rn / __fmul2_rn): two components per instruction;
 //    stencil weights are stored as (w, w) pairs.
@@ -157,6 +159,61 @@ __device__ __forceinline__ void tma_plane(void *dst, const CUtensorMap *map,
         " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
         : "memory");
+}
+
+
+// ------------------------------------------------- tensor memory helpers
+// Tensor memory (256 KiB per SM: 128 lanes x 512 columns of 32 bits) holds
+// each thread's ring of in-plane records.  Warp 0 allocates the CTA's
+// columns when the kernel starts and frees them when it ends, on every path
+// (tcgen05.alloc / tcgen05.dealloc).  A warp can address only the 32 lanes of
+// its quarter of a warpgroup, 32 * (warp % 4); among the warps sharing those
+// lanes, warp w owns columns [kTmemColsPerWarp * (w / 4), +kTmemColsPerWarp).
+// Thread t of a warp reads and writes its own lane (the 32x32b shapes).
+constexpr int kRecCols = 16;                    // one in-plane record (13 values used)
+constexpr int kTmemColsPerWarp = 3 * kRecCols;  // three records in flight
+template <int NW> constexpr uint32_t tmem_cols()
+{
+    constexpr int need = ((NW + 3) / 4) * kTmemColsPerWarp;
+    return need <= 32 ? 32 : need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+        "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]),
+        "f"(v[9]), "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15])
+        : "memory");
+}
+// Load 16 columns; the values are usable only after the wait, so they pass
+// through the wait's own operands (no use can be scheduled before it).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]),
+          "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]),
+                   "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]), "+f"(v[13]), "+f"(v[14]), "+f"(v[15])
+                 :
+                 : "memory");
 }
 
 // ------------------------------------------------- packed 4-vector helpers
@@ -389,8 +446,6 @@ template <int TY, int TZ> struct __align__(128) StepSmem {
     float4 vpl[NSLOT][TY][TZ];            // velocity planes of the centre sites (TMA)
     float4 dy[2][TY][TZ + 4];             // d_y phi exchange for d_yz
     int rel[NSLOT];                       // warps done with the plane in each slot
-    float4 inpl[3][3][TY * TZ];           // per-thread in-plane values of the last 3 planes
-    float inyz[3][TY * TZ];               // ... and their a_yz
     DF accs[kSums][TY * TZ];              // per-thread double-float sums (kept out of registers)
     float amaxs[TY * TZ];                 // per-thread max |F|^2
     unsigned long long bar[NSLOT];
@@ -398,7 +453,21 @@ template <int TY, int TZ> struct __align__(128) StepSmem {
     float mxred[TY * TZ / 32];
     int flag;
     int last;
+    uint32_t tmem;                        // TMEM base address of the CTA's allocation
 };
+
+// Dynamic shared memory requested by a step CTA: its StepSmem, padded so
+// that one CTA more than the SM's 512 TMEM columns can serve would need more
+// than the SM's 228 KiB of shared memory, and so never becomes resident
+// (tcgen05.alloc in that CTA would otherwise wait for a co-resident CTA to
+// free its columns).
+template <int TY, int TZ> constexpr size_t step_smem_bytes()
+{
+    constexpr size_t per_sm = 228 * 1024;
+    constexpr int max_ctas = 512 / tmem_cols<TY * TZ / 32>();
+    constexpr size_t floor_bytes = per_sm / (max_ctas + 1) + 1;  // max_ctas + 1 never fit
+    return sizeof(StepSmem<TY, TZ>) > floor_bytes ? sizeof(StepSmem<TY, TZ>) : floor_bytes;
+}
 
 struct CtaSync {
     __device__ __forceinline__ void operator()() const { __syncthreads(); }
@@ -444,7 +513,7 @@ __device__ __forceinline__ void arrive_plane(const float4 (*P)[TZ + 4], float4 (
 template <int TY, int TZ>
 __device__ __forceinline__ void plane_record(const float4 (*DY)[TZ + 4], const InstDesc &D, int ty,
                                              int tz, const PlaneVals &rv, const P4 &dyy,
-                                             const P4 &dzz, float4 *wrec, float *wyz)
+                                             const P4 &dzz, uint32_t trec)
 {
     constexpr int THREADS = TY * TZ;
     const P4 dy = rv.dy, dz = rv.dz;
@@ -455,10 +524,10 @@ __device__ __forceinline__ void plane_record(const float4 (*DY)[TZ + 4], const I
     const P4 qin = fma(bc(2.f * ayz), dyz, fma(bc(azz), dzz, mul(bc(ayy), dyy)));
     const float gyv = hsum(dot2(dyz, dz, __ffma2_rn(dyy.b, dy.b, __fmul2_rn(dyy.a, dy.a))));
     const float gzv = hsum(dot2(dzz, dz, __ffma2_rn(dyz.b, dy.b, __fmul2_rn(dyz.a, dy.a))));
-    wrec[0] = st4(lin);
-    wrec[THREADS] = st4(qin);
-    wrec[2 * THREADS] = make_float4(gyv, gzv, ayy, azz);
-    *wyz = ayz;
+    const float r[16] = {lin.a.x, lin.a.y, lin.b.x, lin.b.y, qin.a.x, qin.a.y, qin.b.x, qin.b.y,
+                         gyv, gzv, ayy, azz, ayz, 0.f, 0.f, 0.f};
+    (void)THREADS;
+    tmem_st16(trec, r);
 }
 
 // One centre site: x-derivatives from the register ring (M2, M1, C, Q1, Q2 in
@@ -470,7 +539,7 @@ template <int TY, int TZ, bool POT = false, bool DUMP = false>
 __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &M2,
                                             const PlaneVals &M1, const PlaneVals &C,
                                             const PlaneVals &Q1, const PlaneVals &Q2, float2 xc1,
-                                            float2 xc2, const float4 *rec, const float *recyz,
+                                            float2 xc2, uint32_t trec,
                                             const float4 *vp,
                                             bool use_v, bool valid, float4 *phiout, float4 *vout,
                                             size_t si, Acc &a32)
@@ -479,10 +548,14 @@ __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &
     const float2 s1 = D.s1, s2 = D.s2, s0 = D.s0;
     const int mode = D.mode;
     const float2 dt = D.dt, dt2 = D.dt2;
-    const P4 lin = ld4(rec[0]), qin = ld4(rec[THREADS]);
-    const float4 r2 = rec[2 * THREADS];
-    const float Cgy = r2.x, Cgz = r2.y, Cayy = r2.z, Cazz = r2.w;
-    const float Cayz = *recyz;
+    float rv[16];
+    tmem_wait_st();  // this thread's earlier record stores have landed
+    tmem_ld16(trec, rv);
+    const P4 lin = {make_float2(rv[0], rv[1]), make_float2(rv[2], rv[3])};
+    const P4 qin = {make_float2(rv[4], rv[5]), make_float2(rv[6], rv[7])};
+    const float Cgy = rv[8], Cgz = rv[9], Cayy = rv[10], Cazz = rv[11];
+    const float Cayz = rv[12];
+    (void)THREADS;
     const P4 ph = C.phi;
     const P4 dx = fd1(M2.phi, M1.phi, Q1.phi, Q2.phi, xc1, xc2);
     const P4 dxx = fd2(M2.phi, M1.phi, ph, Q1.phi, Q2.phi, s1, s2, s0);
@@ -708,7 +781,13 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
         mbar_fence_init();
         sm.flag = 0;
     }
+    constexpr uint32_t TCOLS = tmem_cols<THREADS / 32>();
+    if (tid < 32) tmem_alloc(&sm.tmem, TCOLS);
+    tmem_fence_before();
     __syncthreads();
+    tmem_fence_after();
+    const uint32_t twarp = sm.tmem + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) +
+                           (uint32_t)(kTmemColsPerWarp * ((tid >> 5) >> 2));
 
     const bool listed = !BATCHED && split.n > 0;
     const long long u0 = listed ? split.start[blockIdx.x] : total_units * blockIdx.x / gridDim.x;
@@ -784,10 +863,11 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
                     // ---- centre x = pp - 2, whose in-plane record is that of plane g - 2
                     const uint32_t g3n = g3 == 2 ? 0 : g3 + 1;  // (g + 1) % 3 == (g - 2) % 3
                     const int x = pp - 2;
+                    __syncwarp();
                     if (x >= xs)
                         centre_site<TY, TZ, POT, DUMP>(D, ring[(k + 1) % 5], ring[(k + 2) % 5], ring[(k + 3) % 5],
                                             ring[(k + 4) % 5], ring[k], D.c1, D.c2,
-                                            &sm.inpl[g3n][0][tid], &sm.inyz[g3n][tid],
+                                            twarp + kRecCols * g3n,
                                             &sm.vpl[s][ty][tz], use_v,
                                             valid, phiout, vout, (size_t)x * plane_stride + col_off, a32);
                     // this warp is done with slot s; the last warp to leave it streams
@@ -808,8 +888,7 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
                         failed = true;
                         break;
                     }
-                    plane_record<TY, TZ>(DY, D, ty, tz, ring[k], dyy, dzz, &sm.inpl[g3][0][tid],
-                                         &sm.inyz[g3][tid]);
+                    plane_record<TY, TZ>(DY, D, ty, tz, ring[k], dyy, dzz, twarp + kRecCols * g3);
                     ++g;
                     g3 = g3n;
                 }
@@ -862,6 +941,14 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
                 (void)mbar_wait(&sm.bar[s], 1, 50000000ull);
             }
         }
+    }
+    // every warp is done with its TMEM columns: free the allocation
+    tmem_wait_st();
+    tmem_fence_before();
+    __syncthreads();
+    if (tid < 32) {
+        tmem_fence_after();
+        tmem_dealloc(sm.tmem, TCOLS);
     }
 }
 
@@ -1030,12 +1117,12 @@ static cudaError_t launch_shape(const InstDesc &one, const CtaSplit &split, cons
         if (dev < 64 && !done[dev]) {
             cudaError_t e = cudaFuncSetAttribute(k_step_f32<TY, TZ, B>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)sizeof(StepSmem<TY, TZ>));
+                                                 (int)step_smem_bytes<TY, TZ>());
             if (e != cudaSuccess) return e;
             done[dev] = true;
         }
     }
-    k_step_f32<TY, TZ, B><<<(unsigned)grid, TY * TZ, sizeof(StepSmem<TY, TZ>), s>>>(
+    k_step_f32<TY, TZ, B><<<(unsigned)grid, TY * TZ, step_smem_bytes<TY, TZ>(), s>>>(
         one, split, table, ninst, units, dry);
     return cudaGetLastError();
 }
@@ -1059,9 +1146,9 @@ template <int TY, int TZ, bool B> static int occupancy_of()
 {
     int n = 0;
     cudaFuncSetAttribute(k_step_f32<TY, TZ, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(StepSmem<TY, TZ>));
+                         (int)step_smem_bytes<TY, TZ>());
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_f32<TY, TZ, B>, TY * TZ,
-                                                      sizeof(StepSmem<TY, TZ>)) != cudaSuccess)
+                                                      step_smem_bytes<TY, TZ>()) != cudaSuccess)
         n = 1;
     return n > 0 ? n : 1;
 }
@@ -1322,7 +1409,7 @@ cudaError_t launch_iterations_f32_fast(const skyrme_lattice &lat, const FlowArgs
         std::lock_guard<std::mutex> lock(mu);
         if (dev < 64 && !done[which][dev]) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)sizeof(StepSmem<16, 32>));
+                                                 (int)step_smem_bytes<16, 32>());
             if (e != cudaSuccess) return e;
             done[which][dev] = true;
         }
@@ -1339,7 +1426,7 @@ cudaError_t launch_iterations_f32_fast(const skyrme_lattice &lat, const FlowArgs
             args[4] = &units;
             args[5] = &dry;
             e = cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(16 * 32), args,
-                                 sizeof(StepSmem<16, 32>), s);
+                                 step_smem_bytes<16, 32>(), s);
         } else {
             e = launch_tile<false>(tile, ds[0], split, nullptr, 1, ds[0].units, grid, 0, s);
         }

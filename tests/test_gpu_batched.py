@@ -52,6 +52,30 @@ def test_batch_matches_lattices_flowed_alone():
     b.close()
 
 
+@pytest.mark.parametrize("tile", [0, 4])
+def test_batch_tracks_the_oracle_trajectories(tile):
+    """Every lattice of a batch of uneven sizes against the FP64 oracle's
+    own flow of the same (FP32-rounded) seed: 40 iterations, per site and in
+    energy, with the same arrest decisions.  The bounds are those of a single
+    FP32 lattice against the oracle (tests/test_gpu_parity.py)."""
+    lats, states = make_states()
+    seeds = [st.field().double().cpu().numpy() for st in states]
+    b = sk.Batch(lats, states, [0.01] * len(lats))
+    b.set_tile(tile)
+    b.step(40)
+    torch.cuda.synchronize()
+    for lat, st, phi0 in zip(lats, states, seeds):
+        ost = oracle.new_state(phi0)
+        oreps = oracle.flow(ost, lat.h, lat.m, 0.01, 40, reports=True)
+        rep = sk.read_report(lat, st)
+        assert rep["steps"] == 40 and rep["status"] == 0
+        assert rep["arrests"] == sum(r["arrested"] for r in oreps)
+        assert rep["E"] == pytest.approx(oreps[-1]["E"], rel=1e-5)
+        assert rep["B"] == pytest.approx(oreps[-1]["B"], abs=1e-5)
+        assert np.max(np.abs(st.field().double().cpu().numpy() - ost.phi)) < 1e-4
+    b.close()
+
+
 @pytest.mark.parametrize("tile", [0, 1, 2, 3, 4])
 def test_every_tile_shape_gives_the_same_flow(tile):
     lats, states = make_states(kind="noise")
