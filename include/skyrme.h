@@ -222,8 +222,8 @@ skyrme_status skyrme_step_densities(const skyrme_lattice *lat, double dt, int mo
 
 /* ---- the flow as a CUDA graph ----
  * skyrme_graph_create captures `nsteps` iterations exactly as
- * skyrme_flow_step launches them (the step kernel and, in ARRESTED mode, the
- * fix-up check) on `stream`, which must be a stream that can be captured
+ * skyrme_flow_step launches them (the step kernel and, where it has one, the
+ * arrest fix-up check) on `stream`, which must be a stream that can be captured
  * (not the legacy default stream), and instantiates the graph.  The flow
  * state lives on the device, so one graph advances the flow by nsteps
  * iterations every time it is launched, for as long as the state's buffers

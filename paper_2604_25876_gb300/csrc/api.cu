@@ -153,6 +153,8 @@ skyrme_status make_graph(skyrme_batch *b, int nsteps, cudaStream_t s, skyrme_gra
         delete g;
         return cuda_fail(e, "instantiate graph");
     }
+    // upload now, so that the first launch does not pay for it
+    (void)cudaGraphUpload(g->exec, s);
     *out = g;
     return SKYRME_OK;
 }
@@ -476,6 +478,8 @@ skyrme_status skyrme_graph_create(const skyrme_lattice *lat, double dt, int nste
         delete g;
         return cuda_fail(e, "instantiate graph");
     }
+    // upload now, so that the first launch does not pay for it
+    (void)cudaGraphUpload(g->exec, s);
     *out = g;
     return SKYRME_OK;
 }
@@ -551,6 +555,8 @@ skyrme_status skyrme_graph_create_until(const skyrme_lattice *lat, double dt, in
         delete g;
         return cuda_fail(e, "instantiate graph");
     }
+    // upload now, so that the first launch does not pay for it
+    (void)cudaGraphUpload(g->exec, s);
     *out = g;
     return SKYRME_OK;
 }

@@ -90,6 +90,7 @@ struct InstDesc {
     int mode;
     double *slab_rec;      // x-slab of a larger lattice: record out, no decision (else null)
     float4 *dump;          // DUMP kernels: per-site densities the step sums
+    int fuse_fix;          // single lattice, ARRESTED: the step corrects its own mispredictions
 };
 
 // Unit ranges of the CTAs of a single-lattice launch: CTA b streams units
@@ -453,6 +454,9 @@ template <int TY, int TZ> struct __align__(128) StepSmem {
     float mxred[TY * TZ / 32];
     int flag;
     int last;
+    int fixv;                             // the decided correction (fused arrest fix-up)
+    int cur_used;                         // ... the buffers the step read
+    long long steps0;                     // ... and the step count before the step
     uint32_t tmem;                        // TMEM base address of the CTA's allocation
 };
 
@@ -633,6 +637,23 @@ __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &
     }
 }
 
+// One site of the correction of a mispredicted arrest decision:
+// v = v_new + sgn v_old, phi = normalise(phi_old + dt v).  Every operation is
+// rounded explicitly, so that every path that corrects a site (the fix-up
+// kernels, the step's own correction, an x-slab's fix-up) gives the same bits.
+__device__ __forceinline__ void arrest_fix_site(const float4 &vn, const float4 &vo,
+                                                const float4 &fo, float sgn, float dt, float4 &v,
+                                                float4 &p)
+{
+    v = make_float4(__fmaf_rn(sgn, vo.x, vn.x), __fmaf_rn(sgn, vo.y, vn.y),
+                    __fmaf_rn(sgn, vo.z, vn.z), __fmaf_rn(sgn, vo.w, vn.w));
+    const float4 t = make_float4(__fmaf_rn(dt, v.x, fo.x), __fmaf_rn(dt, v.y, fo.y),
+                                 __fmaf_rn(dt, v.z, fo.z), __fmaf_rn(dt, v.w, fo.w));
+    const float r =
+        rsqrtf(__fmaf_rn(t.w, t.w, __fmaf_rn(t.z, t.z, __fmaf_rn(t.y, t.y, __fmul_rn(t.x, t.x)))));
+    p = make_float4(__fmul_rn(t.x, r), __fmul_rn(t.y, r), __fmul_rn(t.z, r), __fmul_rn(t.w, r));
+}
+
 __device__ __forceinline__ void write_record(const InstDesc &D, int slot, const DF (&tot)[kSums], float tmax)
 {
     float4 *recp = reinterpret_cast<float4 *>(D.parts + (size_t)slot * kPartialDoubles);
@@ -740,7 +761,6 @@ __device__ __forceinline__ void finish_lattice(const InstDesc &D, Ctrl *c, int c
     c->arrests = arrests + actual;
     c->fixups = fixups + (fix != 0);
     c->E_prev = Ed;
-    c->steps = steps + 1;
     c->cur = cur ^ 1;
     const double nsites = (double)(D.n0 - 4) * (double)(D.n1 - 4) * (double)(D.n2 - 4);
     c->last[0] = Ed;
@@ -753,6 +773,72 @@ __device__ __forceinline__ void finish_lattice(const InstDesc &D, Ctrl *c, int c
     c->last[7] = sqrt(df_value(t[4]) / (double)nsites);
     if (!(isfinite(Ed) && isfinite(B.hi) && isfinite(t[4].hi))) c->status = DEV_NONFINITE;
     c->done = 0;
+    // the step count goes last, after a fence: CTAs that correct their own
+    // sites wait for it, and then see every field above
+    __threadfence();
+    *(volatile long long *)&c->steps = steps + 1;
+}
+
+__device__ __forceinline__ long long ld_acquire_s64(const long long *p)
+{
+    long long v;
+    asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// The step's own correction of a mispredicted arrest decision, at the sites
+// this CTA updated (units [u0, u1) of the single lattice D, whose step read
+// buffers `cur`): v = v' + fix v_old, phi = normalise(phi_old + dt v) by
+// arrest_fix_site.  Each thread corrects the very sites it wrote, four planes
+// of loads in flight at a time.
+// (Its unit arithmetic is 32-bit: a 64-bit division here made the compiler
+// spill the main loop's registers.)
+template <int TY, int TZ>
+__device__ __forceinline__ void correct_own_sites(const InstDesc &D, long long u0, long long u1,
+                                                  int cur, int fix, int ty, int tz)
+{
+    // buffers selected by value, not by a run-time index into the parameter
+    const float4 *__restrict__ vo_p = cur ? D.vel[1] : D.vel[0];
+    const float4 *__restrict__ fo_p = cur ? D.phi[1] : D.phi[0];
+    float4 *__restrict__ vn_p = cur ? D.vel[0] : D.vel[1];
+    float4 *__restrict__ fn_p = cur ? D.phi[0] : D.phi[1];
+    const size_t ps = (size_t)D.n1 * D.n2;
+    const float sgn = (float)fix, dt = D.dt.x;
+    // a single lattice's units (columns x interior planes) fit in an int
+    const int nix = D.nix, nzt = D.nzt, w1 = (int)(u1 - D.unit_start);
+    for (int us = (int)(u0 - D.unit_start); us < w1;) {
+        const int col = us / nix;
+        const int ue = min(w1, (col + 1) * nix);
+        const int xs = 2 + (us - col * nix);
+        const int xe = 2 + (ue - col * nix);
+        us = ue;
+        const int y = 2 + (col / nzt) * TY + ty, z = 2 + (col % nzt) * TZ + tz;
+        if (y > D.n1 - 3 || z > D.n2 - 3) continue;
+        size_t si = (size_t)xs * ps + (size_t)y * D.n2 + z;
+        int x = xs;
+        for (; x + 4 <= xe; x += 4, si += 4 * ps) {
+            float4 vn[4], vo[4], fo[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                vn[k] = __ldcg(vn_p + si + k * ps);
+                vo[k] = __ldcs(vo_p + si + k * ps);
+                fo[k] = __ldcs(fo_p + si + k * ps);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float4 v, p;
+                arrest_fix_site(vn[k], vo[k], fo[k], sgn, dt, v, p);
+                vn_p[si + k * ps] = v;
+                fn_p[si + k * ps] = p;
+            }
+        }
+        for (; x < xe; ++x, si += ps) {
+            float4 v, p;
+            arrest_fix_site(__ldcg(vn_p + si), __ldcs(vo_p + si), __ldcs(fo_p + si), sgn, dt, v, p);
+            vn_p[si] = v;
+            fn_p[si] = p;
+        }
+    }
 }
 
 // The step for every lattice of the launch, two CTAs per SM.  BATCHED:
@@ -796,6 +882,9 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
     int inst = 0;
     if (BATCHED)
         while (inst + 1 < ninst && table[inst + 1].unit_start <= u0) ++inst;
+    // single lattice with the fused correction: the step count before this
+    // step (kept in shared memory, out of the main loop's registers)
+    if (!BATCHED && one.fuse_fix && tid == 0) sm.steps0 = __ldcg(&one.ctrl->steps);
     uint32_t g = 0;   // planes consumed by this CTA (ring sequence number)
     uint32_t g3 = 0;  // g % 3, the in-plane record slot of plane g
     bool failed = false;
@@ -807,6 +896,7 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
         const long long seg_hi = min(u1, D.unit_start + D.units);
         Ctrl *ctrl = D.ctrl;
         const int cur = __ldcg(&ctrl->cur);
+        if (!BATCHED && tid == 0) sm.cur_used = cur;
         const int pred = (D.mode == MODE_ARRESTED) ? __ldcg(&ctrl->pred) : 0;
         const CUtensorMap *map = &D.map[cur];
         const CUtensorMap *vmap = &D.vmap[cur];
@@ -930,6 +1020,37 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
         __syncthreads();
     }
 
+    if constexpr (!BATCHED) {
+        if (one.fuse_fix && !failed) {
+            // the arrest decision is made by the last CTA to finish; every CTA
+            // (all resident: a cooperative launch of at most one per SM) waits
+            // for it, bounded, and corrects its own sites when the decision the
+            // step ran with was wrong
+            if (tid == 0) {
+                const long long steps0 = sm.steps0;
+                long long st = ld_acquire_s64(&one.ctrl->steps);
+                if (st == steps0) {
+                    const unsigned long long t0 = global_ns();
+                    do {
+                        st = ld_acquire_s64(&one.ctrl->steps);
+                    } while (st == steps0 && global_ns() - t0 < kWaitLimitNs);
+                }
+                sm.fixv = (st == steps0) ? 2 : __ldcg(&one.ctrl->fix);
+            }
+            __syncthreads();
+            const int fx = sm.fixv;
+            if (fx == 2) {
+                if (tid == 0) atomicExch(&one.ctrl->status, (int)DEV_TIMEOUT);
+            } else if (fx != 0) {
+                const bool listed2 = split.n > 0;
+                const long long v0 = listed2 ? split.start[blockIdx.x] : total_units * blockIdx.x / gridDim.x;
+                const long long v1 =
+                    listed2 ? split.start[blockIdx.x + 1] : total_units * (blockIdx.x + 1) / gridDim.x;
+                correct_own_sites<TY, TZ>(one, v0, v1, sm.cur_used, fx, tid / TZ, tid % TZ);
+            }
+        }
+    }
+
     if (failed) {
         // a plane copy never landed: record it, let in-flight copies finish
         // (bounded), and leave without closing the lattice's reduction
@@ -988,13 +1109,10 @@ __device__ __forceinline__ void fixup_rows(float4 *const (&phi)[2], float4 *cons
             for (int k = 0; k < 2; ++k) {
                 const int z = z0 + 32 * k + lane;
                 if (z < iz) {
-                    const float4 v = make_float4(vn[k].x + sgn * vo[k].x, vn[k].y + sgn * vo[k].y,
-                                                 vn[k].z + sgn * vo[k].z, vn[k].w + sgn * vo[k].w);
-                    const float4 t = make_float4(fo[k].x + dt * v.x, fo[k].y + dt * v.y,
-                                                 fo[k].z + dt * v.z, fo[k].w + dt * v.w);
-                    const float r = rsqrtf(t.x * t.x + t.y * t.y + t.z * t.z + t.w * t.w);
+                    float4 v, p;
+                    arrest_fix_site(vn[k], vo[k], fo[k], sgn, dt, v, p);
                     vst[base + z] = v;
-                    fst[base + z] = make_float4(t.x * r, t.y * r, t.z * r, t.w * r);
+                    fst[base + z] = p;
                 }
             }
         }
@@ -1378,32 +1496,22 @@ cudaError_t launch_iterations_f32_fast(const skyrme_lattice &lat, const FlowArgs
     if (balanced_split(ds[0].units, ds[0].nix, grid, split)) grid = split.n;
     partition(ds, grid, a.step_parts);
 
-    FixDesc fx;
-    for (int i = 0; i < 2; ++i) {
-        fx.phi[i] = static_cast<float4 *>(a.phi[i]);
-        fx.vel[i] = static_cast<float4 *>(a.vel[i]);
-    }
-    fx.ctrl = static_cast<Ctrl *>(a.ctrl);
-    fx.n0 = lat.n[0];
-    fx.n1 = lat.n[1];
-    fx.n2 = lat.n[2];
-    fx.dt = (float)a.dt;
-    const long long rows = (long long)(lat.n[0] - 4) * (lat.n[1] - 4);
-    const int fix_blocks = (int)std::max(1LL, std::min((long long)sm_count() * 2, (rows + 15) / 16));
-
     ds[0].slab_rec = a.slab_rec;
     ds[0].dump = static_cast<float4 *>(a.dump);
+    // ARRESTED whole lattices correct their own mispredicted decisions inside
+    // the step (the CTAs wait for the last one's decision, so the launch is
+    // cooperative: every CTA resident at once); an x-slab's decision and
+    // fix-up come after the decision over all slabs
+    const bool fused = a.mode == SKYRME_ARRESTED && !a.slab_rec;
+    ds[0].fuse_fix = fused ? 1 : 0;
     const bool pot = lattice_potentials(lat);
     const bool dump = a.dump != nullptr;
-    // the single-lattice instantiations besides the tile table: the
-    // potentials variant and the density-dump variants
-    void *kern = nullptr;
-    if (pot) kern = dump ? kernel_ptr<16, 32, false, true, true>() : kernel_ptr<16, 32, false, true>();
-    else if (dump) kern = kernel_ptr<16, 32, false, false, true>();
-    if (kern) {
+    void *kern = pot ? (dump ? kernel_ptr<16, 32, false, true, true>() : kernel_ptr<16, 32, false, true>())
+                     : (dump ? kernel_ptr<16, 32, false, false, true>() : kernel_ptr<16, 32, false>());
+    {
         static std::mutex mu;
-        static bool done[3][64] = {{false}};
-        const int which = pot ? (dump ? 2 : 1) : 0;
+        static bool done[4][64] = {{false}};
+        const int which = (pot ? 2 : 0) + (dump ? 1 : 0);
         int dev = 0;
         cudaGetDevice(&dev);
         std::lock_guard<std::mutex> lock(mu);
@@ -1414,28 +1522,24 @@ cudaError_t launch_iterations_f32_fast(const skyrme_lattice &lat, const FlowArgs
             done[which][dev] = true;
         }
     }
+    const InstDesc *tab = nullptr;
+    int ninst = 1, dry = 0;
+    long long units = ds[0].units;
+    void *args[] = {(void *)&ds[0], (void *)&split, (void *)&tab, (void *)&ninst, (void *)&units,
+                    (void *)&dry};
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeCooperative;
+    attr.val.cooperative = fused ? 1 : 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(16 * 32);
+    cfg.dynamicSmemBytes = step_smem_bytes<16, 32>();
+    cfg.stream = s;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
     for (int k = 0; k < nsteps; ++k) {
-        cudaError_t e;
-        if (kern) {
-            void *args[] = {(void *)&ds[0], (void *)&split, nullptr, nullptr, nullptr, nullptr};
-            const InstDesc *tab = nullptr;
-            int ninst = 1, dry = 0;
-            long long units = ds[0].units;
-            args[2] = &tab;
-            args[3] = &ninst;
-            args[4] = &units;
-            args[5] = &dry;
-            e = cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(16 * 32), args,
-                                 step_smem_bytes<16, 32>(), s);
-        } else {
-            e = launch_tile<false>(tile, ds[0], split, nullptr, 1, ds[0].units, grid, 0, s);
-        }
+        const cudaError_t e = cudaLaunchKernelExC(&cfg, kern, args);
         if (e != cudaSuccess) return e;
-        // an x-slab's fix-up follows the decision over all slabs
-        if (a.mode == SKYRME_ARRESTED && !a.slab_rec) {
-            k_fixup_one<<<fix_blocks, 512, 0, s>>>(fx);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        }
     }
     return cudaSuccess;
 }
