@@ -60,9 +60,9 @@ typedef enum { SKYRME_NEWTON = 0, SKYRME_ARRESTED = 1, SKYRME_GRADIENT = 2 } sky
  * All five coefficients are finite and >= 0; m_y = m_z = m_w = c6 = 0 is the
  * standard model.  A lattice with any of the four extension coefficients
  * non-zero is an "extended" lattice: the batched flow and the Section 5
- * observables reject it with SKYRME_EUNSUPPORTED.  An FP32 flow with only the
- * potentials (c6 = 0) runs on the streaming FP32 kernel; with the sextic
- * term, and in FP64, it runs on the tile kernels. */
+ * observables reject it with SKYRME_EUNSUPPORTED.  An FP32 flow runs on the
+ * streaming FP32 kernel with any of the terms; an FP64 flow runs on the tile
+ * kernels. */
 typedef struct {
     int n[3];       /* sites per axis (x slowest, z fastest); each >= 5 */
     double h;       /* lattice spacing, > 0, equal on every axis */

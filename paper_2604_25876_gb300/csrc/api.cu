@@ -282,17 +282,18 @@ skyrme_status skyrme_load_field(const skyrme_lattice *lat, skyrme_state *st, voi
     return SKYRME_OK;
 }
 
-// FP32 flows without the sextic term run on the streaming kernel
+// FP32 flows run on the streaming kernel (the standard model, the Section 7.8
+// potentials and the sextic term)
 static bool fp32_streaming(const skyrme_lattice &lat)
 {
-    return lat.precision == 32 && lat.c6 == 0.0 && f32_fast_path_available(lat);
+    return lat.precision == 32 && f32_fast_path_available(lat);
 }
 
 static skyrme_status launch_iterations(const skyrme_lattice &lat, const FlowArgs &a, int nsteps,
                                        cudaStream_t s)
 {
-    // the streaming FP32 kernel implements the standard model and the
-    // Section 7.8 potentials; the sextic term runs on the tile kernels
+    // FP32: the streaming kernel (the standard model, the Section 7.8
+    // potentials, the sextic term); FP64: the tile kernels
     if (fp32_streaming(lat)) {
         CK(launch_iterations_f32_fast(lat, a, nsteps, s), "step and fix-up kernels (fp32)");
         return SKYRME_OK;
@@ -385,7 +386,7 @@ skyrme_status skyrme_step_densities(const skyrme_lattice *lat, double dt, int mo
     if (rc != SKYRME_OK) return rc;
     if (!(dt > 0.0) || !isfinite(dt) || !mode_ok(mode)) return SKYRME_EINVAL;
     if (!dens || ((uintptr_t)dens % 16)) return SKYRME_EINVAL;
-    if (!fp32_streaming(*lat)) return SKYRME_EUNSUPPORTED;
+    if (!fp32_streaming(*lat) || lat->c6 != 0.0) return SKYRME_EUNSUPPORTED;
     CKDEV(state_on_device(st));
     {
         const void *p = dens;

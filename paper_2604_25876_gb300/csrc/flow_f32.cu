@@ -86,6 +86,7 @@ struct InstDesc {
     // modified-pion, loosely and lightly bound terms
     float my2, mz2, mw2;
     float e0_scale;        // E0 = h^3 e0_scale sum(e0 slot): 2 m^2 (standard) or 1 (POT)
+    float c6;              // Section 7.8 sextic coefficient (the SEX kernels)
     float h3_hi, h3_lo;    // h^3 as an unevaluated float sum
     int mode;
     double *slab_rec;      // x-slab of a larger lattice: record out, no decision (else null)
@@ -169,13 +170,16 @@ __device__ __forceinline__ void tma_plane(void *dst, const CUtensorMap *map,
 // columns when the kernel starts and frees them when it ends, on every path
 // (tcgen05.alloc / tcgen05.dealloc).  A warp can address only the 32 lanes of
 // its quarter of a warpgroup, 32 * (warp % 4); among the warps sharing those
-// lanes, warp w owns columns [kTmemColsPerWarp * (w / 4), +kTmemColsPerWarp).
+// lanes, warp w owns columns [C * (w / 4), C * (w / 4) + C) with
+// C = tmem_cols_per_warp.
 // Thread t of a warp reads and writes its own lane (the 32x32b shapes).
-constexpr int kRecCols = 16;                    // one in-plane record (13 values used)
-constexpr int kTmemColsPerWarp = 3 * kRecCols;  // three records in flight
-template <int NW> constexpr uint32_t tmem_cols()
+// One in-plane record: 16 columns (13 values used), or 32 (25 used) in the
+// sextic kernels, which also carry d_yy, d_zz and d_yz phi to the centre.
+template <bool SEX> constexpr int rec_cols() { return SEX ? 32 : 16; }
+template <bool SEX> constexpr int tmem_cols_per_warp() { return 3 * rec_cols<SEX>(); }  // 3 in flight
+template <int NW, bool SEX = false> constexpr uint32_t tmem_cols()
 {
-    constexpr int need = ((NW + 3) / 4) * kTmemColsPerWarp;
+    constexpr int need = ((NW + 3) / 4) * tmem_cols_per_warp<SEX>();
     return need <= 32 ? 32 : need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
 }
 __device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, uint32_t ncols)
@@ -305,8 +309,10 @@ __device__ __forceinline__ DF df_shfl_xor(DF a, int o)
     return {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
 }
 
-// the five sums of a step: e2, e4, (1 - phi^0), det, |F|^2; plus max |F|^2
-constexpr int kSums = 5;
+// the six sums of a step: e2, e4, the potential (1 - phi^0 for the standard
+// model), det, |F|^2 and the sextic density e6 (zero without the sextic
+// term); plus max |F|^2
+constexpr int kSums = 6;
 
 // A thread's running sums between two flushes.  The energy and charge
 // densities are added with Knuth's error-free two-sum, two quantities per
@@ -319,8 +325,18 @@ constexpr int kSums = 5;
 struct Acc {
     float2 s24, c24;  // (e2, e4) and their compensation
     float2 s0b, c0b;  // (e0, det) and their compensation
+    float s6, c6;     // e6 and its compensation (the sextic kernels)
     float f2, fmax2;
 };
+
+// the same for one quantity
+__device__ __forceinline__ void two_sum_acc1(float &s, float &c, float x)
+{
+    const float t = __fadd_rn(s, x);
+    const float bb = __fsub_rn(t, s);
+    c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(x, bb)));
+    s = t;
+}
 
 // s + x with the rounding error of the addition added to c (two quantities)
 __device__ __forceinline__ void two_sum_acc(float2 &s, float2 &c, float2 x)
@@ -343,6 +359,7 @@ __device__ __forceinline__ void flush(DF *acc, float *amax, int nthreads, Acc &a
     acc[2 * nthreads] = df_add(df_add(acc[2 * nthreads], a.s0b.x), a.c0b.x);
     acc[3 * nthreads] = df_add(df_add(acc[3 * nthreads], a.s0b.y), a.c0b.y);
     acc[4 * nthreads] = df_add(acc[4 * nthreads], a.f2);
+    acc[5 * nthreads] = df_add(df_add(acc[5 * nthreads], a.s6), a.c6);
     *amax = fmaxf(*amax, a.fmax2);
     a = Acc{};
 }
@@ -465,10 +482,10 @@ template <int TY, int TZ> struct __align__(128) StepSmem {
 // than the SM's 228 KiB of shared memory, and so never becomes resident
 // (tcgen05.alloc in that CTA would otherwise wait for a co-resident CTA to
 // free its columns).
-template <int TY, int TZ> constexpr size_t step_smem_bytes()
+template <int TY, int TZ, bool SEX = false> constexpr size_t step_smem_bytes()
 {
     constexpr size_t per_sm = 228 * 1024;
-    constexpr int max_ctas = 512 / tmem_cols<TY * TZ / 32>();
+    constexpr int max_ctas = 512 / tmem_cols<TY * TZ / 32, SEX>();
     constexpr size_t floor_bytes = per_sm / (max_ctas + 1) + 1;  // max_ctas + 1 never fit
     return sizeof(StepSmem<TY, TZ>) > floor_bytes ? sizeof(StepSmem<TY, TZ>) : floor_bytes;
 }
@@ -514,7 +531,7 @@ __device__ __forceinline__ void arrive_plane(const float4 (*P)[TZ + 4], float4 (
 
 // In-plane values of a plane for its own centre two planes later: d_yz, the
 // y/z parts of a_ij, of the Laplacian, of d_ij phi a_ij and of g_y, g_z.
-template <int TY, int TZ>
+template <int TY, int TZ, bool SEX = false>
 __device__ __forceinline__ void plane_record(const float4 (*DY)[TZ + 4], const InstDesc &D, int ty,
                                              int tz, const PlaneVals &rv, const P4 &dyy,
                                              const P4 &dzz, uint32_t trec)
@@ -532,6 +549,11 @@ __device__ __forceinline__ void plane_record(const float4 (*DY)[TZ + 4], const I
                          gyv, gzv, ayy, azz, ayz, 0.f, 0.f, 0.f};
     (void)THREADS;
     tmem_st16(trec, r);
+    if constexpr (SEX) {
+        const float r2[16] = {dyy.a.x, dyy.a.y, dyy.b.x, dyy.b.y, dzz.a.x, dzz.a.y, dzz.b.x, dzz.b.y,
+                              dyz.a.x, dyz.a.y, dyz.b.x, dyz.b.y, 0.f, 0.f, 0.f, 0.f};
+        tmem_st16(trec + 16, r2);
+    }
 }
 
 // One centre site: x-derivatives from the register ring (M2, M1, C, Q1, Q2 in
@@ -539,7 +561,7 @@ __device__ __forceinline__ void plane_record(const float4 (*DY)[TZ + 4], const I
 // Euler-Lagrange force of Eq. (3.3) projected on the tangent space, the
 // symplectic update with renormalisation, and the energy, charge and force
 // densities into a32 (valid sites only).
-template <int TY, int TZ, bool POT = false, bool DUMP = false>
+template <int TY, int TZ, bool POT = false, bool DUMP = false, bool SEX = false>
 __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &M2,
                                             const PlaneVals &M1, const PlaneVals &C,
                                             const PlaneVals &Q1, const PlaneVals &Q2, float2 xc1,
@@ -555,6 +577,7 @@ __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &
     float rv[16];
     tmem_wait_st();  // this thread's earlier record stores have landed
     tmem_ld16(trec, rv);
+
     const P4 lin = {make_float2(rv[0], rv[1]), make_float2(rv[2], rv[3])};
     const P4 qin = {make_float2(rv[4], rv[5]), make_float2(rv[6], rv[7])};
     const float Cgy = rv[8], Cgz = rv[9], Cayy = rv[10], Cazz = rv[11];
@@ -592,6 +615,40 @@ __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &
         u = one_minus_phi0();
         br.a.x += fmaf(D.my2, ph.a.x, u * fmaf(D.mw2 * u, u, D.mz2));
     }
+    float e6 = 0.f;
+    if constexpr (SEX) {
+        // Section 7.8 sextic term c6 D^2, D = det[phi, d_x phi, d_y phi, d_z phi]
+        // (= c6 4 pi^4 (B0)^2): its Euler-Lagrange gradient is
+        // 2 c6 [4 D P - sum_i (d_i D) Q_i] with P = dD/dphi, Q_i = dD/d(d_i phi)
+        // and d_i D = sum_j Q_j . d_i d_j phi; in the brace (G = -2 brace) it
+        // enters as -c6 [...].
+        float rs[16];  // d_yy, d_zz, d_yz phi of the centre plane
+        tmem_ld16(trec + 16, rs);
+        const float ph4[4] = {ph.a.x, ph.a.y, ph.b.x, ph.b.y};
+        const float u4[4] = {dx.a.x, dx.a.y, dx.b.x, dx.b.y};
+        const float v4[4] = {dyc.a.x, dyc.a.y, dyc.b.x, dyc.b.y};
+        const float w4[4] = {dzc.a.x, dzc.a.y, dzc.b.x, dzc.b.y};
+        float P[4], Qx[4], Qy[4], Qz[4];
+        cross3<float>(u4, v4, w4, P);
+        cross3<float>(ph4, v4, w4, Qx);
+        cross3<float>(ph4, u4, w4, Qy);
+        cross3<float>(ph4, u4, v4, Qz);
+        const float Dd = ph4[0] * P[0] + ph4[1] * P[1] + ph4[2] * P[2] + ph4[3] * P[3];
+        const P4 qx = {make_float2(-Qx[0], -Qx[1]), make_float2(-Qx[2], -Qx[3])};
+        const P4 qy = {make_float2(Qy[0], Qy[1]), make_float2(Qy[2], Qy[3])};
+        const P4 qz = {make_float2(-Qz[0], -Qz[1]), make_float2(-Qz[2], -Qz[3])};
+        const P4 dyy = {make_float2(rs[0], rs[1]), make_float2(rs[2], rs[3])};
+        const P4 dzz = {make_float2(rs[4], rs[5]), make_float2(rs[6], rs[7])};
+        const P4 dyz = {make_float2(rs[8], rs[9]), make_float2(rs[10], rs[11])};
+        const float dDx = dot(qx, dxx) + dot(qy, dxy) + dot(qz, dxz);
+        const float dDy = dot(qx, dxy) + dot(qy, dyy) + dot(qz, dyz);
+        const float dDz = dot(qx, dxz) + dot(qy, dyz) + dot(qz, dzz);
+        const P4 pp = {make_float2(P[0], P[1]), make_float2(P[2], P[3])};
+        const P4 sx = fma(bc(-dDz), qz, fma(bc(-dDy), qy, fma(bc(-dDx), qx, mul(bc(4.f * Dd), pp))));
+        br = fma(bc(-D.c6), sx, br);
+        e6 = D.c6 * Dd * Dd;
+    }
+
     // F = -G + (G.phi) phi = 2 (br - (br.phi) phi)
     const float bp = dot(br, ph);
     const P4 Fh = fma(bc(-bp), ph, br);
@@ -630,6 +687,7 @@ __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &
             e0v = one_minus_phi0();
         }
         if constexpr (DUMP) __stcs(D.dump + si, make_float4(tra, e4, e0v, det));
+        if constexpr (SEX) two_sum_acc1(a32.s6, a32.c6, e6);
         two_sum_acc(a32.s24, a32.c24, make_float2(tra, e4));
         two_sum_acc(a32.s0b, a32.c0b, make_float2(e0v, det));
         a32.f2 += f2;
@@ -660,6 +718,7 @@ __device__ __forceinline__ void write_record(const InstDesc &D, int slot, const 
     recp[0] = make_float4(tot[0].hi, tot[0].lo, tot[1].hi, tot[1].lo);
     recp[1] = make_float4(tot[2].hi, tot[2].lo, tot[3].hi, tot[3].lo);
     recp[2] = make_float4(tot[4].hi, tot[4].lo, tmax, 0.f);
+    recp[3] = make_float4(tot[5].hi, tot[5].lo, 0.f, 0.f);
 }
 
 // End of a step for one lattice, run by every thread of the last CTA to
@@ -692,12 +751,13 @@ __device__ __forceinline__ void finish_lattice(const InstDesc &D, Ctrl *c, int c
     float amax = 0.f;
     for (int i = tid; i < D.cta_count; i += NW * 32) {
         const float4 *r = reinterpret_cast<const float4 *>(D.parts + (size_t)i * kPartialDoubles);
-        const float4 a = __ldcg(r), b = __ldcg(r + 1), e = __ldcg(r + 2);
+        const float4 a = __ldcg(r), b = __ldcg(r + 1), e = __ldcg(r + 2), f = __ldcg(r + 3);
         v[0] = df_add(v[0], DF{a.x, a.y});
         v[1] = df_add(v[1], DF{a.z, a.w});
         v[2] = df_add(v[2], DF{b.x, b.y});
         v[3] = df_add(v[3], DF{b.z, b.w});
         v[4] = df_add(v[4], DF{e.x, e.y});
+        v[5] = df_add(v[5], DF{f.x, f.y});
         amax = fmaxf(amax, e.z);
     }
     DF t[kSums];
@@ -734,16 +794,19 @@ __device__ __forceinline__ void finish_lattice(const InstDesc &D, Ctrl *c, int c
         r[4] = df_value(t[4]);
         r[5] = (double)tmax;
         r[6] = (double)(D.n0 - 4) * (double)(D.n1 - 4) * (double)(D.n2 - 4);
-        r[7] = 0.0;
+        r[7] = df_value(t[5]);
         c->done = 0;
         return;
     }
     const DF h3 = {D.h3_hi, D.h3_lo};
     const DF E2 = df_mul(h3, t[0]), E4 = df_mul(h3, t[1]);
     const DF E0 = df_mul(h3, df_mul(DF{D.e0_scale, 0.f}, t[2]));  // 2 m^2 sum(1 - phi^0), or the potentials' sum
-    const DF E = df_add(df_add(E2, E4), E0);
+    const DF E6 = df_mul(h3, t[5]);  // the sextic term (zero without it)
+    const DF E = df_add(df_add(df_add(E2, E4), E0), E6);
     const DF B = df_mul(h3, df_mul(bfac, t[3]));
-    const DF V = df_add(df_add(df_neg(E2), E4), df_mul(DF{-3.f, 0.f}, E0));
+    // Derrick scaling: -E2 + E4 - 3 E0 + 3 E6
+    const DF V = df_add(df_add(df_add(df_neg(E2), E4), df_mul(DF{-3.f, 0.f}, E0)),
+                        df_mul(DF{3.f, 0.f}, E6));
     const double Ed = df_value(E);
     const int actual = (mode == MODE_ARRESTED && Ed > E_prev) ? 1 : 0;
     const int fix = (actual == pred) ? 0 : (actual ? -1 : +1);
@@ -771,6 +834,7 @@ __device__ __forceinline__ void finish_lattice(const InstDesc &D, Ctrl *c, int c
     c->last[5] = df_value(V);
     c->last[6] = sqrt((double)tmax);
     c->last[7] = sqrt(df_value(t[4]) / (double)nsites);
+    c->e6_last = df_value(E6);
     if (!(isfinite(Ed) && isfinite(B.hi) && isfinite(t[4].hi))) c->status = DEV_NONFINITE;
     c->done = 0;
     // the step count goes last, after a fence: CTAs that correct their own
@@ -845,7 +909,7 @@ __device__ __forceinline__ void correct_own_sites(const InstDesc &D, long long u
 // lattices come from `table` (ninst entries, ordered by unit_start); otherwise
 // from `one`.  dry != 0 (autotuning): outputs land in the inactive buffers and
 // the control blocks are left as they were.
-template <int TY, int TZ, bool BATCHED, bool POT = false, bool DUMP = false>
+template <int TY, int TZ, bool BATCHED, bool POT = false, bool DUMP = false, bool SEX = false>
 __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
     k_step_f32(const __grid_constant__ InstDesc one, const __grid_constant__ CtaSplit split,
                const InstDesc *__restrict__ table, int ninst, long long total_units, int dry)
@@ -867,13 +931,14 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
         mbar_fence_init();
         sm.flag = 0;
     }
-    constexpr uint32_t TCOLS = tmem_cols<THREADS / 32>();
+    constexpr uint32_t TCOLS = tmem_cols<THREADS / 32, SEX>();
+    constexpr int RECC = rec_cols<SEX>();
     if (tid < 32) tmem_alloc(&sm.tmem, TCOLS);
     tmem_fence_before();
     __syncthreads();
     tmem_fence_after();
     const uint32_t twarp = sm.tmem + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) +
-                           (uint32_t)(kTmemColsPerWarp * ((tid >> 5) >> 2));
+                           (uint32_t)(tmem_cols_per_warp<SEX>() * ((tid >> 5) >> 2));
 
     const bool listed = !BATCHED && split.n > 0;
     const long long u0 = listed ? split.start[blockIdx.x] : total_units * blockIdx.x / gridDim.x;
@@ -955,9 +1020,9 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
                     const int x = pp - 2;
                     __syncwarp();
                     if (x >= xs)
-                        centre_site<TY, TZ, POT, DUMP>(D, ring[(k + 1) % 5], ring[(k + 2) % 5], ring[(k + 3) % 5],
+                        centre_site<TY, TZ, POT, DUMP, SEX>(D, ring[(k + 1) % 5], ring[(k + 2) % 5], ring[(k + 3) % 5],
                                             ring[(k + 4) % 5], ring[k], D.c1, D.c2,
-                                            twarp + kRecCols * g3n,
+                                            twarp + RECC * g3n,
                                             &sm.vpl[s][ty][tz], use_v,
                                             valid, phiout, vout, (size_t)x * plane_stride + col_off, a32);
                     // this warp is done with slot s; the last warp to leave it streams
@@ -978,7 +1043,7 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
                         failed = true;
                         break;
                     }
-                    plane_record<TY, TZ>(DY, D, ty, tz, ring[k], dyy, dzz, twarp + kRecCols * g3);
+                    plane_record<TY, TZ, SEX>(DY, D, ty, tz, ring[k], dyy, dzz, twarp + RECC * g3);
                     ++g;
                     g3 = g3n;
                 }
@@ -1217,9 +1282,10 @@ constexpr int kNumTiles = 5;
 // faster than two 8 x 32 CTAs per SM on 128^3, 256^3 and 512^3)
 constexpr int kSingleTile = 4;
 
-template <int TY, int TZ, bool B, bool POT = false, bool DUMP = false> static void *kernel_ptr()
+template <int TY, int TZ, bool B, bool POT = false, bool DUMP = false, bool SEX = false>
+static void *kernel_ptr()
 {
-    return reinterpret_cast<void *>(&k_step_f32<TY, TZ, B, POT, DUMP>);
+    return reinterpret_cast<void *>(&k_step_f32<TY, TZ, B, POT, DUMP, SEX>);
 }
 
 template <int TY, int TZ, bool B>
@@ -1326,7 +1392,8 @@ static bool fill_desc(InstDesc &d, const skyrme_lattice &lat, const skyrme_state
     d.my2 = (float)(lat.m_y * lat.m_y);
     d.mz2 = (float)(lat.m_z * lat.m_z);
     d.mw2 = (float)(lat.m_w * lat.m_w);
-    d.e0_scale = lattice_potentials(lat) ? 1.f : 2.f * d.m2;
+    d.e0_scale = lattice_potentials(lat) || lat.c6 != 0.0 ? 1.f : 2.f * d.m2;
+    d.c6 = (float)lat.c6;
     d.dt = make_float2((float)dt, (float)dt);
     d.dt2 = make_float2(2.f * (float)dt, 2.f * (float)dt);
     const double h3 = lat.h * lat.h * lat.h;
@@ -1504,20 +1571,27 @@ cudaError_t launch_iterations_f32_fast(const skyrme_lattice &lat, const FlowArgs
     // fix-up come after the decision over all slabs
     const bool fused = a.mode == SKYRME_ARRESTED && !a.slab_rec;
     ds[0].fuse_fix = fused ? 1 : 0;
-    const bool pot = lattice_potentials(lat);
+    // the instantiation: the standard model, the Section 7.8 potentials, the
+    // sextic term (with any potentials), each also with the density dump
+    // (not for the sextic term)
+    const bool sex = lat.c6 != 0.0;
+    const bool pot = sex || lattice_potentials(lat);
     const bool dump = a.dump != nullptr;
-    void *kern = pot ? (dump ? kernel_ptr<16, 32, false, true, true>() : kernel_ptr<16, 32, false, true>())
+    if (sex && dump) return cudaErrorInvalidValue;
+    void *kern = sex ? kernel_ptr<16, 32, false, true, false, true>()
+               : pot ? (dump ? kernel_ptr<16, 32, false, true, true>() : kernel_ptr<16, 32, false, true>())
                      : (dump ? kernel_ptr<16, 32, false, false, true>() : kernel_ptr<16, 32, false>());
+    const size_t smem = sex ? step_smem_bytes<16, 32, true>() : step_smem_bytes<16, 32>();
     {
         static std::mutex mu;
-        static bool done[4][64] = {{false}};
-        const int which = (pot ? 2 : 0) + (dump ? 1 : 0);
+        static bool done[5][64] = {{false}};
+        const int which = sex ? 4 : (pot ? 2 : 0) + (dump ? 1 : 0);
         int dev = 0;
         cudaGetDevice(&dev);
         std::lock_guard<std::mutex> lock(mu);
         if (dev < 64 && !done[which][dev]) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)step_smem_bytes<16, 32>());
+                                                 (int)smem);
             if (e != cudaSuccess) return e;
             done[which][dev] = true;
         }
@@ -1533,7 +1607,7 @@ cudaError_t launch_iterations_f32_fast(const skyrme_lattice &lat, const FlowArgs
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(16 * 32);
-    cfg.dynamicSmemBytes = step_smem_bytes<16, 32>();
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cfg.attrs = &attr;
     cfg.numAttrs = 1;

@@ -148,6 +148,32 @@ def test_fp32_potentials_flow_on_the_streaming_kernel_tracks_the_oracle(pot):
     assert rep["arrests"] == sum(r["arrested"] for r in oreps)
 
 
+def test_fp32_sextic_flow_on_the_streaming_kernel_tracks_the_oracle():
+    """With the sextic term the FP32 flow runs on the streaming kernel's
+    sextic variant.  Its first energy and sextic energy equal the tile
+    kernel's evaluation of the same field, and 50 arrested iterations follow
+    the FP64 oracle: field within 1e-4, E and E6 within 1e-5, the same
+    arrests."""
+    n, h = (38, 41, 44), 0.2  # ragged against the 16 x 32 column tile
+    phi = oracle.seed_rational_map(n, h, 4, 2.0)
+    for kw in (dict(m_y=0.0, m_z=0.0, m_w=0.0), dict()):
+        ost = oracle.new_state(phi)
+        oreps = oracle.flow(ost, h, model(**kw), 0.05 * h, 50, reports=True)
+        lat, st = on_gpu(phi, h, 32, **kw)
+        e_tile = sk.energy(lat, st)
+        e6_tile = sk.sextic_energy(lat, st)
+        r1 = sk.flow_step(lat, 0.05 * h, 1, sk.ARRESTED, st)
+        assert r1["E"] == pytest.approx(e_tile["E"], rel=2e-6)
+        assert r1["E6"] == pytest.approx(e6_tile, rel=2e-6)
+        assert r1["virial"] == pytest.approx(e_tile["virial"], rel=2e-5, abs=2e-6 * r1["E"])
+        rep = sk.flow_step(lat, 0.05 * h, 49, sk.ARRESTED, st)
+        assert rep["status"] == 0 and rep["steps"] == 50
+        assert np.max(np.abs(st.field().double().cpu().numpy() - ost.phi)) < 1e-4
+        assert rep["E"] == pytest.approx(oreps[-1]["E"], rel=1e-5)
+        assert rep["E6"] == pytest.approx(oreps[-1]["E6"], rel=1e-5)
+        assert rep["arrests"] == sum(r["arrested"] for r in oreps)
+
+
 def test_standard_model_report_has_no_sextic_part_and_vacuum_stays_fixed():
     for prec in (32, 64):
         lat = sk.Lattice((20, 21, 22), 0.2, 1.0, prec)

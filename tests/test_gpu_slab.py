@@ -91,9 +91,9 @@ def test_fp64_slab_flow_matches_the_oracle():
     assert reps[0]["arrests"] == sum(r["arrested"] for r in oreps)
 
 
-def test_slabs_of_an_extended_model_on_the_tile_kernel():
-    """The sextic term runs on the tile kernel in both precisions; its slab
-    records carry the sextic sum."""
+def test_slabs_of_an_extended_model():
+    """A potential and the sextic term (the streaming kernel's sextic
+    variant in FP32): the slab records carry the sextic sum."""
     n, h = (26, 20, 22), H
     lat = sk.Lattice(n, h, 1.0, 32, m_w=0.5, c6=1.0)
     phi0 = seed(n, h)
