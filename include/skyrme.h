@@ -59,8 +59,9 @@ typedef enum { SKYRME_NEWTON = 0, SKYRME_ARRESTED = 1, SKYRME_GRADIENT = 2 } sky
  *   e6 = c6 4 pi^4 (B0)^2  (the BPS sextic term, B0 of Eq. "B0_components").
  * All five coefficients are finite and >= 0; m_y = m_z = m_w = c6 = 0 is the
  * standard model.  A lattice with any of the four extension coefficients
- * non-zero is an "extended" lattice: the batched flow and the Section 5
- * observables reject it with SKYRME_EUNSUPPORTED.  An FP32 flow runs on the
+ * non-zero is an "extended" lattice: the Section 5 observables reject it with
+ * SKYRME_EUNSUPPORTED, and so does the batched flow when c6 != 0 (batches
+ * take the standard model and the potentials).  An FP32 flow runs on the
  * streaming FP32 kernel with any of the terms; an FP64 flow runs on the tile
  * kernels. */
 typedef struct {
@@ -259,7 +260,9 @@ skyrme_status skyrme_graph_create_until(const skyrme_lattice *lat, double dt, in
  * one fix-up check launch), and each lattice's energy sums and arrest
  * decision close as soon as the CTAs that touched it are done.  Each lattice
  * keeps its own skyrme_state (initialise it with skyrme_init_field or
- * skyrme_load_field; read its results with skyrme_read_report).
+ * skyrme_load_field; read its results with skyrme_read_report).  Lattices
+ * may differ in size, spacing, pion mass and Section 7.8 potentials; the
+ * sextic term is not taken (SKYRME_EUNSUPPORTED).
  *   skyrme_batch_scratch_bytes: size of the caller-owned batch scratch
  *     (lattice table and per-CTA partial records), 256-byte aligned.
  *   skyrme_batch_create: validates the states (precision 32 only), encodes

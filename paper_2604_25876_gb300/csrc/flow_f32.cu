@@ -1288,7 +1288,7 @@ static void *kernel_ptr()
     return reinterpret_cast<void *>(&k_step_f32<TY, TZ, B, POT, DUMP, SEX>);
 }
 
-template <int TY, int TZ, bool B>
+template <int TY, int TZ, bool B, bool POT = false>
 static cudaError_t launch_shape(const InstDesc &one, const CtaSplit &split, const InstDesc *table,
                                 int ninst, long long units, int grid, int dry, cudaStream_t s)
 {
@@ -1299,29 +1299,29 @@ static cudaError_t launch_shape(const InstDesc &one, const CtaSplit &split, cons
     {
         std::lock_guard<std::mutex> lock(mu);
         if (dev < 64 && !done[dev]) {
-            cudaError_t e = cudaFuncSetAttribute(k_step_f32<TY, TZ, B>,
+            cudaError_t e = cudaFuncSetAttribute(k_step_f32<TY, TZ, B, POT>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)step_smem_bytes<TY, TZ>());
             if (e != cudaSuccess) return e;
             done[dev] = true;
         }
     }
-    k_step_f32<TY, TZ, B><<<(unsigned)grid, TY * TZ, step_smem_bytes<TY, TZ>(), s>>>(
+    k_step_f32<TY, TZ, B, POT><<<(unsigned)grid, TY * TZ, step_smem_bytes<TY, TZ>(), s>>>(
         one, split, table, ninst, units, dry);
     return cudaGetLastError();
 }
 
-template <bool B>
+template <bool B, bool POT = false>
 static cudaError_t launch_tile(int tile, const InstDesc &one, const CtaSplit &split,
                                const InstDesc *table, int ninst, long long units, int grid, int dry,
                                cudaStream_t s)
 {
     switch (tile) {
-    case 0: return launch_shape<8, 32, B>(one, split, table, ninst, units, grid, dry, s);
-    case 1: return launch_shape<4, 32, B>(one, split, table, ninst, units, grid, dry, s);
-    case 2: return launch_shape<16, 16, B>(one, split, table, ninst, units, grid, dry, s);
-    case 4: return launch_shape<16, 32, B>(one, split, table, ninst, units, grid, dry, s);
-    default: return launch_shape<8, 16, B>(one, split, table, ninst, units, grid, dry, s);
+    case 0: return launch_shape<8, 32, B, POT>(one, split, table, ninst, units, grid, dry, s);
+    case 1: return launch_shape<4, 32, B, POT>(one, split, table, ninst, units, grid, dry, s);
+    case 2: return launch_shape<16, 16, B, POT>(one, split, table, ninst, units, grid, dry, s);
+    case 4: return launch_shape<16, 32, B, POT>(one, split, table, ninst, units, grid, dry, s);
+    default: return launch_shape<8, 16, B, POT>(one, split, table, ninst, units, grid, dry, s);
     }
 }
 
@@ -1362,8 +1362,10 @@ static int blocks_per_sm(int tile, bool batched)
 
 
 // Lattice description for a tile shape; the work partition is filled later.
+// pot_sums: the lattice runs in a potentials instantiation (its e0 slot
+// then holds the whole potential density, whatever the lattice's model).
 static bool fill_desc(InstDesc &d, const skyrme_lattice &lat, const skyrme_state &st, Ctrl *ctrl,
-                      double dt, int mode, int tile)
+                      double dt, int mode, int tile, bool pot_sums = false)
 {
     const int ty = kTiles[tile].ty, tz = kTiles[tile].tz;
     memset(&d, 0, sizeof(d));
@@ -1392,7 +1394,7 @@ static bool fill_desc(InstDesc &d, const skyrme_lattice &lat, const skyrme_state
     d.my2 = (float)(lat.m_y * lat.m_y);
     d.mz2 = (float)(lat.m_z * lat.m_z);
     d.mw2 = (float)(lat.m_w * lat.m_w);
-    d.e0_scale = lattice_potentials(lat) || lat.c6 != 0.0 ? 1.f : 2.f * d.m2;
+    d.e0_scale = pot_sums || lattice_potentials(lat) || lat.c6 != 0.0 ? 1.f : 2.f * d.m2;
     d.c6 = (float)lat.c6;
     d.dt = make_float2((float)dt, (float)dt);
     d.dt2 = make_float2(2.f * (float)dt, 2.f * (float)dt);
@@ -1653,6 +1655,7 @@ struct skyrme_batch {
     InstDesc *d_table = nullptr;  // in the caller's batch scratch
     double *d_parts = nullptr;
     int fixup_blocks = 1;
+    bool pot = false;  // some lattice has a Section 7.8 potential: the POT kernels
 };
 
 static size_t table_bytes(int ninst) { return ((size_t)ninst * sizeof(InstDesc) + 255) & ~(size_t)255; }
@@ -1667,7 +1670,7 @@ static skyrme_status upload_table(skyrme_batch *b, int tile)
     std::vector<InstDesc> ds(b->ninst);
     for (int i = 0; i < b->ninst; ++i) {
         Ctrl *ctrl = static_cast<Ctrl *>(b->states[i].scratch);
-        if (!fill_desc(ds[i], b->lats[i], b->states[i], ctrl, b->dt[i], b->mode, tile))
+        if (!fill_desc(ds[i], b->lats[i], b->states[i], ctrl, b->dt[i], b->mode, tile, b->pot))
             return SKYRME_EINVAL;
     }
     const long long units = total_units(ds);
@@ -1687,10 +1690,12 @@ static skyrme_status batch_launch(skyrme_batch *b, int nsteps, int dry, cudaStre
     InstDesc dummy;
     memset(&dummy, 0, sizeof(dummy));
     for (int k = 0; k < nsteps; ++k) {
-        if (launch_tile<true>(b->tile, dummy, kEvenSplit, b->d_table, b->ninst, b->units, b->grid,
-                              dry, s) !=
-            cudaSuccess)
-            return SKYRME_ECUDA;
+        const cudaError_t e =
+            b->pot ? launch_tile<true, true>(b->tile, dummy, kEvenSplit, b->d_table, b->ninst,
+                                             b->units, b->grid, dry, s)
+                   : launch_tile<true>(b->tile, dummy, kEvenSplit, b->d_table, b->ninst, b->units,
+                                       b->grid, dry, s);
+        if (e != cudaSuccess) return SKYRME_ECUDA;
         if (!dry && b->mode == MODE_ARRESTED) {
             k_fixup_batch<<<(unsigned)b->fixup_blocks, 512, 0, s>>>(b->d_table, b->ninst);
             if (cudaGetLastError() != cudaSuccess) return SKYRME_ECUDA;
@@ -1727,10 +1732,13 @@ skyrme_status skyrme_batch_create(int ninst, const skyrme_lattice *lats, skyrme_
         if (!state_ok_for_batch(&lats[i], &states[i])) return SKYRME_EINVAL;
         if (!(dt[i] > 0.0)) return SKYRME_EINVAL;
     }
-    // the streaming kernel implements the standard model only (Section 7.8
-    // extensions run on the single-lattice tile kernels)
-    for (int i = 0; i < ninst; ++i)
-        if (lattice_extended(lats[i])) return SKYRME_EUNSUPPORTED;
+    // batches run the standard model and the Section 7.8 potentials; the
+    // sextic term runs on single lattices
+    bool pot = false;
+    for (int i = 0; i < ninst; ++i) {
+        if (lats[i].c6 != 0.0) return SKYRME_EUNSUPPORTED;
+        pot = pot || lattice_potentials(lats[i]);
+    }
     if (!f32_fast_path_available(lats[0])) return SKYRME_EUNSUPPORTED;
     {
         const void *p = scratch;
@@ -1747,6 +1755,7 @@ skyrme_status skyrme_batch_create(int ninst, const skyrme_lattice *lats, skyrme_
     b->ninst = ninst;
     b->mode = mode;
     b->fixup_blocks = sm_count() * 2;
+    b->pot = pot;
     b->lats.assign(lats, lats + ninst);
     b->states.assign(states, states + ninst);
     b->dt.assign(dt, dt + ninst);

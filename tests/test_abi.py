@@ -184,7 +184,7 @@ def test_extension_coefficients_are_validated_and_gated_without_cuda():
     # Section 5 observables are those of the standard model
     assert lib.skyrme_observables(ctypes.byref(c), ctypes.byref(st),
                                   ctypes.byref(sk.c_observables()), None) == 6
-    # the batched streaming kernel implements the standard model only
+    # batches take the standard model and the potentials, not the sextic term
     lats = (sk.c_lattice * 1)(c)
     sts = (sk.c_state * 1)(st)
     dts = (ctypes.c_double * 1)(0.01)

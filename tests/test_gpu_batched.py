@@ -52,6 +52,46 @@ def test_batch_matches_lattices_flowed_alone():
     b.close()
 
 
+def test_batch_with_potentials_matches_lattices_flowed_alone():
+    """Lattices with Section 7.8 potentials (and standard ones) in one batch:
+    the batch runs the potentials instantiation for all of them, and each
+    lattice follows its solo flow (which runs the single-lattice potentials
+    or standard kernel) to FP32 rounding."""
+    pots = [dict(), dict(m_w=1.0), dict(m_y=0.5, m_z=0.4), dict(), dict(m_w=0.7)]
+
+    def states():
+        lats, sts = [], []
+        for i, (n, kw) in enumerate(zip(SHAPES, pots)):
+            lat = sk.Lattice(n, 0.2, 1.0, 32, **kw)
+            st = sk.State(lat, DEV)
+            sk.load_field(lat, st, oracle.seed_rational_map(n, 0.2, 1 if i % 2 else 4, 1.2))
+            lats.append(lat)
+            sts.append(st)
+        return lats, sts
+
+    lats, sts = states()
+    solo_lats, solo = states()
+    b = sk.Batch(lats, sts, [0.01] * len(lats))
+    b.step(30)
+    torch.cuda.synchronize()
+    for lat, st, ref in zip(solo_lats, solo, sts):
+        sk.flow_step(lat, 0.01, 30, sk.ARRESTED, st)
+        r0, r1 = sk.read_report(lat, st), sk.read_report(lat, ref)
+        assert r1["steps"] == 30 and r1["status"] == 0
+        assert r1["E"] == pytest.approx(r0["E"], rel=1e-7)
+        assert r1["E0"] == pytest.approx(r0["E0"], rel=1e-6)
+        assert r1["arrests"] == r0["arrests"]
+        np.testing.assert_allclose(ref.field().cpu().numpy(), st.field().cpu().numpy(),
+                                   rtol=0, atol=2e-6)
+    b.close()
+    # the sextic term is not taken by batches
+    lat = sk.Lattice(SHAPES[0], 0.2, 1.0, 32, c6=0.5)
+    st = sk.State(lat, DEV)
+    with pytest.raises(sk.SkyrmeError) as e:
+        sk.Batch([lat], [st], [0.01])
+    assert e.value.status == 6
+
+
 @pytest.mark.parametrize("tile", [0, 4])
 def test_batch_tracks_the_oracle_trajectories(tile):
     """Every lattice of a batch of uneven sizes against the FP64 oracle's
