@@ -24,9 +24,18 @@
 
 namespace skyrme {
 
-constexpr int GTX = 2, GTY = 4, GTZ = 32;  // interior sites per CTA
-constexpr int GSX = GTX + 4, GSY = GTY + 4, GSZ = GTZ + 4;
-constexpr int GTHREADS = GTX * GTY * GTZ;
+// Tile geometry: TX x TY x TZ interior sites per CTA, one thread per site,
+// 256 threads either way.  TZ = 32 (2 x 4 x 32) in general; TZ = 16
+// (2 x 8 x 16) for lattices whose z-interior pads less to 16 than to 32
+// (a 44-site interior: 8% idle lanes instead of 31%).  S* are the haloed
+// extents, DXN / DYN / TILEN the entries of d_x phi, d_y phi and the field
+// tile in shared memory.
+template <int TZ_> struct TileG {
+    static constexpr int TX = 2, TZ = TZ_, TY = 256 / (TX * TZ_);
+    static constexpr int SX = TX + 4, SY = TY + 4, SZ = TZ + 4;
+    static constexpr int DXN = TX * SY * SZ, DYN = TX * TY * SZ, TILEN = SX * SY * SZ;
+};
+constexpr int GTHREADS = 256;
 
 template <typename T> struct FlowParams {
     vec4_t<T> *phi[2];
@@ -55,13 +64,14 @@ __device__ __forceinline__ size_t site_index(int x, int y, int z, int n1, int n2
 
 // Stage the field tile with its halo; entries outside the lattice are left
 // unwritten (only sites outside the interior would read them).
-template <typename T>
+template <int TZ, typename T>
 __device__ __forceinline__ void load_tile(vec4_t<T> *tile, const vec4_t<T> *phi, int x0, int y0,
                                           int z0, int n0, int n1, int n2)
 {
+    using G = TileG<TZ>;
     const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-    for (int i = tid; i < GSX * GSY * GSZ; i += GTHREADS) {
-        const int lz = i % GSZ, ly = (i / GSZ) % GSY, lx = i / (GSZ * GSY);
+    for (int i = tid; i < G::TILEN; i += GTHREADS) {
+        const int lz = i % G::SZ, ly = (i / G::SZ) % G::SY, lx = i / (G::SZ * G::SY);
         const int x = x0 - 2 + lx, y = y0 - 2 + ly, z = z0 - 2 + lz;
         if (x < n0 && y < n1 && z < n2) tile[i] = load4<T>(phi + site_index(x, y, z, n1, n2));
     }
@@ -70,12 +80,14 @@ __device__ __forceinline__ void load_tile(vec4_t<T> *tile, const vec4_t<T> *phi,
 // The same staging with asynchronous copies (cp.async, 16 bytes per site of
 // an FP32 field), committed as one group: the copies of the next tile fly
 // while the current one is computed.
+template <int TZ>
 __device__ __forceinline__ void load_tile_async(float4 *tile, const float4 *phi, int x0, int y0,
                                                 int z0, int n0, int n1, int n2)
 {
+    using G = TileG<TZ>;
     const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-    for (int i = tid; i < GSX * GSY * GSZ; i += GTHREADS) {
-        const int lz = i % GSZ, ly = (i / GSZ) % GSY, lx = i / (GSZ * GSY);
+    for (int i = tid; i < G::TILEN; i += GTHREADS) {
+        const int lz = i % G::SZ, ly = (i / G::SZ) % G::SY, lx = i / (G::SZ * G::SY);
         const int x = x0 - 2 + lx, y = y0 - 2 + ly, z = z0 - 2 + lz;
         if (x < n0 && y < n1 && z < n2) {
             const unsigned dst = static_cast<unsigned>(__cvta_generic_to_shared(tile + i));
@@ -116,48 +128,48 @@ __device__ __forceinline__ vec4_t<T> sd1v(const vec4_t<T> &m2v, const vec4_t<T> 
 // d_xy = d_y(d_x phi), d_xz = d_z(d_x phi), d_yz = d_z(d_y phi)),
 // which costs a quarter of the FP64 operations of the 16-tap sums.
 // FP32 kernels keep two field tiles, the next one arriving by cp.async.
-constexpr int GDX = GTX * GSY * GSZ;  // entries of d_x phi
-constexpr int GDY = GTX * GTY * GSZ;  // entries of d_y phi
-constexpr int GTILE = GSX * GSY * GSZ;  // entries of one haloed field tile
 template <typename T> constexpr int kTileBufs = sizeof(T) == 4 ? 2 : 1;
-template <typename T> constexpr size_t tile_smem_bytes()
+template <typename T, int TZ> constexpr size_t tile_smem_bytes()
 {
-    return (size_t)(kTileBufs<T> * GTILE + GDX + GDY) * sizeof(vec4_t<T>);
+    using G = TileG<TZ>;
+    return (size_t)(kTileBufs<T> * G::TILEN + G::DXN + G::DYN) * sizeof(vec4_t<T>);
 }
 
 // Stage d_x phi and d_y phi of the tile (all threads), from the loaded tile.
 // Entries whose stencil leaves the lattice hold garbage that only sites
 // outside the interior read.
-template <typename T>
+template <int TZ, typename T>
 __device__ __forceinline__ void stage_first_derivatives(const vec4_t<T> *tile, vec4_t<T> *dxs,
                                                         vec4_t<T> *dys, T w1, T w2)
 {
+    using G = TileG<TZ>;
     const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-    auto P = [&](int tx, int ty, int tz) -> const vec4_t<T> & { return tile[(tx * GSY + ty) * GSZ + tz]; };
-    for (int i = tid; i < GDX; i += GTHREADS) {
-        const int lz = i % GSZ, ly = (i / GSZ) % GSY, lx = i / (GSZ * GSY);
+    auto P = [&](int tx, int ty, int tz) -> const vec4_t<T> & { return tile[(tx * G::SY + ty) * G::SZ + tz]; };
+    for (int i = tid; i < G::DXN; i += GTHREADS) {
+        const int lz = i % G::SZ, ly = (i / G::SZ) % G::SY, lx = i / (G::SZ * G::SY);
         dxs[i] = sd1v<T>(P(lx, ly, lz), P(lx + 1, ly, lz), P(lx + 3, ly, lz), P(lx + 4, ly, lz), w1, w2);
     }
-    for (int i = tid; i < GDY; i += GTHREADS) {
-        const int lz = i % GSZ, ly = (i / GSZ) % GTY, lx = i / (GSZ * GTY);
+    for (int i = tid; i < G::DYN; i += GTHREADS) {
+        const int lz = i % G::SZ, ly = (i / G::SZ) % G::TY, lx = i / (G::SZ * G::TY);
         dys[i] = sd1v<T>(P(lx + 2, ly, lz), P(lx + 2, ly + 1, lz), P(lx + 2, ly + 3, lz),
                          P(lx + 2, ly + 4, lz), w1, w2);
     }
 }
 
 // All derivatives of the site at local interior coordinate (lx, ly, lz).
-template <typename T>
+template <int TZ, typename T>
 __device__ __forceinline__ void tile_derivatives(const vec4_t<T> *tile, const vec4_t<T> *dxs,
                                                  const vec4_t<T> *dys, int lx, int ly, int lz,
                                                  const FlowParams<T> &p, T phi[4], T d1[3][4],
                                                  T d2[3][4], T dm[3][4])
 {
+    using G = TileG<TZ>;
     auto P = [&](int dx, int dy, int dz) -> vec4_t<T> {
-        return tile[((lx + 2 + dx) * GSY + (ly + 2 + dy)) * GSZ + (lz + 2 + dz)];
+        return tile[((lx + 2 + dx) * G::SY + (ly + 2 + dy)) * G::SZ + (lz + 2 + dz)];
     };
     // d_x phi at (lx, ly + 2 + dy, lz + 2 + dz) and d_y phi at (lx, ly, lz + 2 + dz)
-    auto DX = [&](int dy, int dz) -> vec4_t<T> { return dxs[(lx * GSY + ly + 2 + dy) * GSZ + lz + 2 + dz]; };
-    auto DY = [&](int dz) -> vec4_t<T> { return dys[(lx * GTY + ly) * GSZ + lz + 2 + dz]; };
+    auto DX = [&](int dy, int dz) -> vec4_t<T> { return dxs[(lx * G::SY + ly + 2 + dy) * G::SZ + lz + 2 + dz]; };
+    auto DY = [&](int dz) -> vec4_t<T> { return dys[(lx * G::TY + ly) * G::SZ + lz + 2 + dz]; };
     const T w1 = p.w1, w2 = p.w2, v1 = p.v1, v2 = p.v2, v0 = p.v0;
     const vec4_t<T> c = P(0, 0, 0);
     const int off[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
@@ -267,14 +279,15 @@ constexpr int kTileMinBlocks = sizeof(T) == 4 ? 3 : (EXT ? 1 : 2);
 
 // kind 0: fused step; kind 1: energy only; kind 2: per-site dump.
 // EXT: the Section 7.8 extension terms are included.
-template <typename T, int KIND, bool EXT>
+template <typename T, int KIND, bool EXT, int TZ>
 __global__ void __launch_bounds__(GTHREADS, kTileMinBlocks<T, EXT>) k_tile(FlowParams<T> p, vec4_t<T> *fout,
                                                    vec4_t<T> *dout)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     vec4_t<T> *tiles = reinterpret_cast<vec4_t<T> *>(smem_raw);
-    vec4_t<T> *dxs = tiles + kTileBufs<T> * GTILE;
-    vec4_t<T> *dys = dxs + GDX;
+    using G = TileG<TZ>;
+    vec4_t<T> *dxs = tiles + kTileBufs<T> * G::TILEN;
+    vec4_t<T> *dys = dxs + G::DXN;
     const int cur = __ldcg(&p.ctrl->cur);
     const int pred = (KIND == 0 && p.mode == MODE_ARRESTED) ? __ldcg(&p.ctrl->pred) : 0;
     // buffers selected by value (a run-time index into the parameter copies it to the stack)
@@ -284,8 +297,8 @@ __global__ void __launch_bounds__(GTHREADS, kTileMinBlocks<T, EXT>) k_tile(FlowP
     vec4_t<T> *vel_out = cur ? p.vel[0] : p.vel[1];
     const int lz = threadIdx.x, ly = threadIdx.y, lx = threadIdx.z;
     // persistent CTAs walk the tiles z-fastest, so CTAs in flight share halos in L2
-    const int nz = (p.n2 - 4 + GTZ - 1) / GTZ, ny = (p.n1 - 4 + GTY - 1) / GTY;
-    const int ntiles = nz * ny * ((p.n0 - 4 + GTX - 1) / GTX);
+    const int nz = (p.n2 - 4 + G::TZ - 1) / G::TZ, ny = (p.n1 - 4 + G::TY - 1) / G::TY;
+    const int ntiles = nz * ny * ((p.n0 - 4 + G::TX - 1) / G::TX);
     // Per-thread sums {e2, e4, e0, b, |F|^2, max |F|^2, e6}.  The FP32 kernels
     // add in FP32 over at most kFoldTiles tiles and then fold into FP64, so
     // that the FP64 pipe (1/64 of the FP32 rate) does a few operations per
@@ -318,18 +331,18 @@ __global__ void __launch_bounds__(GTHREADS, kTileMinBlocks<T, EXT>) k_tile(FlowP
         for (int q = 0; q < 7; ++q) part[q] = T(0), comp[q] = T(0);
         pending = 0;
     };
-    auto x0_of = [&](int t) { return 2 + (t / (nz * ny)) * GTX; };
-    auto y0_of = [&](int t) { return 2 + ((t / nz) % ny) * GTY; };
-    auto z0_of = [&](int t) { return 2 + (t % nz) * GTZ; };
+    auto x0_of = [&](int t) { return 2 + (t / (nz * ny)) * G::TX; };
+    auto y0_of = [&](int t) { return 2 + ((t / nz) % ny) * G::TY; };
+    auto z0_of = [&](int t) { return 2 + (t % nz) * G::TZ; };
     if constexpr (kTileBufs<T> == 2) {
         if (blockIdx.x < ntiles)
-            load_tile_async(tiles, phi, x0_of(blockIdx.x), y0_of(blockIdx.x), z0_of(blockIdx.x),
+            load_tile_async<TZ>(tiles, phi, x0_of(blockIdx.x), y0_of(blockIdx.x), z0_of(blockIdx.x),
                             p.n0, p.n1, p.n2);
     }
     int buf = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, buf ^= (kTileBufs<T> - 1)) {
         const int x0 = x0_of(t), y0 = y0_of(t), z0 = z0_of(t);
-        vec4_t<T> *tile = tiles + buf * GTILE;
+        vec4_t<T> *tile = tiles + buf * G::TILEN;
         if constexpr (kTileBufs<T> == 2) {
             wait_tile_async();  // this thread's copies of tile t have landed
             // every thread's copies have landed, and every thread is done with
@@ -337,19 +350,19 @@ __global__ void __launch_bounds__(GTHREADS, kTileMinBlocks<T, EXT>) k_tile(FlowP
             __syncthreads();
             const int tn = t + gridDim.x;
             if (tn < ntiles)
-                load_tile_async(tiles + (buf ^ 1) * GTILE, phi, x0_of(tn), y0_of(tn), z0_of(tn),
+                load_tile_async<TZ>(tiles + (buf ^ 1) * G::TILEN, phi, x0_of(tn), y0_of(tn), z0_of(tn),
                                 p.n0, p.n1, p.n2);
         } else {
             __syncthreads();  // the previous tile's readers are done with shared memory
-            load_tile<T>(tile, phi, x0, y0, z0, p.n0, p.n1, p.n2);
+            load_tile<TZ, T>(tile, phi, x0, y0, z0, p.n0, p.n1, p.n2);
             __syncthreads();
         }
-        stage_first_derivatives<T>(tile, dxs, dys, p.w1, p.w2);
+        stage_first_derivatives<TZ, T>(tile, dxs, dys, p.w1, p.w2);
         __syncthreads();
         const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
         if (!((x <= p.n0 - 3) && (y <= p.n1 - 3) && (z <= p.n2 - 3))) continue;
         T ph[4], d1[3][4], d2[3][4], dm[3][4], F[4], dens[4], e6 = T(0);
-        tile_derivatives<T>(tile, dxs, dys, lx, ly, lz, p, ph, d1, d2, dm);
+        tile_derivatives<TZ, T>(tile, dxs, dys, lx, ly, lz, p, ph, d1, d2, dm);
         site_physics<T, EXT>(ph, d1, d2, dm, p.m2, F, dens, &p.ext, &e6);
         const size_t s = site_index(x, y, z, p.n1, p.n2);
         if (KIND == 0) {
@@ -519,17 +532,28 @@ cudaError_t launch_until_check(void *ctrl, unsigned long long handle, double tol
 // (the partial-record space of the scratch holds at least that many).
 constexpr int kTileGridCap = 152 * 8;
 
-TileGeom tile_geometry(const skyrme_lattice &lat)
+template <int TZ> static TileGeom tile_geometry_tz(const skyrme_lattice &lat)
 {
+    using G = TileG<TZ>;
     TileGeom g;
     const int ix = lat.n[0] - 4, iy = lat.n[1] - 4, iz = lat.n[2] - 4;
-    const long long ntiles = (long long)((iz + GTZ - 1) / GTZ) * ((iy + GTY - 1) / GTY) *
-                             ((ix + GTX - 1) / GTX);
+    const long long ntiles = (long long)((iz + G::TZ - 1) / G::TZ) * ((iy + G::TY - 1) / G::TY) *
+                             ((ix + G::TX - 1) / G::TX);
     g.nblocks = (int)std::min<long long>(ntiles, kTileGridCap);
     g.grid = dim3(g.nblocks);
-    g.block = dim3(GTZ, GTY, GTX);
-    g.smem = lat.precision == 64 ? tile_smem_bytes<double>() : tile_smem_bytes<float>();
+    g.block = dim3(G::TZ, G::TY, G::TX);
+    g.smem = lat.precision == 64 ? tile_smem_bytes<double, TZ>() : tile_smem_bytes<float, TZ>();
+    g.tz = TZ;
     return g;
+}
+
+// The 16-wide z tile is taken only where it leaves fewer idle lanes than the
+// 32-wide one (it pays more halo per site where both pad alike).
+TileGeom tile_geometry(const skyrme_lattice &lat)
+{
+    const int iz = lat.n[2] - 4;
+    const int pad32 = (iz + 31) / 32 * 32 - iz, pad16 = (iz + 15) / 16 * 16 - iz;
+    return pad16 < pad32 ? tile_geometry_tz<16>(lat) : tile_geometry_tz<32>(lat);
 }
 
 template <typename T> static FlowParams<T> make_params(const FlowArgs &a, double *parts)
@@ -564,30 +588,38 @@ template <typename T> static FlowParams<T> make_params(const FlowArgs &a, double
     return p;
 }
 
-template <typename T, int KIND, bool EXT>
-static cudaError_t launch_tile_model(const skyrme_lattice &lat, const FlowParams<T> &p,
-                                     vec4_t<T> *fo, vec4_t<T> *dout, cudaStream_t s)
+template <typename T, int KIND, bool EXT, int TZ>
+static cudaError_t launch_tile_geom(const TileGeom &g, const FlowParams<T> &p, vec4_t<T> *fo,
+                                    vec4_t<T> *dout, cudaStream_t s)
 {
-    const TileGeom g = tile_geometry(lat);
     // resident CTAs of this instantiation on the whole GPU (queried once)
     static thread_local int resident = 0;
     if (!resident) {
-        cudaError_t e = cudaFuncSetAttribute(k_tile<T, KIND, EXT>,
+        cudaError_t e = cudaFuncSetAttribute(k_tile<T, KIND, EXT, TZ>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)tile_smem_bytes<T>());
+                                             (int)tile_smem_bytes<T, TZ>());
         if (e != cudaSuccess) return e;
         int dev = 0, sms = 0, per_sm = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
             return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile<T, KIND, EXT>, GTHREADS,
-                                                          tile_smem_bytes<T>());
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile<T, KIND, EXT, TZ>,
+                                                          GTHREADS, tile_smem_bytes<T, TZ>());
         if (e != cudaSuccess) return e;
         resident = std::max(1, sms * std::max(1, per_sm));
     }
     const int grid = std::min(g.nblocks, resident);
-    k_tile<T, KIND, EXT><<<grid, g.block, g.smem, s>>>(p, fo, dout);
+    k_tile<T, KIND, EXT, TZ><<<grid, g.block, g.smem, s>>>(p, fo, dout);
     return cudaGetLastError();
+}
+
+template <typename T, int KIND, bool EXT>
+static cudaError_t launch_tile_model(const skyrme_lattice &lat, const FlowParams<T> &p,
+                                     vec4_t<T> *fo, vec4_t<T> *dout, cudaStream_t s)
+{
+    const TileGeom g = tile_geometry(lat);
+    return g.tz == 16 ? launch_tile_geom<T, KIND, EXT, 16>(g, p, fo, dout, s)
+                      : launch_tile_geom<T, KIND, EXT, 32>(g, p, fo, dout, s);
 }
 
 template <typename T, int KIND>

@@ -25,6 +25,7 @@ struct TileGeom {
     dim3 block;
     int nblocks;
     size_t smem;
+    int tz;  // z extent of the tile: 32, or 16 where that pads the lattice less
 };
 
 TileGeom tile_geometry(const skyrme_lattice &lat);
