@@ -16,7 +16,8 @@
 //    touched it are done (per-lattice arrival counter, last-CTA finish), so
 //    lattices of different sizes need no global barrier.
 //  * each x-plane of the column tile, with its 2-site halo, is streamed into
-//    a 4-slot shared-memory ring by TMA (cp.async.bulk.tensor.3d) with an
+//    a shared-memory ring (8 slots for a single lattice's 16 x 32 tile, else
+//    4) by TMA (cp.async.bulk.tensor.3d) with an
 //    mbarrier per slot; every wait is bounded and reports SKYRME_ETIMEOUT
 //    instead of hanging.  Warps consume the planes independently: the last
 //    warp to be done with a slot (a shared-memory counter) streams the next
@@ -25,9 +26,14 @@
 //    later (13 per site) wait in tensor memory: each warp keeps a 3-slot ring
 //    of them in its TMEM lanes (tcgen05.st / tcgen05.ld), which takes them
 //    off the shared-memory pipe and out of shared memory.
+//  * derivatives are carried without their 1/(12h), 1/(12h^2) factors (the
+//    first-derivative stencil is then 3 instructions per component pair, the
+//    second 4); the factors move into the time step, the mass terms and the
+//    FP64 scale of the sums.
 //  * in-plane derivatives (d_y, d_z, d_yy, d_zz) come from the staged plane;
 //    d_yz = d_z(d_y phi) uses a per-warp shared-memory exchange of d_y phi
-//    (each warp computes the 4 z-halo columns of its own rows); d_x, d_xx,
+//    (each warp computes the 4 z-halo columns of its own rows, one
+//    component per lane); d_x, d_xx,
 //    d_xy = d_x(d_y phi), d_xz = d_x(d_z phi) come from a 5-plane register
 //    ring of (phi, d_y phi, d_z phi) that the x-loop cycles through (unrolled
 //    by 5 so no register is ever moved).  The velocity of each centre plane
@@ -59,7 +65,15 @@
 
 namespace skyrme {
 
-constexpr int NSLOT = 4;
+// Depth of the TMA plane ring: 8 slots for the 512-thread tile of a single
+// lattice (one CTA per SM; more copies in flight), 4 for the smaller tiles
+// that share an SM and for the sextic variant (its register spills live in
+// the L1 share of the SM's shared-memory array).  A power of two keeps the
+// slot arithmetic to shifts.
+template <int TY, int TZ, bool SEX = false> constexpr int nslot()
+{
+    return TY * TZ >= 512 && !SEX ? 8 : 4;
+}
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per plane copy
 
 // One lattice of a step launch: a kernel parameter for a single lattice, an
@@ -76,17 +90,34 @@ struct InstDesc {
     int n0, n1, n2;
     int nzt, nix;          // column tiles along z, interior planes along x
     int cta_first, cta_count;
-    // stencil weights and time steps as (w, w) pairs: the packed FP32
-    // instructions take them as one 64-bit operand
-    float2 c1, c2;         // first-derivative weights / h
-    float2 s1, s2, s0;     // second-derivative weights / h^2
-    float2 dt, dt2;        // dt and 2 dt
-    float m2;
+    // Stencil weights and time steps as (w, w) pairs: the packed FP32
+    // instructions take them as one 64-bit operand.  The kernels carry the
+    // derivatives without their 1/(12h), 1/(12h^2) factors: u_i = 12h d_i phi
+    // = 8 (p1 - m1) - (p2 - m2), and every second derivative negated on one
+    // scale, N_ij = -12h^2 d_ij phi: the pure ones as (p2 + m2) + 30 c -
+    // 16 (p1 + m1), the mixed ones as -(2/3)(p1 - m1) + (1/12)(p2 - m2) of
+    // the u_i.  The force then comes out as F / B, B = 1/(1728 h^4); B moves
+    // into the time step and the mass terms, and the sums are scaled in the
+    // finish.
+    float2 w8;             // (8, 8)
+    float2 wm16, w30;      // (-16, -16), (30, 30)
+    float2 xm1, xm2;       // (-2/3, -2/3), (1/12, 1/12)
+    float2 dt, dt2;        // dt and 2 dt B
+    float m2;              // m^2 (potential energy density)
+    float bm2;             // m^2 / B (its force term)
+    float negK;            // -144 h^2: the quadratic term of the force against the quartic ones
     // Section 7.8 potentials (the POT kernels): squared masses of the
-    // modified-pion, loosely and lightly bound terms
+    // modified-pion, loosely and lightly bound terms, and the same / B
     float my2, mz2, mw2;
+    float bmy2, bmz2, bmw2;
     float e0_scale;        // E0 = h^3 e0_scale sum(e0 slot): 2 m^2 (standard) or 1 (POT)
     float c6;              // Section 7.8 sextic coefficient (the SEX kernels)
+    float c6b;             // c6 / (144 h^2): the sextic force term's weight
+    float dk2, dk3, dk4;   // DUMP kernels: (12h)^-2, ^-3, ^-4 to the densities they write
+    // (hi, lo) factors of the sums: e2 (12h)^-2, e4 (12h)^-4, det (12h)^-3,
+    // e6 (12h)^-6, |F|^2 B^2 (all 1 but |F|^2 in the DUMP kernels, whose
+    // per-site densities are already scaled)
+    float2 s_e2, s_e4, s_b, s_e6, s_f;
     float h3_hi, h3_lo;    // h^3 as an unevaluated float sum
     int mode;
     double *slab_rec;      // x-slab of a larger lattice: record out, no decision (else null)
@@ -248,17 +279,24 @@ __device__ __forceinline__ float dot(const P4 &u, const P4 &v)
 {
     return hsum(__ffma2_rn(u.b, v.b, __fmul2_rn(u.a, v.a)));
 }
-// first derivative c1 (p1 - m1) + c2 (p2 - m2)
+// weighted first difference c1 (p1 - m1) + c2 (p2 - m2) (the mixed second
+// derivatives, of the u_i)
 __device__ __forceinline__ P4 fd1(const P4 &m2, const P4 &m1, const P4 &p1, const P4 &p2, float2 c1,
                                   float2 c2)
 {
     return fma(c2, sub(p2, m2), mul(c1, sub(p1, m1)));
 }
-// second derivative s1 (p1 + m1) + s2 (p2 + m2) + s0 c
-__device__ __forceinline__ P4 fd2(const P4 &m2, const P4 &m1, const P4 &c, const P4 &p1,
-                                  const P4 &p2, float2 s1, float2 s2, float2 s0)
+// 12h d phi = 8 (p1 - m1) - (p2 - m2), w8 = (8, 8)
+__device__ __forceinline__ P4 fd1u(const P4 &m2, const P4 &m1, const P4 &p1, const P4 &p2,
+                                   float2 w8)
 {
-    return fma(s0, c, fma(s2, add(p2, m2), mul(s1, add(p1, m1))));
+    return fma(w8, sub(p1, m1), sub(m2, p2));
+}
+// -12h^2 d^2 phi = (p2 + m2) + 30 c - 16 (p1 + m1), wm16 = (-16, -16), w30 = (30, 30)
+__device__ __forceinline__ P4 fd2n(const P4 &m2, const P4 &m1, const P4 &c, const P4 &p1,
+                                   const P4 &p2, float2 wm16, float2 w30)
+{
+    return fma(wm16, add(p1, m1), fma(w30, c, add(p2, m2)));
 }
 
 // ------------------------------------------------- double-float sums
@@ -414,34 +452,43 @@ __device__ __forceinline__ void block_reduce_df(DF (&v)[kSums], float amax, DF *
     }
 }
 
+// Pairwise sum of x[0..K) into x[0] (K a power of two): a tree of depth log2 K
+template <int K> __device__ __forceinline__ void df_tree(DF (&x)[K])
+{
+#pragma unroll
+    for (int w = 1; w < K; w <<= 1) {
+#pragma unroll
+        for (int k = 0; k + w < K; k += 2 * w) x[k] = df_add(x[k], x[k + w]);
+    }
+}
+
 // Block sum of the per-thread double-float sums kept in shared memory
 // (accs: kSums arrays of NT, amaxs: NT) for CTAs of at least kSums + 1 warps:
-// warp q sums quantity q, each lane over two independent chains, then a
-// butterfly; warp kSums takes the max.  Fixed order; thread 0 ends with the
-// totals.  The caller has synchronised after the last write to accs.
+// warp q sums quantity q, each lane its NT / 32 entries as a pairwise tree,
+// then a butterfly; warp kSums takes the max.  Fixed order; thread 0 ends
+// with the totals.  The caller has synchronised after the last write to accs.
 template <int NT>
 __device__ __forceinline__ void block_reduce_df_smem(const DF *accs, const float *amaxs, DF *red,
                                                      float *mred, DF (&tot)[kSums], float &tmax,
                                                      int tid)
 {
-    static_assert(NT / 32 > kSums && NT % 64 == 0, "one warp per quantity and two chains");
+    constexpr int K = NT / 32;
+    static_assert(K > kSums && (K & (K - 1)) == 0, "one warp per quantity, a power-of-two tree");
     const int lane = tid & 31, warp = tid >> 5;
     if (warp < kSums) {
         const DF *a = accs + warp * NT + lane;
-        DF c0 = {0.f, 0.f}, c1 = {0.f, 0.f};
-#pragma unroll 1
-        for (int k = 0; k < NT / 32; k += 2) {
-            c0 = df_add(c0, a[32 * k]);
-            c1 = df_add(c1, a[32 * k + 32]);
-        }
-        DF v = df_add(c0, c1);
+        DF x[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) x[k] = a[32 * k];
+        df_tree<K>(x);
+        DF v = x[0];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
         if (lane == 0) red[warp] = v;
     } else if (warp == kSums) {
         float m = 0.f;
-#pragma unroll 1
-        for (int k = 0; k < NT / 32; ++k) m = fmaxf(m, amaxs[lane + 32 * k]);
+#pragma unroll
+        for (int k = 0; k < K; ++k) m = fmaxf(m, amaxs[lane + 32 * k]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
         if (lane == 0) *mred = m;
@@ -459,14 +506,14 @@ struct PlaneVals {
     P4 phi, dy, dz;
 };
 
-template <int TY, int TZ> struct __align__(128) StepSmem {
-    float4 plane[NSLOT][TY + 4][TZ + 4];  // haloed field planes (TMA)
-    float4 vpl[NSLOT][TY][TZ];            // velocity planes of the centre sites (TMA)
+template <int TY, int TZ, bool SEX = false> struct __align__(128) StepSmem {
+    float4 plane[nslot<TY, TZ, SEX>()][TY + 4][TZ + 4];  // haloed field planes (TMA)
+    float4 vpl[nslot<TY, TZ, SEX>()][TY][TZ];            // velocity planes of the centre sites (TMA)
     float4 dy[2][TY][TZ + 4];             // d_y phi exchange for d_yz
-    int rel[NSLOT];                       // warps done with the plane in each slot
+    int rel[nslot<TY, TZ, SEX>()];        // warps done with the plane in each slot
     DF accs[kSums][TY * TZ];              // per-thread double-float sums (kept out of registers)
     float amaxs[TY * TZ];                 // per-thread max |F|^2
-    unsigned long long bar[NSLOT];
+    unsigned long long bar[nslot<TY, TZ, SEX>()];
     DF dfred[kSums * (TY * TZ / 32)];
     float mxred[TY * TZ / 32];
     int flag;
@@ -487,7 +534,7 @@ template <int TY, int TZ, bool SEX = false> constexpr size_t step_smem_bytes()
     constexpr size_t per_sm = 228 * 1024;
     constexpr int max_ctas = 512 / tmem_cols<TY * TZ / 32, SEX>();
     constexpr size_t floor_bytes = per_sm / (max_ctas + 1) + 1;  // max_ctas + 1 never fit
-    return sizeof(StepSmem<TY, TZ>) > floor_bytes ? sizeof(StepSmem<TY, TZ>) : floor_bytes;
+    return sizeof(StepSmem<TY, TZ, SEX>) > floor_bytes ? sizeof(StepSmem<TY, TZ, SEX>) : floor_bytes;
 }
 
 struct CtaSync {
@@ -503,25 +550,28 @@ __device__ __forceinline__ void arrive_plane(const float4 (*P)[TZ + 4], float4 (
                                              const InstDesc &D, int tid, int ty, int tz,
                                              PlaneVals &rv, P4 &dyy, P4 &dzz)
 {
-    const float2 c1 = D.c1, c2 = D.c2, s1 = D.s1, s2 = D.s2, s0 = D.s0;
+    const float2 w8 = D.w8, wm16 = D.wm16, w30 = D.w30;
     const P4 c = ld4(P[ty + 2][tz + 2]);
     const P4 ym2 = ld4(P[ty][tz + 2]), ym1 = ld4(P[ty + 1][tz + 2]);
     const P4 yp1 = ld4(P[ty + 3][tz + 2]), yp2 = ld4(P[ty + 4][tz + 2]);
     const P4 zm2 = ld4(P[ty + 2][tz]), zm1 = ld4(P[ty + 2][tz + 1]);
     const P4 zp1 = ld4(P[ty + 2][tz + 3]), zp2 = ld4(P[ty + 2][tz + 4]);
-    const P4 dy = fd1(ym2, ym1, yp1, yp2, c1, c2);
-    const P4 dz = fd1(zm2, zm1, zp1, zp2, c1, c2);
-    dyy = fd2(ym2, ym1, c, yp1, yp2, s1, s2, s0);
-    dzz = fd2(zm2, zm1, c, zp1, zp2, s1, s2, s0);
+    const P4 dy = fd1u(ym2, ym1, yp1, yp2, w8);
+    const P4 dz = fd1u(zm2, zm1, zp1, zp2, w8);
+    dyy = fd2n(ym2, ym1, c, yp1, yp2, wm16, w30);
+    dzz = fd2n(zm2, zm1, c, zp1, zp2, wm16, w30);
     DY[ty][tz + 2] = st4(dy);
-    {  // each warp fills the z-halo columns of d_y phi of its own rows
-        constexpr int ROWS = 32 / TZ;
+    {  // each warp fills the z-halo columns of u_y of its own rows, one
+       // component per lane (a packed 4-vector stencil would idle 28 lanes);
+       // the same roundings as fd1u
+        constexpr int ROWS = 32 / TZ, RS = 4 * (TZ + 4);  // floats per haloed row
         const int lane = tid & 31;
-        if (lane < 4 * ROWS) {
-            const int hr = (tid >> 5) * ROWS + (lane >> 2), ci = lane & 3;
+        if (lane < 16 * ROWS) {
+            const int hr = (tid >> 5) * ROWS + (lane >> 4), ci = (lane >> 2) & 3, k = lane & 3;
             const int hc = ci < 2 ? ci : TZ + ci;
-            DY[hr][hc] = st4(fd1(ld4(P[hr][hc]), ld4(P[hr + 1][hc]), ld4(P[hr + 3][hc]),
-                                 ld4(P[hr + 4][hc]), c1, c2));
+            const float *pc = reinterpret_cast<const float *>(&P[hr][hc]) + k;
+            const float m2 = pc[0], m1 = pc[RS], p1 = pc[3 * RS], p2 = pc[4 * RS];
+            reinterpret_cast<float *>(&DY[hr][hc])[k] = __fmaf_rn(w8.x, __fsub_rn(p1, m1), __fsub_rn(m2, p2));
         }
     }
     rv.phi = c;
@@ -539,7 +589,7 @@ __device__ __forceinline__ void plane_record(const float4 (*DY)[TZ + 4], const I
     constexpr int THREADS = TY * TZ;
     const P4 dy = rv.dy, dz = rv.dz;
     const P4 dyz = fd1(ld4(DY[ty][tz]), ld4(DY[ty][tz + 1]), ld4(DY[ty][tz + 3]), ld4(DY[ty][tz + 4]),
-                       D.c1, D.c2);
+                       D.xm1, D.xm2);
     const float ayy = dot(dy, dy), azz = dot(dz, dz), ayz = dot(dy, dz);
     const P4 lin = add(dyy, dzz);
     const P4 qin = fma(bc(2.f * ayz), dyz, fma(bc(azz), dzz, mul(bc(ayy), dyy)));
@@ -557,7 +607,7 @@ __device__ __forceinline__ void plane_record(const float4 (*DY)[TZ + 4], const I
 }
 
 // One centre site: x-derivatives from the register ring (M2, M1, C, Q1, Q2 in
-// streaming order; xc1, xc2 are the first-derivative weights along x), the
+// streaming order; xc1, xc2 are the mixed-derivative weights along x), the
 // Euler-Lagrange force of Eq. (3.3) projected on the tangent space, the
 // symplectic update with renormalisation, and the energy, charge and force
 // densities into a32 (valid sites only).
@@ -571,7 +621,6 @@ __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &
                                             size_t si, Acc &a32)
 {
     constexpr int THREADS = TY * TZ;
-    const float2 s1 = D.s1, s2 = D.s2, s0 = D.s0;
     const int mode = D.mode;
     const float2 dt = D.dt, dt2 = D.dt2;
     float rv[16];
@@ -584,24 +633,27 @@ __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &
     const float Cayz = rv[12];
     (void)THREADS;
     const P4 ph = C.phi;
-    const P4 dx = fd1(M2.phi, M1.phi, Q1.phi, Q2.phi, xc1, xc2);
-    const P4 dxx = fd2(M2.phi, M1.phi, ph, Q1.phi, Q2.phi, s1, s2, s0);
+    // u_x and the negated second derivatives N_xx, N_xy, N_xz (the scales
+    // are those of the descriptor's stencil weights)
+    const P4 dx = fd1u(M2.phi, M1.phi, Q1.phi, Q2.phi, D.w8);
+    const P4 dxx = fd2n(M2.phi, M1.phi, ph, Q1.phi, Q2.phi, D.wm16, D.w30);
     const P4 dxy = fd1(M2.dy, M1.dy, Q1.dy, Q2.dy, xc1, xc2);
     const P4 dxz = fd1(M2.dz, M1.dz, Q1.dz, Q2.dz, xc1, xc2);
     const P4 dyc = C.dy, dzc = C.dz;
     const float axx = dot(dx, dx), axy = dot(dx, dyc), axz = dot(dx, dzc);
     const float tra = axx + Cayy + Cazz;
-    const P4 L = add(dxx, lin);
-    // g_i = sum_j d_ij phi.d_j phi; c_i = g_i - Laplacian.d_i phi
+    const P4 L = add(dxx, lin);  // -12h^2 Laplacian phi
+    // g_i = sum_j d_ij phi.d_j phi and c_i = g_i - Laplacian.d_i phi, both
+    // negated; nc_i = -c_i
     const float gx = hsum(dot2(dxz, dzc, dot2(dxy, dyc, __ffma2_rn(dxx.b, dx.b, __fmul2_rn(dxx.a, dx.a)))));
     const float gy = dot(dxy, dx) + Cgy;
     const float gz = dot(dxz, dx) + Cgz;
-    const float ccx = gx - dot(L, dx), ccy = gy - dot(L, dyc), ccz = gz - dot(L, dzc);
-    // d_ij phi a_ij summed over i, j
+    const float ncx = dot(L, dx) - gx, ncy = dot(L, dyc) - gy, ncz = dot(L, dzc) - gz;
+    // -d_ij phi a_ij summed over i, j
     const P4 Ha = fma(bc(2.f * axz), dxz, fma(bc(2.f * axy), dxy, fma(bc(axx), dxx, qin)));
-    // brace of the Euler-Lagrange equation; G = -2 (brace + m^2 e_0)
-    P4 br = fma(bc(ccz), dzc, fma(bc(ccy), dyc, fma(bc(ccx), dx, fma(bc(1.f + tra), L, mul(bc(-1.f), Ha)))));
-    br.a.x += D.m2;
+    // brace of the Euler-Lagrange equation / B; G = -2 B (brace + m^2 e_0 / B)
+    P4 br = fma(bc(ncz), dzc, fma(bc(ncy), dyc, fma(bc(ncx), dx, fma(bc(D.negK - tra), L, Ha))));
+    br.a.x += D.bm2;
     // 1 - phi^0 from the pion components where it cancels (phi^0 >= 0)
     auto one_minus_phi0 = [&]() {
         const float2 pq = __fmul2_rn(ph.b, ph.b);
@@ -613,7 +665,7 @@ __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &
         // d/dphi^0 of the Section 7.8 potentials m_y^2 (1 - phi0^2) + m_z^2 u^2
         // + m_w^2 u^4 / 2, u = 1 - phi^0, in the brace (G = -2 brace)
         u = one_minus_phi0();
-        br.a.x += fmaf(D.my2, ph.a.x, u * fmaf(D.mw2 * u, u, D.mz2));
+        br.a.x += fmaf(D.bmy2, ph.a.x, u * fmaf(D.bmw2 * u, u, D.bmz2));
     }
     float e6 = 0.f;
     if constexpr (SEX) {
@@ -621,8 +673,11 @@ __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &
         // (= c6 4 pi^4 (B0)^2): its Euler-Lagrange gradient is
         // 2 c6 [4 D P - sum_i (d_i D) Q_i] with P = dD/dphi, Q_i = dD/d(d_i phi)
         // and d_i D = sum_j Q_j . d_i d_j phi; in the brace (G = -2 brace) it
-        // enters as -c6 [...].
-        float rs[16];  // d_yy, d_zz, d_yz phi of the centre plane
+        // enters as -c6 [...].  From the u_i and N_ij (D, P, Q, d_i D carry
+        // (12h)^-3, ^-3, ^-2 and -(12h)^-2 (12h^2)^-1) the bracket is
+        // (12h)^-4 (12h^2)^-1 [D P / 3 + sum_i dDn_i Q_i], which enters the
+        // brace / B with the weight -c6 / (144 h^2).
+        float rs[16];  // N_yy, N_zz, N_yz of the centre plane
         tmem_ld16(trec + 16, rs);
         const float ph4[4] = {ph.a.x, ph.a.y, ph.b.x, ph.b.y};
         const float u4[4] = {dx.a.x, dx.a.y, dx.b.x, dx.b.y};
@@ -644,12 +699,12 @@ __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &
         const float dDy = dot(qx, dxy) + dot(qy, dyy) + dot(qz, dyz);
         const float dDz = dot(qx, dxz) + dot(qy, dyz) + dot(qz, dzz);
         const P4 pp = {make_float2(P[0], P[1]), make_float2(P[2], P[3])};
-        const P4 sx = fma(bc(-dDz), qz, fma(bc(-dDy), qy, fma(bc(-dDx), qx, mul(bc(4.f * Dd), pp))));
-        br = fma(bc(-D.c6), sx, br);
+        const P4 sx = fma(bc(dDz), qz, fma(bc(dDy), qy, fma(bc(dDx), qx, mul(bc(Dd * (1.f / 3.f)), pp))));
+        br = fma(bc(-D.c6b), sx, br);
         e6 = D.c6 * Dd * Dd;
     }
 
-    // F = -G + (G.phi) phi = 2 (br - (br.phi) phi)
+    // F = -G + (G.phi) phi = 2 B (br - (br.phi) phi); dt2 = 2 dt B
     const float bp = dot(br, ph);
     const P4 Fh = fma(bc(-bp), ph, br);
     const float f2 = 4.f * dot(Fh, Fh);
@@ -686,10 +741,17 @@ __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &
         } else {
             e0v = one_minus_phi0();
         }
-        if constexpr (DUMP) __stcs(D.dump + si, make_float4(tra, e4, e0v, det));
+        if constexpr (DUMP) {
+            // the densities in lattice units; the sums take the same values
+            const float e2s = tra * D.dk2, e4s = e4 * D.dk4, dets = det * D.dk3;
+            __stcs(D.dump + si, make_float4(e2s, e4s, e0v, dets));
+            two_sum_acc(a32.s24, a32.c24, make_float2(e2s, e4s));
+            two_sum_acc(a32.s0b, a32.c0b, make_float2(e0v, dets));
+        } else {
+            two_sum_acc(a32.s24, a32.c24, make_float2(tra, e4));
+            two_sum_acc(a32.s0b, a32.c0b, make_float2(e0v, det));
+        }
         if constexpr (SEX) two_sum_acc1(a32.s6, a32.c6, e6);
-        two_sum_acc(a32.s24, a32.c24, make_float2(tra, e4));
-        two_sum_acc(a32.s0b, a32.c0b, make_float2(e0v, det));
         a32.f2 += f2;
         a32.fmax2 = fmaxf(a32.fmax2, f2);
     }
@@ -721,18 +783,32 @@ __device__ __forceinline__ void write_record(const InstDesc &D, int slot, const 
     recp[3] = make_float4(tot[5].hi, tot[5].lo, 0.f, 0.f);
 }
 
+__device__ __forceinline__ void st_release_s64(long long *p, long long v)
+{
+    asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+// Arrival at a lattice's counter: releases this thread's earlier stores (the
+// CTA record) and acquires every earlier arrival's
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 // End of a step for one lattice, run by every thread of the last CTA to
 // leave it.  The CTA records {e2, e4, 1 - phi^0, det, |F|^2} (as hi, lo float
-// pairs) and max |F|^2 are summed in a fixed order; thread 0 then forms the
-// energies of Eq. (2.4), the charge of Eq. (2.6) and the virial, rounds them
-// to FP64, applies the arrest rule of Section 4 in FP64 (E_n > E_{n-1}: the
-// velocity is zeroed), scores the prediction the launch ran with, and updates
-// the two-level predictor: the last four decisions select a 2-bit saturating
-// counter.
+// pairs) and max |F|^2 are summed in a fixed order.  Thread 0 then forms the
+// energy of Eq. (2.4), applies the arrest rule of Section 4 in FP64
+// (E_n > E_{n-1}: the velocity is zeroed), scores the prediction the launch
+// ran with, updates the two-level predictor (the last four decisions select a
+// 2-bit saturating counter) and publishes the step; meanwhile thread 32 forms
+// the reported energies, the charge of Eq. (2.6), the virial and the force
+// norms, which nothing in the launch waits for.
 template <int NW, typename Sync>
 __device__ __forceinline__ void finish_lattice(const InstDesc &D, Ctrl *c, int cur, int mode,
                                                int pred, int dry, DF *buf, float *amx, int tid,
-                                               Sync sync, DF *accs = nullptr, float *amaxs = nullptr)
+                                               Sync sync)
 {
     // thread 0 fetches the control fields it needs while the block sums the records
     double E_prev = 0.0;
@@ -747,52 +823,91 @@ __device__ __forceinline__ void finish_lattice(const InstDesc &D, Ctrl *c, int c
         arrests = __ldcg(&c->arrests);
         fixups = __ldcg(&c->fixups);
     }
-    DF v[kSums] = {};
-    float amax = 0.f;
-    for (int i = tid; i < D.cta_count; i += NW * 32) {
-        const float4 *r = reinterpret_cast<const float4 *>(D.parts + (size_t)i * kPartialDoubles);
-        const float4 a = __ldcg(r), b = __ldcg(r + 1), e = __ldcg(r + 2), f = __ldcg(r + 3);
-        v[0] = df_add(v[0], DF{a.x, a.y});
-        v[1] = df_add(v[1], DF{a.z, a.w});
-        v[2] = df_add(v[2], DF{b.x, b.y});
-        v[3] = df_add(v[3], DF{b.z, b.w});
-        v[4] = df_add(v[4], DF{e.x, e.y});
-        v[5] = df_add(v[5], DF{f.x, f.y});
-        amax = fmaxf(amax, e.z);
-    }
     DF t[kSums];
     float tmax = 0.f;
-    if constexpr (NW > kSums && (NW * 32) % 64 == 0) {
-        if (accs) {
-            // the CTA's own sums are already in its record: reuse their slots
+    if constexpr (NW > kSums) {
+        // warp q sums quantity q of every record straight from global memory
+        // (eight independent loads per lane and pass, a pairwise tree, then a
+        // butterfly); warp kSums takes the max
+        const int lane = tid & 31, warp = tid >> 5;
+        // float offsets in a record: e2 0, e4 2, e0 4, det 6, |F|^2 8, e6 12; max 10
+        const int off = warp < 5 ? 2 * warp : (warp == 5 ? 12 : 10);
+        const float *base = reinterpret_cast<const float *>(D.parts) + off;
+        constexpr int kRec = 2 * kPartialDoubles;                 // floats per record
+        if (warp < kSums) {
+            DF acc = {0.f, 0.f};
+            for (int i0 = 0; i0 < D.cta_count; i0 += 256) {
+                DF x[8];
 #pragma unroll
-            for (int q = 0; q < kSums; ++q) accs[q * NW * 32 + tid] = v[q];
-            amaxs[tid] = amax;
-            sync();
-            block_reduce_df_smem<NW * 32>(accs, amaxs, buf, amx, t, tmax, tid);
-        } else {
-            block_reduce_df<NW>(v, amax, buf, amx, t, tmax, tid, sync);
+                for (int k = 0; k < 8; ++k) {
+                    const int i = i0 + lane + 32 * k;
+                    float2 r = make_float2(0.f, 0.f);
+                    if (i < D.cta_count)
+                        r = __ldcg(reinterpret_cast<const float2 *>(base + (size_t)i * kRec));
+                    x[k] = DF{r.x, r.y};
+                }
+                df_tree<8>(x);
+                acc = df_add(acc, x[0]);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc = df_add(acc, df_shfl_xor(acc, o));
+            if (lane == 0) buf[warp] = acc;
+        } else if (warp == kSums) {
+            float m = 0.f;
+            for (int i = lane; i < D.cta_count; i += 32)
+                m = fmaxf(m, __ldcg(base + (size_t)i * kRec));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (lane == 0) *amx = m;
         }
+        sync();
+        if (tid != 0 && tid != 32) return;
+#pragma unroll
+        for (int q = 0; q < kSums; ++q) t[q] = buf[q];
+        tmax = *amx;
     } else {
+        DF v[kSums] = {};
+        float amax = 0.f;
+        for (int i = tid; i < D.cta_count; i += NW * 32) {
+            const float4 *r = reinterpret_cast<const float4 *>(D.parts + (size_t)i * kPartialDoubles);
+            const float4 a = __ldcg(r), b = __ldcg(r + 1), e = __ldcg(r + 2), f = __ldcg(r + 3);
+            v[0] = df_add(v[0], DF{a.x, a.y});
+            v[1] = df_add(v[1], DF{a.z, a.w});
+            v[2] = df_add(v[2], DF{b.x, b.y});
+            v[3] = df_add(v[3], DF{b.z, b.w});
+            v[4] = df_add(v[4], DF{e.x, e.y});
+            v[5] = df_add(v[5], DF{f.x, f.y});
+            amax = fmaxf(amax, e.z);
+        }
         block_reduce_df<NW>(v, amax, buf, amx, t, tmax, tid, sync);
+        if (tid != 0) return;
     }
-    if (tid != 0) return;
+    const bool reporter = NW > kSums ? tid == 32 : tid == 0;
+    const bool decider = tid == 0;
     if (dry) {
-        c->done = 0;
+        if (decider) c->done = 0;
         return;
     }
+    // the sums in lattice units (the step sums unscaled densities)
+    t[0] = df_mul(DF{D.s_e2.x, D.s_e2.y}, t[0]);
+    t[1] = df_mul(DF{D.s_e4.x, D.s_e4.y}, t[1]);
+    t[3] = df_mul(DF{D.s_b.x, D.s_b.y}, t[3]);
+    t[4] = df_mul(DF{D.s_f.x, D.s_f.y}, t[4]);
+    t[5] = df_mul(DF{D.s_e6.x, D.s_e6.y}, t[5]);
+    const double fmax2 = (double)tmax * ((double)D.s_f.x + (double)D.s_f.y);
     constexpr double kB = -0.050660591821168885;  // b = -det / (2 pi^2)
     const DF bfac = {(float)kB, (float)(kB - (double)(float)kB)};
     if (D.slab_rec) {
         // one x-slab of a larger lattice: leave this slab's record for the
         // decision over all slabs, {e2, e4, e0, b, |F|^2, max |F|^2, sites, e6}
+        if (!decider) return;
         double *r = D.slab_rec;
         r[0] = df_value(t[0]);
         r[1] = df_value(t[1]);
         r[2] = df_value(df_mul(DF{D.e0_scale, 0.f}, t[2]));
         r[3] = df_value(df_mul(bfac, t[3]));
         r[4] = df_value(t[4]);
-        r[5] = (double)tmax;
+        r[5] = fmax2;
         r[6] = (double)(D.n0 - 4) * (double)(D.n1 - 4) * (double)(D.n2 - 4);
         r[7] = df_value(t[5]);
         c->done = 0;
@@ -803,44 +918,49 @@ __device__ __forceinline__ void finish_lattice(const InstDesc &D, Ctrl *c, int c
     const DF E0 = df_mul(h3, df_mul(DF{D.e0_scale, 0.f}, t[2]));  // 2 m^2 sum(1 - phi^0), or the potentials' sum
     const DF E6 = df_mul(h3, t[5]);  // the sextic term (zero without it)
     const DF E = df_add(df_add(df_add(E2, E4), E0), E6);
-    const DF B = df_mul(h3, df_mul(bfac, t[3]));
-    // Derrick scaling: -E2 + E4 - 3 E0 + 3 E6
-    const DF V = df_add(df_add(df_add(df_neg(E2), E4), df_mul(DF{-3.f, 0.f}, E0)),
-                        df_mul(DF{3.f, 0.f}, E6));
     const double Ed = df_value(E);
-    const int actual = (mode == MODE_ARRESTED && Ed > E_prev) ? 1 : 0;
-    const int fix = (actual == pred) ? 0 : (actual ? -1 : +1);
-    unsigned char pht[16];
-    memcpy(pht, &pht4, sizeof(pht));
-    const int h = hist & 15;
-    int ctr = pht[h];
-    ctr = actual ? (ctr < 3 ? ctr + 1 : 3) : (ctr > 0 ? ctr - 1 : 0);
-    pht[h] = (unsigned char)ctr;
-    const int hn = ((h << 1) | actual) & 15;
-    c->pht[h] = (unsigned char)ctr;
-    c->hist = hn;
-    c->pred = pht[hn] >= 2 ? 1 : 0;
-    c->fix = fix;
-    c->arrests = arrests + actual;
-    c->fixups = fixups + (fix != 0);
-    c->E_prev = Ed;
-    c->cur = cur ^ 1;
-    const double nsites = (double)(D.n0 - 4) * (double)(D.n1 - 4) * (double)(D.n2 - 4);
-    c->last[0] = Ed;
-    c->last[1] = df_value(E2);
-    c->last[2] = df_value(E4);
-    c->last[3] = df_value(E0);
-    c->last[4] = df_value(B);
-    c->last[5] = df_value(V);
-    c->last[6] = sqrt((double)tmax);
-    c->last[7] = sqrt(df_value(t[4]) / (double)nsites);
-    c->e6_last = df_value(E6);
-    if (!(isfinite(Ed) && isfinite(B.hi) && isfinite(t[4].hi))) c->status = DEV_NONFINITE;
-    c->done = 0;
-    // the step count goes last, after a fence: CTAs that correct their own
-    // sites wait for it, and then see every field above
-    __threadfence();
-    *(volatile long long *)&c->steps = steps + 1;
+    if (decider) {
+        const int actual = (mode == MODE_ARRESTED && Ed > E_prev) ? 1 : 0;
+        const int fix = (actual == pred) ? 0 : (actual ? -1 : +1);
+        // counter i of the 16 is byte i of pht4 (read by shifts, no local copy)
+        auto counter = [&](int i) {
+            const unsigned w = i < 8 ? (i < 4 ? pht4.x : pht4.y) : (i < 12 ? pht4.z : pht4.w);
+            return (int)((w >> (8 * (i & 3))) & 0xffu);
+        };
+        const int h = hist & 15;
+        int ctr = counter(h);
+        ctr = actual ? (ctr < 3 ? ctr + 1 : 3) : (ctr > 0 ? ctr - 1 : 0);
+        const int hn = ((h << 1) | actual) & 15;
+        c->pht[h] = (unsigned char)ctr;
+        c->hist = hn;
+        c->pred = (h == hn ? ctr : counter(hn)) >= 2 ? 1 : 0;
+        c->fix = fix;
+        c->arrests = arrests + actual;
+        c->fixups = fixups + (fix != 0);
+        c->E_prev = Ed;
+        c->cur = cur ^ 1;
+        c->done = 0;
+        // the step count goes last, released: CTAs that correct their own
+        // sites wait for it, and then see every field above
+        st_release_s64(&c->steps, steps + 1);
+    }
+    if (reporter) {
+        const DF B = df_mul(h3, df_mul(bfac, t[3]));
+        // Derrick scaling: -E2 + E4 - 3 E0 + 3 E6
+        const DF V = df_add(df_add(df_add(df_neg(E2), E4), df_mul(DF{-3.f, 0.f}, E0)),
+                            df_mul(DF{3.f, 0.f}, E6));
+        const double nsites = (double)(D.n0 - 4) * (double)(D.n1 - 4) * (double)(D.n2 - 4);
+        c->last[0] = Ed;
+        c->last[1] = df_value(E2);
+        c->last[2] = df_value(E4);
+        c->last[3] = df_value(E0);
+        c->last[4] = df_value(B);
+        c->last[5] = df_value(V);
+        c->last[6] = sqrt(fmax2);
+        c->last[7] = sqrt(df_value(t[4]) / nsites);
+        c->e6_last = df_value(E6);
+        if (!(isfinite(Ed) && isfinite(B.hi) && isfinite(t[4].hi))) c->status = DEV_NONFINITE;
+    }
 }
 
 __device__ __forceinline__ long long ld_acquire_s64(const long long *p)
@@ -915,13 +1035,24 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
                const InstDesc *__restrict__ table, int ninst, long long total_units, int dry)
 {
     constexpr int THREADS = TY * TZ;
+    constexpr int NSLOT = nslot<TY, TZ, SEX>();
     constexpr unsigned PLANE_BYTES = (TY + 4) * (TZ + 4) * 16;
     constexpr unsigned VPLANE_BYTES = TY * TZ * 16;
-    using Smem = StepSmem<TY, TZ>;
+    using Smem = StepSmem<TY, TZ, SEX>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     const int tid = threadIdx.x;
     const int ty = tid / TZ, tz = tid % TZ;
+    // a single lattice's control fields, loaded together ahead of the
+    // prologue (one round trip instead of two dependent ones)
+    int cur0 = 0, pred0 = 0;
+    if constexpr (!BATCHED) {
+        cur0 = __ldcg(&one.ctrl->cur);
+        pred0 = one.mode == MODE_ARRESTED ? __ldcg(&one.ctrl->pred) : 0;
+        // the step count before this step, for the fused correction (kept in
+        // shared memory, out of the main loop's registers)
+        if (one.fuse_fix && tid == 0) sm.steps0 = __ldcg(&one.ctrl->steps);
+    }
 
     if (tid == 0) {
         for (int s = 0; s < NSLOT; ++s) {
@@ -947,9 +1078,6 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
     int inst = 0;
     if (BATCHED)
         while (inst + 1 < ninst && table[inst + 1].unit_start <= u0) ++inst;
-    // single lattice with the fused correction: the step count before this
-    // step (kept in shared memory, out of the main loop's registers)
-    if (!BATCHED && one.fuse_fix && tid == 0) sm.steps0 = __ldcg(&one.ctrl->steps);
     uint32_t g = 0;   // planes consumed by this CTA (ring sequence number)
     uint32_t g3 = 0;  // g % 3, the in-plane record slot of plane g
     bool failed = false;
@@ -960,9 +1088,9 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
         const InstDesc &D = BATCHED ? table[inst] : one;
         const long long seg_hi = min(u1, D.unit_start + D.units);
         Ctrl *ctrl = D.ctrl;
-        const int cur = __ldcg(&ctrl->cur);
+        const int cur = BATCHED ? __ldcg(&ctrl->cur) : cur0;
         if (!BATCHED && tid == 0) sm.cur_used = cur;
-        const int pred = (D.mode == MODE_ARRESTED) ? __ldcg(&ctrl->pred) : 0;
+        const int pred = BATCHED ? ((D.mode == MODE_ARRESTED) ? __ldcg(&ctrl->pred) : 0) : pred0;
         const CUtensorMap *map = &D.map[cur];
         const CUtensorMap *vmap = &D.vmap[cur];
         float4 *__restrict__ phiout = D.phi[cur ^ 1];
@@ -1021,7 +1149,7 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
                     __syncwarp();
                     if (x >= xs)
                         centre_site<TY, TZ, POT, DUMP, SEX>(D, ring[(k + 1) % 5], ring[(k + 2) % 5], ring[(k + 3) % 5],
-                                            ring[(k + 4) % 5], ring[k], D.c1, D.c2,
+                                            ring[(k + 4) % 5], ring[k], D.xm1, D.xm2,
                                             twarp + RECC * g3n,
                                             &sm.vpl[s][ty][tz], use_v,
                                             valid, phiout, vout, (size_t)x * plane_stride + col_off, a32);
@@ -1073,15 +1201,13 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
         }
         if (tid == 0) {
             write_record(D, (int)blockIdx.x - D.cta_first, tot, tmax);
-            __threadfence();
-            sm.last = (atomicAdd(&ctrl->done, 1u) == (unsigned)(D.cta_count - 1));
+            sm.last = (atom_add_acq_rel(&ctrl->done, 1u) == (unsigned)(D.cta_count - 1));
         }
+        // the last CTA's threads read the records after thread 0's acquire
         __syncthreads();
-        if (sm.last) {
-            __threadfence();
+        if (sm.last)
             finish_lattice<THREADS / 32>(D, ctrl, cur, mode, pred, dry, sm.dfred, sm.mxred, tid,
-                                         CtaSync{}, &sm.accs[0][0], sm.amaxs);
-        }
+                                         CtaSync{});
         __syncthreads();
     }
 
@@ -1383,21 +1509,41 @@ static bool fill_desc(InstDesc &d, const skyrme_lattice &lat, const skyrme_state
     d.nzt = (lat.n[2] - 4 + tz - 1) / tz;
     d.nix = lat.n[0] - 4;
     d.units = (long long)nyt * d.nzt * d.nix;
-    const double ih = 1.0 / lat.h, ih2 = ih * ih;
     auto pair = [](double w) { return make_float2((float)w, (float)w); };
-    d.c1 = pair(2.0 / 3.0 * ih);
-    d.c2 = pair(-1.0 / 12.0 * ih);
-    d.s1 = pair(4.0 / 3.0 * ih2);
-    d.s2 = pair(-1.0 / 12.0 * ih2);
-    d.s0 = pair(-2.5 * ih2);
+    auto split = [](double w) {  // (hi, lo) with hi + lo = w to about 48 bits
+        const float hi = (float)w;
+        return make_float2(hi, (float)(w - (double)hi));
+    };
+    // unscaled stencils: u = 12h d phi, N = -12h^2 d^2 phi; the force scale
+    // B = k1^2 k2 with k1 = 1/(12h), k2 = 1/(12h^2)
+    const double k1 = 1.0 / (12.0 * lat.h), k2 = 1.0 / (12.0 * lat.h * lat.h), B = k1 * k1 * k2;
+    d.w8 = pair(8.0);
+    d.wm16 = pair(-16.0);
+    d.w30 = pair(30.0);
+    d.xm1 = pair(-2.0 / 3.0);
+    d.xm2 = pair(1.0 / 12.0);
     d.m2 = (float)(lat.m * lat.m);
+    d.bm2 = (float)(lat.m * lat.m / B);
+    d.negK = (float)(-1.0 / (k1 * k1));
     d.my2 = (float)(lat.m_y * lat.m_y);
     d.mz2 = (float)(lat.m_z * lat.m_z);
     d.mw2 = (float)(lat.m_w * lat.m_w);
+    d.bmy2 = (float)(lat.m_y * lat.m_y / B);
+    d.bmz2 = (float)(lat.m_z * lat.m_z / B);
+    d.bmw2 = (float)(lat.m_w * lat.m_w / B);
     d.e0_scale = pot_sums || lattice_potentials(lat) || lat.c6 != 0.0 ? 1.f : 2.f * d.m2;
     d.c6 = (float)lat.c6;
+    d.c6b = (float)(lat.c6 * k1 * k1);
+    d.dk2 = (float)(k1 * k1);
+    d.dk3 = (float)(k1 * k1 * k1);
+    d.dk4 = (float)(k1 * k1 * k1 * k1);
+    d.s_e2 = split(k1 * k1);
+    d.s_e4 = split(k1 * k1 * k1 * k1);
+    d.s_b = split(k1 * k1 * k1);
+    d.s_e6 = split(k1 * k1 * k1 * k1 * k1 * k1);
+    d.s_f = split(B * B);
     d.dt = make_float2((float)dt, (float)dt);
-    d.dt2 = make_float2(2.f * (float)dt, 2.f * (float)dt);
+    d.dt2 = pair(2.0 * dt * B);
     const double h3 = lat.h * lat.h * lat.h;
     d.h3_hi = (float)h3;
     d.h3_lo = (float)(h3 - (double)d.h3_hi);
@@ -1567,6 +1713,10 @@ cudaError_t launch_iterations_f32_fast(const skyrme_lattice &lat, const FlowArgs
 
     ds[0].slab_rec = a.slab_rec;
     ds[0].dump = static_cast<float4 *>(a.dump);
+    if (a.dump) {
+        // the dump kernels scale each site's densities and sum the scaled values
+        ds[0].s_e2 = ds[0].s_e4 = ds[0].s_b = make_float2(1.f, 0.f);
+    }
     // ARRESTED whole lattices correct their own mispredicted decisions inside
     // the step (the CTAs wait for the last one's decision, so the launch is
     // cooperative: every CTA resident at once); an x-slab's decision and
