@@ -227,29 +227,40 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
 __device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16])
+// Stores and loads of 8, 4 and 1 consecutive columns of this thread's TMEM
+// lane (32x32b shapes).  Loaded values are usable only after a wait, so they
+// pass through the wait's own operands (no use can be scheduled before it).
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float *v)
 {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
-        "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]),
-        "f"(v[9]), "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15])
-        : "memory");
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]) : "memory");
 }
-// Load 16 columns; the values are usable only after the wait, so they pass
-// through the wait's own operands (no use can be scheduled before it).
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const float *v)
 {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]),
-          "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15])
-        : "r"(taddr)
-        : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]),
-                   "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]), "+f"(v[13]), "+f"(v[14]), "+f"(v[15])
-                 :
-                 : "memory");
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]) : "memory");
+}
+__device__ __forceinline__ void tmem_st1(uint32_t taddr, float v)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(taddr), "f"(v) : "memory");
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];" : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]) : "r"(taddr) : "memory");
+}
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float *v)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];" : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]) : "r"(taddr) : "memory");
+}
+__device__ __forceinline__ void tmem_ld1(uint32_t taddr, float &v)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=f"(v) : "r"(taddr) : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld13(float (&v)[13])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]), "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]) : : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld12(float (&v)[12])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]), "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]) : : "memory");
 }
 
 // ------------------------------------------------- packed 4-vector helpers
@@ -595,14 +606,19 @@ __device__ __forceinline__ void plane_record(const float4 (*DY)[TZ + 4], const I
     const P4 qin = fma(bc(2.f * ayz), dyz, fma(bc(azz), dzz, mul(bc(ayy), dyy)));
     const float gyv = hsum(dot2(dyz, dz, __ffma2_rn(dyy.b, dy.b, __fmul2_rn(dyy.a, dy.a))));
     const float gzv = hsum(dot2(dzz, dz, __ffma2_rn(dyz.b, dy.b, __fmul2_rn(dyz.a, dy.a))));
-    const float r[16] = {lin.a.x, lin.a.y, lin.b.x, lin.b.y, qin.a.x, qin.a.y, qin.b.x, qin.b.y,
-                         gyv, gzv, ayy, azz, ayz, 0.f, 0.f, 0.f};
+    // columns 0-7 lin, qin; 8-11 g_y, g_z, a_yy, a_zz; 12 a_yz
+    const float r[12] = {lin.a.x, lin.a.y, lin.b.x, lin.b.y, qin.a.x, qin.a.y, qin.b.x, qin.b.y,
+                         gyv, gzv, ayy, azz};
     (void)THREADS;
-    tmem_st16(trec, r);
+    tmem_st8(trec, r);
+    tmem_st4(trec + 8, r + 8);
+    tmem_st1(trec + 12, ayz);
     if constexpr (SEX) {
-        const float r2[16] = {dyy.a.x, dyy.a.y, dyy.b.x, dyy.b.y, dzz.a.x, dzz.a.y, dzz.b.x, dzz.b.y,
-                              dyz.a.x, dyz.a.y, dyz.b.x, dyz.b.y, 0.f, 0.f, 0.f, 0.f};
-        tmem_st16(trec + 16, r2);
+        // columns 16-27: N_yy, N_zz, N_yz
+        const float r2[12] = {dyy.a.x, dyy.a.y, dyy.b.x, dyy.b.y, dzz.a.x, dzz.a.y, dzz.b.x, dzz.b.y,
+                              dyz.a.x, dyz.a.y, dyz.b.x, dyz.b.y};
+        tmem_st8(trec + 16, r2);
+        tmem_st4(trec + 24, r2 + 8);
     }
 }
 
@@ -623,9 +639,12 @@ __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &
     constexpr int THREADS = TY * TZ;
     const int mode = D.mode;
     const float2 dt = D.dt, dt2 = D.dt2;
-    float rv[16];
+    float rv[13];
     tmem_wait_st();  // this thread's earlier record stores have landed
-    tmem_ld16(trec, rv);
+    tmem_ld8(trec, rv);
+    tmem_ld4(trec + 8, rv + 8);
+    tmem_ld1(trec + 12, rv[12]);
+    tmem_wait_ld13(rv);
 
     const P4 lin = {make_float2(rv[0], rv[1]), make_float2(rv[2], rv[3])};
     const P4 qin = {make_float2(rv[4], rv[5]), make_float2(rv[6], rv[7])};
@@ -677,8 +696,10 @@ __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &
         // (12h)^-3, ^-3, ^-2 and -(12h)^-2 (12h^2)^-1) the bracket is
         // (12h)^-4 (12h^2)^-1 [D P / 3 + sum_i dDn_i Q_i], which enters the
         // brace / B with the weight -c6 / (144 h^2).
-        float rs[16];  // N_yy, N_zz, N_yz of the centre plane
-        tmem_ld16(trec + 16, rs);
+        float rs[12];  // N_yy, N_zz, N_yz of the centre plane
+        tmem_ld8(trec + 16, rs);
+        tmem_ld4(trec + 24, rs + 8);
+        tmem_wait_ld12(rs);
         const float ph4[4] = {ph.a.x, ph.a.y, ph.b.x, ph.b.y};
         const float u4[4] = {dx.a.x, dx.a.y, dx.b.x, dx.b.y};
         const float v4[4] = {dyc.a.x, dyc.a.y, dyc.b.x, dyc.b.y};
