@@ -576,6 +576,7 @@ def run_batched(sk, torch, dev, ws, rank, steps=200):
     return {"value": round(gs, 4), "unit": UNIT, "instances": len(wls),
             "interior_sites": sum(w.interior_sites for w in wls), "steps": reps * chunk,
             "tile": [info["ty"], info["tz"]], "grid": info["grid"],
+            "split": "plane-balanced" if info.get("balanced") else "even by centres",
             "autotune_ms_per_step": round(tune_ms, 4),
             "roofline": {"bound": "hbm", "achieved": round(gs * BYTES_PER_SITE_F32, 1),
                          "peak": hbm, "unit": "GB/s",

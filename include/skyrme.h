@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-#define SKYRME_ABI_VERSION 3
+#define SKYRME_ABI_VERSION 4
 
 typedef enum {
     SKYRME_OK = 0,
@@ -269,12 +269,21 @@ skyrme_status skyrme_graph_create_until(const skyrme_lattice *lat, double dt, in
  *     the lattice table for the default tile shape and uploads it (a
  *     synchronous copy); the handle owns no device memory.
  *   skyrme_batch_step: nsteps iterations, asynchronous.
- *   skyrme_batch_autotune: times every candidate tile shape on these
- *     lattices with `trials` dry steps each (outputs go to the inactive
- *     buffers; the flows do not advance) and keeps the fastest.
+ *   skyrme_batch_autotune: times every candidate tile shape, each with both
+ *     work splits, on these lattices with `trials` dry steps each (outputs
+ *     go to the inactive buffers; the flows do not advance) and keeps the
+ *     fastest pair; best_tile is its tile shape.
  *   skyrme_batch_set_tile / skyrme_batch_tile: choose or query the tile
  *     shape (0: 8x32, 1: 4x32, 2: 16x16, 3: 8x16, 4: 16x32 interior sites per CTA) and
  *     the persistent grid.
+ *   skyrme_batch_set_split / skyrme_batch_split: how the (column, x-plane)
+ *     work of the concatenated lattices is divided among the persistent
+ *     CTAs: balanced = 1 (the default) gives each CTA about the same number
+ *     of streamed planes (a run of r centres streams r + 4), balanced = 0
+ *     the same number of centres.  Results are the same either way (each
+ *     site's arithmetic does not depend on the split; the sums' order
+ *     does).  Both re-encode the table (a synchronous copy): re-capture
+ *     graphs afterwards.
  *   skyrme_batch_graph_create: capture nsteps batched iterations as a
  *     skyrme_graph (launch and destroy it with skyrme_graph_launch /
  *     skyrme_graph_destroy).  Re-capture after changing the tile shape. */
@@ -287,6 +296,8 @@ skyrme_status skyrme_batch_step(skyrme_batch *b, int nsteps, void *stream);
 skyrme_status skyrme_batch_autotune(skyrme_batch *b, int trials, void *stream, int *best_tile,
                                     double *best_ms);
 skyrme_status skyrme_batch_set_tile(skyrme_batch *b, int tile);
+skyrme_status skyrme_batch_set_split(skyrme_batch *b, int balanced);
+skyrme_status skyrme_batch_split(const skyrme_batch *b, int *balanced);
 skyrme_status skyrme_batch_tile(const skyrme_batch *b, int *tile, int *ty, int *tz, int *grid);
 skyrme_status skyrme_batch_graph_create(skyrme_batch *b, int nsteps, void *stream,
                                         skyrme_graph **out);

@@ -123,6 +123,8 @@ _SIGNATURES = {
     "skyrme_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int),
                                              ctypes.POINTER(ctypes.c_double)]),
     "skyrme_batch_set_tile": (ctypes.c_int, [_P, ctypes.c_int]),
+    "skyrme_batch_set_split": (ctypes.c_int, [_P, ctypes.c_int]),
+    "skyrme_batch_split": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "skyrme_batch_tile": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int)]),
@@ -692,11 +694,18 @@ class Batch:
     def set_tile(self, tile: int):
         _check(_on(self.states[0].device).skyrme_batch_set_tile(self._h, int(tile)), "skyrme_batch_set_tile")
 
+    def set_split(self, balanced: bool):
+        """Divide the work among CTAs by streamed planes (True) or by centres."""
+        _check(_on(self.states[0].device).skyrme_batch_set_split(self._h, 1 if balanced else 0),
+               "skyrme_batch_set_split")
+
     def tile(self):
-        t, ty, tz, g = (ctypes.c_int() for _ in range(4))
+        t, ty, tz, g, sp = (ctypes.c_int() for _ in range(5))
         _check(load().skyrme_batch_tile(self._h, ctypes.byref(t), ctypes.byref(ty),
                                         ctypes.byref(tz), ctypes.byref(g)), "skyrme_batch_tile")
-        return {"tile": t.value, "ty": ty.value, "tz": tz.value, "grid": g.value}
+        _check(load().skyrme_batch_split(self._h, ctypes.byref(sp)), "skyrme_batch_split")
+        return {"tile": t.value, "ty": ty.value, "tz": tz.value, "grid": g.value,
+                "balanced": bool(sp.value)}
 
     def reports(self):
         return [read_report(l, st) for l, st in zip(self.lats, self.states)]

@@ -90,18 +90,15 @@ struct InstDesc {
     int n0, n1, n2;
     int nzt, nix;          // column tiles along z, interior planes along x
     int cta_first, cta_count;
-    // Stencil weights and time steps as (w, w) pairs: the packed FP32
-    // instructions take them as one 64-bit operand.  The kernels carry the
-    // derivatives without their 1/(12h), 1/(12h^2) factors: u_i = 12h d_i phi
-    // = 8 (p1 - m1) - (p2 - m2), and every second derivative negated on one
-    // scale, N_ij = -12h^2 d_ij phi: the pure ones as (p2 + m2) + 30 c -
-    // 16 (p1 + m1), the mixed ones as -(2/3)(p1 - m1) + (1/12)(p2 - m2) of
-    // the u_i.  The force then comes out as F / B, B = 1/(1728 h^4); B moves
-    // into the time step and the mass terms, and the sums are scaled in the
-    // finish.
-    float2 w8;             // (8, 8)
-    float2 wm16, w30;      // (-16, -16), (30, 30)
-    float2 xm1, xm2;       // (-2/3, -2/3), (1/12, 1/12)
+    // Time steps as (w, w) pairs: the packed FP32 instructions take them as
+    // one 64-bit operand.  The kernels carry the derivatives without their
+    // 1/(12h), 1/(12h^2) factors: u_i = 12h d_i phi = 8 (p1 - m1) - (p2 - m2),
+    // and every second derivative negated on one scale, N_ij = -12h^2 d_ij phi:
+    // the pure ones as (p2 + m2) + 30 c - 16 (p1 + m1), the mixed ones as
+    // -(2/3)(p1 - m1) + (1/12)(p2 - m2) of the u_i (weights the same for every
+    // lattice: kW8 ... kXm2).  The force then comes out as F / B,
+    // B = 1/(1728 h^4); B moves into the time step and the mass terms, and
+    // the sums are scaled in the finish.
     float2 dt, dt2;        // dt and 2 dt B
     float m2;              // m^2 (potential energy density)
     float bm2;             // m^2 / B (its force term)
@@ -290,6 +287,16 @@ __device__ __forceinline__ float dot(const P4 &u, const P4 &v)
 {
     return hsum(__ffma2_rn(u.b, v.b, __fmul2_rn(u.a, v.a)));
 }
+// The unscaled stencils' weights, the same for every lattice (compile-time
+// constants: the compiler takes them from its constant bank instead of
+// registers, which matters in the batched kernels, whose lattice
+// descriptors live in global memory)
+__device__ __forceinline__ float2 kW8() { return make_float2(8.f, 8.f); }
+__device__ __forceinline__ float2 kWm16() { return make_float2(-16.f, -16.f); }
+__device__ __forceinline__ float2 kW30() { return make_float2(30.f, 30.f); }
+__device__ __forceinline__ float2 kXm1() { return make_float2(-2.f / 3.f, -2.f / 3.f); }
+__device__ __forceinline__ float2 kXm2() { return make_float2(1.f / 12.f, 1.f / 12.f); }
+
 // weighted first difference c1 (p1 - m1) + c2 (p2 - m2) (the mixed second
 // derivatives, of the u_i)
 __device__ __forceinline__ P4 fd1(const P4 &m2, const P4 &m1, const P4 &p1, const P4 &p2, float2 c1,
@@ -561,7 +568,7 @@ __device__ __forceinline__ void arrive_plane(const float4 (*P)[TZ + 4], float4 (
                                              const InstDesc &D, int tid, int ty, int tz,
                                              PlaneVals &rv, P4 &dyy, P4 &dzz)
 {
-    const float2 w8 = D.w8, wm16 = D.wm16, w30 = D.w30;
+    const float2 w8 = kW8(), wm16 = kWm16(), w30 = kW30();
     const P4 c = ld4(P[ty + 2][tz + 2]);
     const P4 ym2 = ld4(P[ty][tz + 2]), ym1 = ld4(P[ty + 1][tz + 2]);
     const P4 yp1 = ld4(P[ty + 3][tz + 2]), yp2 = ld4(P[ty + 4][tz + 2]);
@@ -600,7 +607,7 @@ __device__ __forceinline__ void plane_record(const float4 (*DY)[TZ + 4], const I
     constexpr int THREADS = TY * TZ;
     const P4 dy = rv.dy, dz = rv.dz;
     const P4 dyz = fd1(ld4(DY[ty][tz]), ld4(DY[ty][tz + 1]), ld4(DY[ty][tz + 3]), ld4(DY[ty][tz + 4]),
-                       D.xm1, D.xm2);
+                       kXm1(), kXm2());
     const float ayy = dot(dy, dy), azz = dot(dz, dz), ayz = dot(dy, dz);
     const P4 lin = add(dyy, dzz);
     const P4 qin = fma(bc(2.f * ayz), dyz, fma(bc(azz), dzz, mul(bc(ayy), dyy)));
@@ -654,8 +661,8 @@ __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &
     const P4 ph = C.phi;
     // u_x and the negated second derivatives N_xx, N_xy, N_xz (the scales
     // are those of the descriptor's stencil weights)
-    const P4 dx = fd1u(M2.phi, M1.phi, Q1.phi, Q2.phi, D.w8);
-    const P4 dxx = fd2n(M2.phi, M1.phi, ph, Q1.phi, Q2.phi, D.wm16, D.w30);
+    const P4 dx = fd1u(M2.phi, M1.phi, Q1.phi, Q2.phi, kW8());
+    const P4 dxx = fd2n(M2.phi, M1.phi, ph, Q1.phi, Q2.phi, kWm16(), kW30());
     const P4 dxy = fd1(M2.dy, M1.dy, Q1.dy, Q2.dy, xc1, xc2);
     const P4 dxz = fd1(M2.dz, M1.dz, Q1.dz, Q2.dz, xc1, xc2);
     const P4 dyc = C.dy, dzc = C.dz;
@@ -1092,10 +1099,18 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
     const uint32_t twarp = sm.tmem + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) +
                            (uint32_t)(tmem_cols_per_warp<SEX>() * ((tid >> 5) >> 2));
 
+    // unit ranges: a single lattice's listed in the parameter; a batch's,
+    // when balanced (split.n < 0), in device memory right after its table;
+    // else the even split
     const bool listed = !BATCHED && split.n > 0;
-    const long long u0 = listed ? split.start[blockIdx.x] : total_units * blockIdx.x / gridDim.x;
-    const long long u1 =
-        listed ? split.start[blockIdx.x + 1] : total_units * (blockIdx.x + 1) / gridDim.x;
+    const int *bstart = reinterpret_cast<const int *>(table + ninst);
+    const bool blisted = BATCHED && split.n < 0;
+    const long long u0 = listed ? split.start[blockIdx.x]
+                         : blisted ? bstart[blockIdx.x]
+                                   : total_units * blockIdx.x / gridDim.x;
+    const long long u1 = listed ? split.start[blockIdx.x + 1]
+                         : blisted ? bstart[blockIdx.x + 1]
+                                   : total_units * (blockIdx.x + 1) / gridDim.x;
     int inst = 0;
     if (BATCHED)
         while (inst + 1 < ninst && table[inst + 1].unit_start <= u0) ++inst;
@@ -1170,7 +1185,7 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
                     __syncwarp();
                     if (x >= xs)
                         centre_site<TY, TZ, POT, DUMP, SEX>(D, ring[(k + 1) % 5], ring[(k + 2) % 5], ring[(k + 3) % 5],
-                                            ring[(k + 4) % 5], ring[k], D.xm1, D.xm2,
+                                            ring[(k + 4) % 5], ring[k], kXm1(), kXm2(),
                                             twarp + RECC * g3n,
                                             &sm.vpl[s][ty][tz], use_v,
                                             valid, phiout, vout, (size_t)x * plane_stride + col_off, a32);
@@ -1538,11 +1553,6 @@ static bool fill_desc(InstDesc &d, const skyrme_lattice &lat, const skyrme_state
     // unscaled stencils: u = 12h d phi, N = -12h^2 d^2 phi; the force scale
     // B = k1^2 k2 with k1 = 1/(12h), k2 = 1/(12h^2)
     const double k1 = 1.0 / (12.0 * lat.h), k2 = 1.0 / (12.0 * lat.h * lat.h), B = k1 * k1 * k2;
-    d.w8 = pair(8.0);
-    d.wm16 = pair(-16.0);
-    d.w30 = pair(30.0);
-    d.xm1 = pair(-2.0 / 3.0);
-    d.xm2 = pair(1.0 / 12.0);
     d.m2 = (float)(lat.m * lat.m);
     d.bm2 = (float)(lat.m * lat.m / B);
     d.negK = (float)(-1.0 / (k1 * k1));
@@ -1574,7 +1584,8 @@ static bool fill_desc(InstDesc &d, const skyrme_lattice &lat, const skyrme_state
 
 // Split total units over `grid` CTAs and record, for each lattice, the CTAs
 // that touch it; partial records are laid out lattice after lattice.
-static void partition(std::vector<InstDesc> &ds, int grid, double *parts)
+static void partition(std::vector<InstDesc> &ds, int grid, double *parts,
+                      const int *starts = nullptr)
 {
     long long total = 0;
     for (auto &d : ds) {
@@ -1586,7 +1597,8 @@ static void partition(std::vector<InstDesc> &ds, int grid, double *parts)
         const long long lo = d.unit_start, hi = d.unit_start + d.units;
         int first = -1, count = 0;
         for (int b = 0; b < grid; ++b) {
-            const long long b0 = total * b / grid, b1 = total * (b + 1) / grid;
+            const long long b0 = starts ? starts[b] : total * b / grid;
+            const long long b1 = starts ? starts[b + 1] : total * (b + 1) / grid;
             if (b1 > lo && b0 < hi) {
                 if (first < 0) first = b;
                 ++count;
@@ -1688,6 +1700,57 @@ static bool balanced_split(long long units, int nix, int grid, CtaSplit &out)
     return out.n > 0;
 }
 
+// The same cover for a batch: the lattices' columns concatenated, each
+// lattice with its own column length (interior planes).
+static int greedy_split_batch(const std::vector<InstDesc> &ds, long long units, double cap,
+                              int max_ctas, int *start)
+{
+    long long pos = 0;
+    int b = 0;
+    size_t i = 0;
+    while (pos < units) {
+        if (b >= max_ctas) return 0x7fffffff;
+        start[b++] = (int)pos;
+        double budget = cap;
+        bool first = true;
+        while (pos < units) {
+            while (pos >= ds[i].unit_start + ds[i].units) ++i;
+            const long long nix = ds[i].nix;
+            const long long col_end = ds[i].unit_start + ((pos - ds[i].unit_start) / nix + 1) * nix;
+            long long take = (long long)(budget - kRunFill);
+            if (first) take = std::max(take, 1LL);
+            take = std::min(take, col_end - pos);
+            if (take <= 0) break;
+            pos += take;
+            budget -= (double)(kRunFill + take);
+            first = false;
+            if (pos < col_end) break;
+        }
+    }
+    start[b] = (int)pos;
+    return b;
+}
+
+// Unit ranges of at most `grid` CTAs over a batch whose largest plane count
+// is as small as the greedy cover allows; the number of ranges, or 0.
+// ds[].unit_start must be set.
+static int balanced_split_batch(const std::vector<InstDesc> &ds, int grid, std::vector<int> &start)
+{
+    const long long units = total_units(ds);
+    start.assign((size_t)grid + 1, 0);
+    if (grid <= 0 || units > 0x7fffffffLL || units < grid) return 0;
+    long long maxnix = 1;
+    for (auto &d : ds) maxnix = std::max<long long>(maxnix, d.nix);
+    double lo = (double)units / grid, hi = (double)units / grid + 2.0 * kRunFill + (double)maxnix;
+    for (int it = 0; it < 48; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (greedy_split_batch(ds, units, mid, grid, start.data()) <= grid) hi = mid;
+        else lo = mid;
+    }
+    const int n = greedy_split_batch(ds, units, hi, grid, start.data());
+    return n <= grid ? n : 0;
+}
+
 // Self-test of the bounded wait the step kernels use on their TMA copies:
 // thread 0 waits on a shared-memory mbarrier that nothing ever completes,
 // gives up after limit_ns, and records SKYRME_ETIMEOUT in the control block,
@@ -1730,7 +1793,7 @@ cudaError_t launch_iterations_f32_fast(const skyrme_lattice &lat, const FlowArgs
     int grid = grid_for(tile, false, ds[0].units);
     CtaSplit split;
     if (balanced_split(ds[0].units, ds[0].nix, grid, split)) grid = split.n;
-    partition(ds, grid, a.step_parts);
+    partition(ds, grid, a.step_parts, split.n > 0 ? split.start : nullptr);
 
     ds[0].slab_rec = a.slab_rec;
     ds[0].dump = static_cast<float4 *>(a.dump);
@@ -1827,16 +1890,22 @@ struct skyrme_batch {
     double *d_parts = nullptr;
     int fixup_blocks = 1;
     bool pot = false;  // some lattice has a Section 7.8 potential: the POT kernels
+    int split = 1;     // CTA ranges balanced by streamed planes (1) or even by units (0)
 };
 
-static size_t table_bytes(int ninst) { return ((size_t)ninst * sizeof(InstDesc) + 255) & ~(size_t)255; }
+// The lattice table, followed by the CTAs' unit ranges of a balanced split
+static size_t table_bytes(int ninst)
+{
+    return ((size_t)ninst * sizeof(InstDesc) + (kMaxGrid + 1) * sizeof(int) + 255) & ~(size_t)255;
+}
 static size_t batch_parts_bytes(int ninst)
 {
     return ((size_t)(kMaxGrid + ninst) * kPartialDoubles * sizeof(double) + 255) & ~(size_t)255;
 }
 
-// Encode the lattice table for tile shape `tile` and upload it.
-static skyrme_status upload_table(skyrme_batch *b, int tile)
+// Encode the lattice table for tile shape `tile` and split mode `split` and
+// upload it (with the CTAs' unit ranges when the split is balanced).
+static skyrme_status upload_table(skyrme_batch *b, int tile, int split)
 {
     std::vector<InstDesc> ds(b->ninst);
     for (int i = 0; i < b->ninst; ++i) {
@@ -1845,12 +1914,24 @@ static skyrme_status upload_table(skyrme_batch *b, int tile)
             return SKYRME_EINVAL;
     }
     const long long units = total_units(ds);
-    const int grid = grid_for(tile, true, units);
-    partition(ds, grid, b->d_parts);
-    if (cudaMemcpy(b->d_table, ds.data(), ds.size() * sizeof(InstDesc), cudaMemcpyHostToDevice) !=
-        cudaSuccess)
+    int grid = grid_for(tile, true, units);
+    long long pos = 0;
+    for (auto &d : ds) {
+        d.unit_start = pos;
+        pos += d.units;
+    }
+    std::vector<int> starts;
+    const int n = split ? balanced_split_batch(ds, grid, starts) : 0;
+    if (n > 0) grid = n;
+    partition(ds, grid, b->d_parts, n > 0 ? starts.data() : nullptr);
+    const size_t tb = ds.size() * sizeof(InstDesc);
+    std::vector<unsigned char> host(tb + (n > 0 ? (size_t)(n + 1) * sizeof(int) : 0));
+    memcpy(host.data(), ds.data(), tb);
+    if (n > 0) memcpy(host.data() + tb, starts.data(), (size_t)(n + 1) * sizeof(int));
+    if (cudaMemcpy(b->d_table, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return SKYRME_ECUDA;
     b->tile = tile;
+    b->split = n > 0 ? 1 : 0;
     b->grid = grid;
     b->units = units;
     return SKYRME_OK;
@@ -1860,12 +1941,15 @@ static skyrme_status batch_launch(skyrme_batch *b, int nsteps, int dry, cudaStre
 {
     InstDesc dummy;
     memset(&dummy, 0, sizeof(dummy));
+    // split.n = -1: the ranges follow the table in device memory
+    static const CtaSplit kBatchListed = {-1, {}};
+    const CtaSplit &sp = b->split ? kBatchListed : kEvenSplit;
     for (int k = 0; k < nsteps; ++k) {
         const cudaError_t e =
-            b->pot ? launch_tile<true, true>(b->tile, dummy, kEvenSplit, b->d_table, b->ninst,
-                                             b->units, b->grid, dry, s)
-                   : launch_tile<true>(b->tile, dummy, kEvenSplit, b->d_table, b->ninst, b->units,
-                                       b->grid, dry, s);
+            b->pot ? launch_tile<true, true>(b->tile, dummy, sp, b->d_table, b->ninst, b->units,
+                                             b->grid, dry, s)
+                   : launch_tile<true>(b->tile, dummy, sp, b->d_table, b->ninst, b->units, b->grid,
+                                       dry, s);
         if (e != cudaSuccess) return SKYRME_ECUDA;
         if (!dry && b->mode == MODE_ARRESTED) {
             k_fixup_batch<<<(unsigned)b->fixup_blocks, 512, 0, s>>>(b->d_table, b->ninst);
@@ -1932,7 +2016,7 @@ skyrme_status skyrme_batch_create(int ninst, const skyrme_lattice *lats, skyrme_
     b->dt.assign(dt, dt + ninst);
     b->d_table = static_cast<InstDesc *>(scratch);
     b->d_parts = reinterpret_cast<double *>(static_cast<char *>(scratch) + table_bytes(ninst));
-    skyrme_status rc = upload_table(b, 0);
+    skyrme_status rc = upload_table(b, 0, 1);
     if (rc != SKYRME_OK) {
         delete b;
         return rc;
@@ -1950,7 +2034,20 @@ skyrme_status skyrme_batch_step(skyrme_batch *b, int nsteps, void *stream)
 skyrme_status skyrme_batch_set_tile(skyrme_batch *b, int tile)
 {
     if (!b || tile < 0 || tile >= kNumTiles) return SKYRME_EINVAL;
-    return upload_table(b, tile);
+    return upload_table(b, tile, b->split);
+}
+
+skyrme_status skyrme_batch_set_split(skyrme_batch *b, int balanced)
+{
+    if (!b || (balanced != 0 && balanced != 1)) return SKYRME_EINVAL;
+    return upload_table(b, b->tile, balanced);
+}
+
+skyrme_status skyrme_batch_split(const skyrme_batch *b, int *balanced)
+{
+    if (!b || !balanced) return SKYRME_EINVAL;
+    *balanced = b->split;
+    return SKYRME_OK;
 }
 
 skyrme_status skyrme_batch_autotune(skyrme_batch *b, int trials, void *stream, int *best_tile,
@@ -1964,12 +2061,15 @@ skyrme_status skyrme_batch_autotune(skyrme_batch *b, int trials, void *stream, i
         cudaEventDestroy(e0);
         return SKYRME_ECUDA;
     }
-    int best = -1;
+    int best = -1, best_split = 1;
     float best_t = 0.f;
     skyrme_status rc = SKYRME_OK;
-    for (int t = 0; t < kNumTiles && rc == SKYRME_OK; ++t) {
-        rc = upload_table(b, t);
+    // every tile shape, each with the even and the plane-balanced split
+    for (int c = 0; c < 2 * kNumTiles && rc == SKYRME_OK; ++c) {
+        const int t = c / 2, sp = c % 2;
+        rc = upload_table(b, t, sp);
         if (rc != SKYRME_OK) break;
+        if (sp && !b->split) continue;  // no balanced cover for this geometry
         rc = batch_launch(b, 1, 1, s);  // warm-up (dry: the flow does not advance)
         if (rc != SKYRME_OK) break;
         cudaEventRecord(e0, s);
@@ -1981,13 +2081,14 @@ skyrme_status skyrme_batch_autotune(skyrme_batch *b, int trials, void *stream, i
         ms /= (float)trials;
         if (rc == SKYRME_OK && (best < 0 || ms < best_t)) {
             best = t;
+            best_split = sp;
             best_t = ms;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != SKYRME_OK) return rc;
-    rc = upload_table(b, best);
+    rc = upload_table(b, best, best_split);
     if (rc != SKYRME_OK) return rc;
     if (best_tile) *best_tile = best;
     if (best_ms) *best_ms = best_t;

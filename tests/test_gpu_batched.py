@@ -136,6 +136,34 @@ def test_every_tile_shape_gives_the_same_flow(tile):
     r.close()
 
 
+@pytest.mark.parametrize("tile", [0, 4])
+def test_balanced_and_even_splits_give_the_same_fields(tile):
+    """The plane-balanced division of a batch's work among CTAs changes which
+    CTA updates a site, not the site's arithmetic: the fields agree bit for
+    bit with the even split's, the energies to the rounding of the sums'
+    order."""
+    lats, states = make_states(kind="noise")
+    ref_lats, refs = make_states(kind="noise")
+    b = sk.Batch(lats, states, [0.0075] * len(lats))
+    b.set_tile(tile)
+    b.set_split(True)
+    assert b.tile()["balanced"]
+    r = sk.Batch(ref_lats, refs, [0.0075] * len(lats))
+    r.set_tile(tile)
+    r.set_split(False)
+    assert not r.tile()["balanced"]
+    b.step(12)
+    r.step(12)
+    torch.cuda.synchronize()
+    for lat, a, c in zip(lats, states, refs):
+        ra, rc = sk.read_report(lat, a), sk.read_report(lat, c)
+        assert ra["arrests"] == rc["arrests"] and ra["status"] == rc["status"] == 0
+        assert ra["E"] == pytest.approx(rc["E"], rel=1e-12)
+        assert torch.equal(a.field(), c.field())
+    b.close()
+    r.close()
+
+
 def test_autotune_is_dry_and_picks_a_tile():
     lats, states = make_states()
     b = sk.Batch(lats, states, [0.01] * len(lats))
