@@ -204,10 +204,19 @@ __device__ __forceinline__ void tma_plane(void *dst, const CUtensorMap *map,
 // One in-plane record: 16 columns (13 values used), or 32 (25 used) in the
 // sextic kernels, which also carry d_yy, d_zz and d_yz phi to the centre.
 template <bool SEX> constexpr int rec_cols() { return SEX ? 32 : 16; }
-template <bool SEX> constexpr int tmem_cols_per_warp() { return 3 * rec_cols<SEX>(); }  // 3 in flight
+// the sextic variant also keeps the d_z phi part of its x-ring (5 planes of
+// 4 values) in tensor memory, after its 3 records, for the registers; its
+// warps' column ranges are padded to 128 (4 warps share a lane quarter: 512)
+// so that every record starts on a 32-column boundary
+constexpr int kDzCol = 3 * 32;
+template <bool SEX> constexpr int tmem_cols_per_warp()
+{
+    return SEX ? 128 : 3 * rec_cols<SEX>();  // 3 records in flight (+ the d_z ring)
+}
 template <int NW, bool SEX = false> constexpr uint32_t tmem_cols()
 {
     constexpr int need = ((NW + 3) / 4) * tmem_cols_per_warp<SEX>();
+    static_assert(need <= 512, "the warps' TMEM columns exceed the SM's 512");
     return need <= 32 ? 32 : need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
 }
 __device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, uint32_t ncols)
@@ -254,6 +263,10 @@ __device__ __forceinline__ void tmem_ld1(uint32_t taddr, float &v)
 __device__ __forceinline__ void tmem_wait_ld13(float (&v)[13])
 {
     asm volatile("tcgen05.wait::ld.sync.aligned;" : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]), "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]) : : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld16(float (&v)[16])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]), "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]), "+f"(v[13]), "+f"(v[14]), "+f"(v[15]) : : "memory");
 }
 __device__ __forceinline__ void tmem_wait_ld12(float (&v)[12])
 {
@@ -638,7 +651,7 @@ template <int TY, int TZ, bool POT = false, bool DUMP = false, bool SEX = false>
 __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &M2,
                                             const PlaneVals &M1, const PlaneVals &C,
                                             const PlaneVals &Q1, const PlaneVals &Q2, float2 xc1,
-                                            float2 xc2, uint32_t trec,
+                                            float2 xc2, uint32_t trec, uint4 tdz,
                                             const float4 *vp,
                                             bool use_v, bool valid, float4 *phiout, float4 *vout,
                                             size_t si, Acc &a32)
@@ -651,7 +664,21 @@ __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &
     tmem_ld8(trec, rv);
     tmem_ld4(trec + 8, rv + 8);
     tmem_ld1(trec + 12, rv[12]);
+    // the sextic variant's d_z phi of M2, M1, C, Q1 (tdz: their columns)
+    float zv[16];
+    if constexpr (SEX) {
+        tmem_ld4(tdz.x, zv);
+        tmem_ld4(tdz.y, zv + 4);
+        tmem_ld4(tdz.z, zv + 8);
+        tmem_ld4(tdz.w, zv + 12);
+    }
     tmem_wait_ld13(rv);
+    if constexpr (SEX) tmem_wait_ld16(zv);
+    auto zp4 = [&](int i) -> P4 {
+        return {make_float2(zv[4 * i], zv[4 * i + 1]), make_float2(zv[4 * i + 2], zv[4 * i + 3])};
+    };
+    const P4 zM2 = SEX ? zp4(0) : M2.dz, zM1 = SEX ? zp4(1) : M1.dz;
+    const P4 zC = SEX ? zp4(2) : C.dz, zQ1 = SEX ? zp4(3) : Q1.dz;
 
     const P4 lin = {make_float2(rv[0], rv[1]), make_float2(rv[2], rv[3])};
     const P4 qin = {make_float2(rv[4], rv[5]), make_float2(rv[6], rv[7])};
@@ -664,8 +691,8 @@ __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &
     const P4 dx = fd1u(M2.phi, M1.phi, Q1.phi, Q2.phi, kW8());
     const P4 dxx = fd2n(M2.phi, M1.phi, ph, Q1.phi, Q2.phi, kWm16(), kW30());
     const P4 dxy = fd1(M2.dy, M1.dy, Q1.dy, Q2.dy, xc1, xc2);
-    const P4 dxz = fd1(M2.dz, M1.dz, Q1.dz, Q2.dz, xc1, xc2);
-    const P4 dyc = C.dy, dzc = C.dz;
+    const P4 dxz = fd1(zM2, zM1, zQ1, Q2.dz, xc1, xc2);
+    const P4 dyc = C.dy, dzc = zC;
     const float axx = dot(dx, dx), axy = dot(dx, dyc), axz = dot(dx, dzc);
     const float tra = axx + Cayy + Cazz;
     const P4 L = add(dxx, lin);  // -12h^2 Laplacian phi
@@ -1187,6 +1214,10 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
                         centre_site<TY, TZ, POT, DUMP, SEX>(D, ring[(k + 1) % 5], ring[(k + 2) % 5], ring[(k + 3) % 5],
                                             ring[(k + 4) % 5], ring[k], kXm1(), kXm2(),
                                             twarp + RECC * g3n,
+                                            make_uint4(twarp + kDzCol + 4 * ((k + 1) % 5),
+                                                       twarp + kDzCol + 4 * ((k + 2) % 5),
+                                                       twarp + kDzCol + 4 * ((k + 3) % 5),
+                                                       twarp + kDzCol + 4 * ((k + 4) % 5)),
                                             &sm.vpl[s][ty][tz], use_v,
                                             valid, phiout, vout, (size_t)x * plane_stride + col_off, a32);
                     // this warp is done with slot s; the last warp to leave it streams
@@ -1208,6 +1239,10 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
                         break;
                     }
                     plane_record<TY, TZ, SEX>(DY, D, ty, tz, ring[k], dyy, dzz, twarp + RECC * g3);
+                    if constexpr (SEX) {
+                        const float zr[4] = {ring[k].dz.a.x, ring[k].dz.a.y, ring[k].dz.b.x, ring[k].dz.b.y};
+                        tmem_st4(twarp + kDzCol + 4 * k, zr);
+                    }
                     ++g;
                     g3 = g3n;
                 }
