@@ -597,25 +597,34 @@ def run_e2e(sk, torch, dev, wl, K):
     host_in.copy_(st.phi[0])
     host_out = torch.empty_like(host_in, pin_memory=True)
     stream = torch.cuda.current_stream(dev)
-    torch.cuda.synchronize(dev)
-    a = torch.cuda.Event(enable_timing=True)
-    b = torch.cuda.Event(enable_timing=True)
-    t_wall = time.perf_counter()
-    a.record(stream)
-    st.phi[0].copy_(host_in, non_blocking=True)
-    sk.load_field(lat, st, st.phi[0])
-    rep = sk.flow_step(lat, wl.dt, K, sk.ARRESTED, st, report=True)
-    host_out.copy_(st.phi[rep["cur"]], non_blocking=True)
-    b.record(stream)
-    torch.cuda.synchronize(dev)
-    wall = time.perf_counter() - t_wall
-    ms = a.elapsed_time(b)
+
+    def job():
+        """One job: every byte of its input and output crosses the host link
+        inside the timed region."""
+        torch.cuda.synchronize(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        t_wall = time.perf_counter()
+        a.record(stream)
+        st.phi[0].copy_(host_in, non_blocking=True)
+        sk.load_field(lat, st, st.phi[0])
+        rep = sk.flow_step(lat, wl.dt, K, sk.ARRESTED, st, report=True)
+        host_out.copy_(st.phi[rep["cur"]], non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b), time.perf_counter() - t_wall
+
+    job()  # warm-up: the first call of a lattice encodes its tensor maps and kernel attributes
+    runs = [job() for _ in range(3)]
+    ms, wall = sorted(runs)[1]
     bytes_field = host_in.numel() * host_in.element_size()
     return {"value": round(wl.interior_sites * K / (ms * 1e-3) / 1e9, 4), "unit": UNIT,
             "h2d_bytes_per_step": bytes_field / K,
             "d2h_bytes_per_step": (bytes_field + 128) / K,
             "wall_s": round(wall, 4),
-            "what": f"one job of {K} iterations: seed upload, flow, report and field download"}
+            "jobs_ms": [round(r[0], 4) for r in runs],
+            "what": f"the median of 3 jobs (after one untimed) of {K} iterations each: seed upload, "
+                    "flow, report and field download"}
 
 
 def run_fp64_compare(sk, torch, dev, wl, nsteps, rep32, fp64_tflops):
