@@ -1808,10 +1808,11 @@ cudaError_t launch_wait_selftest(void *ctrl, unsigned long long limit_ns, cudaSt
     return cudaGetLastError();
 }
 
-// nsteps iterations of a single lattice: the step kernel and, in ARRESTED
-// mode, the fix-up check.  The tensor maps, the work split and the fix-up
-// descriptor are the same for every iteration, so they are prepared once per
-// call; the loop only launches.
+// nsteps iterations of a single lattice: one step launch each (a whole
+// lattice in ARRESTED mode corrects its own mispredicted decisions inside
+// it; an x-slab's correction follows the decision over all slabs).  The
+// tensor maps and the work split are the same for every iteration, so they
+// are prepared once per call; the loop only launches.
 cudaError_t launch_iterations_f32_fast(const skyrme_lattice &lat, const FlowArgs &a, int nsteps,
                                        cudaStream_t s)
 {
