@@ -21,6 +21,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -213,16 +214,24 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ our kernels
+def source_code_only(text: str) -> str:
+    """C/CUDA source without its comments and with whitespace runs collapsed
+    (the sources hashed here hold no comment markers inside string literals)."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_fingerprint(kernel_key: str):
-    """Hash of the sources of a step kernel: the FP32 streaming kernel
-    (keys step_f32_*) or the tile kernels (every other key), with their
-    shared header."""
+    """Hash of the code of a step kernel's sources: the FP32 streaming
+    kernel (keys step_f32_*) or the tile kernels (every other key), with
+    their shared header; comments and layout do not count."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2604_25876_gb300", "csrc")
     src = "flow_f32.cu" if kernel_key.startswith("step_f32_") else "flow_generic.cu"
     for name in (src, "skyrme_device.cuh"):
-        with open(os.path.join(csrc, name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(csrc, name), encoding="utf-8") as f:
+            h.update(source_code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -89,3 +89,10 @@ def test_workload_config_names_the_workload_and_the_l2_rule():
     cfg = bench.workload_config(workloads.b4_lightly_bound_128())
     assert cfg["m_w"] == 1.0 and cfg["c6"] == 0.0
     assert "smaller than L2" in bench.l2_note(workloads.b1_hedgehog_48())
+
+
+def test_fingerprints_ignore_comments_and_layout_but_not_code():
+    code = "int f(int a) {\n    return a + 1;  // one more\n}\n"
+    assert bench.source_code_only(code) == bench.source_code_only(
+        "/* a block\n comment */ int f(int a)\n{ return a + 1; }")
+    assert bench.source_code_only(code) != bench.source_code_only(code.replace("+ 1", "+ 2"))
