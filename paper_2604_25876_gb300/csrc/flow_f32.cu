@@ -1098,16 +1098,10 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     const int tid = threadIdx.x;
     const int ty = tid / TZ, tz = tid % TZ;
-    // a single lattice's control fields, loaded together ahead of the
-    // prologue (one round trip instead of two dependent ones)
+    // a single lattice's next step may start its prologue as soon as an SM
+    // frees up (its grid-dependency wait below keeps it off this step's data)
+    if constexpr (!BATCHED) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     int cur0 = 0, pred0 = 0;
-    if constexpr (!BATCHED) {
-        cur0 = __ldcg(&one.ctrl->cur);
-        pred0 = one.mode == MODE_ARRESTED ? __ldcg(&one.ctrl->pred) : 0;
-        // the step count before this step, for the fused correction (kept in
-        // shared memory, out of the main loop's registers)
-        if (one.fuse_fix && tid == 0) sm.steps0 = __ldcg(&one.ctrl->steps);
-    }
 
     if (tid == 0) {
         for (int s = 0; s < NSLOT; ++s) {
@@ -1123,6 +1117,16 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
     tmem_fence_before();
     __syncthreads();
     tmem_fence_after();
+    if constexpr (!BATCHED) {
+        // the previous launch (its field, velocity and control block) is
+        // complete and visible from here on
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        cur0 = __ldcg(&one.ctrl->cur);
+        pred0 = one.mode == MODE_ARRESTED ? __ldcg(&one.ctrl->pred) : 0;
+        // the step count before this step, for the fused correction (kept in
+        // shared memory, out of the main loop's registers)
+        if (one.fuse_fix && tid == 0) sm.steps0 = __ldcg(&one.ctrl->steps);
+    }
     const uint32_t twarp = sm.tmem + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) +
                            (uint32_t)(tmem_cols_per_warp<SEX>() * ((tid >> 5) >> 2));
 
@@ -1873,16 +1877,18 @@ cudaError_t launch_iterations_f32_fast(const skyrme_lattice &lat, const FlowArgs
     long long units = ds[0].units;
     void *args[] = {(void *)&ds[0], (void *)&split, (void *)&tab, (void *)&ninst, (void *)&units,
                     (void *)&dry};
-    cudaLaunchAttribute attr;
-    attr.id = cudaLaunchAttributeCooperative;
-    attr.val.cooperative = fused ? 1 : 0;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = fused ? 1 : 0;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = fused ? 1 : 0;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(16 * 32);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cfg.attrs = &attr;
-    cfg.numAttrs = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
     for (int k = 0; k < nsteps; ++k) {
         const cudaError_t e = cudaLaunchKernelExC(&cfg, kern, args);
         if (e != cudaSuccess) return e;
