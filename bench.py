@@ -596,9 +596,9 @@ def run_batched(sk, torch, dev, ws, rank, steps=200):
 
 
 def run_e2e(sk, torch, dev, wl, K):
-    """The same metric through the public API with host buffers: upload the
-    seed field from pinned host memory, K flow iterations with the report read
-    back, download the final field; all inside the timed region."""
+    """The same metric through the C ABI's host-buffer call (skyrme_flow_host):
+    upload the seed field from pinned host memory, K flow iterations, the
+    report and the final field downloaded; all inside the timed region."""
     lat = lattice_of(sk, wl, wl.precision)
     st = sk.State(lat, dev)
     sk.init_field(lat, sk.Seed.from_spec(wl.seed), st)
@@ -608,17 +608,14 @@ def run_e2e(sk, torch, dev, wl, K):
     stream = torch.cuda.current_stream(dev)
 
     def job():
-        """One job: every byte of its input and output crosses the host link
-        inside the timed region."""
+        """One job through skyrme_flow_host: every byte of its input and
+        output crosses the host link inside the timed region."""
         torch.cuda.synchronize(dev)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         t_wall = time.perf_counter()
         a.record(stream)
-        st.phi[0].copy_(host_in, non_blocking=True)
-        sk.load_field(lat, st, st.phi[0])
-        rep = sk.flow_step(lat, wl.dt, K, sk.ARRESTED, st, report=True)
-        host_out.copy_(st.phi[rep["cur"]], non_blocking=True)
+        sk.flow_host(lat, wl.dt, K, sk.ARRESTED, st, host_in, host_out, report=True, stream=stream)
         b.record(stream)
         torch.cuda.synchronize(dev)
         return a.elapsed_time(b), time.perf_counter() - t_wall
@@ -632,8 +629,9 @@ def run_e2e(sk, torch, dev, wl, K):
             "d2h_bytes_per_step": (bytes_field + 128) / K,
             "wall_s": round(wall, 4),
             "jobs_ms": [round(r[0], 4) for r in runs],
-            "what": f"the median of 3 jobs (after one untimed) of {K} iterations each: seed upload, "
-                    "flow, report and field download"}
+            "what": f"the median of 3 jobs (after one untimed) of {K} iterations each through "
+                    "skyrme_flow_host with pinned host buffers: seed upload, flow, report and field "
+                    "download"}
 
 
 def run_fp64_compare(sk, torch, dev, wl, nsteps, rep32, fp64_tflops):

@@ -159,6 +159,21 @@ skyrme_status skyrme_load_field(const skyrme_lattice *lat, skyrme_state *st, voi
  * stream are host and driver resources released before the call returns. */
 skyrme_status skyrme_flow_step(const skyrme_lattice *lat, double dt, int nsteps, int mode,
                                skyrme_state *st, skyrme_report *report, void *stream);
+/* skyrme_flow_host: one job on host data through a device state: the field
+ * field_in (host; n0*n1*n2 sites of 4 components in the lattice's precision,
+ * index ((x*n1)+y)*n2+z) is copied into phi[0] and loaded as by
+ * skyrme_load_field (vacuum outer layers, zero velocity, a fresh control
+ * block), nsteps iterations run as skyrme_flow_step runs them (Section 3),
+ * and the final field is copied to field_out (host, same layout; it may be
+ * field_in).  Every iteration flips the current buffers, so the result is
+ * phi[nsteps & 1]; the copies are queued behind the flow on `stream` without
+ * a wait in between.  `report` (nullable) as for skyrme_flow_step.  The call
+ * synchronises the stream before returning.  Host buffers may be pageable;
+ * pinned ones move at the host link's full rate.  SKYRME_EINVAL for a null
+ * buffer or the arguments skyrme_flow_step rejects. */
+skyrme_status skyrme_flow_host(const skyrme_lattice *lat, double dt, int nsteps, int mode,
+                               skyrme_state *st, const void *field_in, void *field_out,
+                               skyrme_report *report, void *stream);
 /* ---- x-slab decomposition of one lattice ----
  * The step is a radius-2 stencil (Section 3: the 4th-order first, second and
  * mixed differences reach two sites along each axis), and the arrest rule

@@ -122,6 +122,8 @@ _SIGNATURES = {
     "skyrme_batch_step": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "skyrme_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int),
                                              ctypes.POINTER(ctypes.c_double)]),
+    "skyrme_flow_host": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int, ctypes.c_int, _P, _P, _P,
+                                         _P, _P]),
     "skyrme_batch_set_tile": (ctypes.c_int, [_P, ctypes.c_int]),
     "skyrme_batch_set_split": (ctypes.c_int, [_P, ctypes.c_int]),
     "skyrme_batch_split": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
@@ -366,6 +368,43 @@ def flow_step(lat: Lattice, dt: float, nsteps: int, mode: int, st: State, report
                                  ctypes.byref(cs), ctypes.byref(rep) if report else None,
                                  _stream_ptr(stream, st.device))
     _check(rc, "skyrme_flow_step")
+    return _rep_dict(rep) if report else None
+
+
+def _host_ptr(buf, nbytes: int, writable: bool):
+    """Address of a host buffer (a CPU torch tensor or a NumPy array) of at
+    least nbytes contiguous bytes."""
+    torch = _torch()
+    if isinstance(buf, torch.Tensor):
+        if buf.is_cuda or not buf.is_contiguous():
+            raise ValueError("host buffers must be contiguous CPU tensors")
+        size, ptr = buf.numel() * buf.element_size(), buf.data_ptr()
+    else:
+        import numpy as np
+        if not isinstance(buf, np.ndarray) or not buf.flags["C_CONTIGUOUS"]:
+            raise ValueError("host buffers must be contiguous NumPy arrays or CPU tensors")
+        if writable and not buf.flags["WRITEABLE"]:
+            raise ValueError("the output buffer is read-only")
+        size, ptr = buf.nbytes, buf.ctypes.data
+    if size < nbytes:
+        raise ValueError(f"host buffer of {size} bytes, {nbytes} needed")
+    return ctypes.c_void_p(ptr)
+
+
+def flow_host(lat: Lattice, dt: float, nsteps: int, mode: int, st: State, field_in, field_out,
+              report: bool = True, stream=None):
+    """skyrme_flow_host: upload the host field `field_in` into the state, run
+    nsteps iterations, download the final field into `field_out` (host; may
+    be field_in), all on `stream`, which the call synchronises."""
+    nbytes = int(np.prod(lat.n)) * 4 * (8 if lat.precision == 64 else 4)
+    cl, cs = lat.c(), st.c()
+    rep = c_report()
+    rc = _on(st.device).skyrme_flow_host(ctypes.byref(cl), float(dt), int(nsteps), int(mode),
+                                         ctypes.byref(cs), _host_ptr(field_in, nbytes, False),
+                                         _host_ptr(field_out, nbytes, True),
+                                         ctypes.byref(rep) if report else None,
+                                         _stream_ptr(stream, st.device))
+    _check(rc, "skyrme_flow_host")
     return _rep_dict(rep) if report else None
 
 

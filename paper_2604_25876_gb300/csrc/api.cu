@@ -378,6 +378,35 @@ skyrme_status skyrme_flow_step(const skyrme_lattice *lat, double dt, int nsteps,
     return SKYRME_OK;
 }
 
+skyrme_status skyrme_flow_host(const skyrme_lattice *lat, double dt, int nsteps, int mode,
+                               skyrme_state *st, const void *field_in, void *field_out,
+                               skyrme_report *report, void *stream)
+{
+    skyrme_status rc = check_state(lat, st);
+    if (rc != SKYRME_OK) return rc;
+    if (!field_in || !field_out) return SKYRME_EINVAL;
+    if (!(dt > 0.0) || !isfinite(dt) || nsteps < 0 || !mode_ok(mode)) return SKYRME_EINVAL;
+    CKDEV(state_on_device(st));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t bytes = (size_t)lat->n[0] * lat->n[1] * lat->n[2] * 4 * (lat->precision == 64 ? 8 : 4);
+    CK(cudaMemcpyAsync(st->phi[0], field_in, bytes, cudaMemcpyHostToDevice, s), "upload field");
+    rc = skyrme_load_field(lat, st, stream);
+    if (rc != SKYRME_OK) return rc;
+    FlowArgs a = make_args(*lat, *st, dt, mode);
+    rc = run_iterations(*lat, a, nsteps, s);
+    if (rc != SKYRME_OK) return rc;
+    // the load leaves cur = 0 and every iteration flips it
+    const int cur = nsteps & 1;
+    CK(cudaMemcpyAsync(field_out, st->phi[cur], bytes, cudaMemcpyDeviceToHost, s), "download field");
+    Ctrl c;
+    rc = copy_ctrl(*st, &c, s);
+    if (rc != SKYRME_OK) return rc;
+    if (report) fill_report(c, report);
+    if (c.status) return static_cast<skyrme_status>(c.status);
+    if (c.cur != cur) return SKYRME_ECUDA;  // not reached: a step that did not flip set a status
+    return SKYRME_OK;
+}
+
 skyrme_status skyrme_step_densities(const skyrme_lattice *lat, double dt, int mode,
                                     skyrme_state *st, void *dens, skyrme_report *report,
                                     void *stream)
