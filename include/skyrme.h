@@ -279,7 +279,8 @@ skyrme_status skyrme_graph_create_until(const skyrme_lattice *lat, double dt, in
  * may differ in size, spacing, pion mass and Section 7.8 potentials; the
  * sextic term is not taken (SKYRME_EUNSUPPORTED).
  *   skyrme_batch_scratch_bytes: size of the caller-owned batch scratch
- *     (lattice table and per-CTA partial records), 256-byte aligned.
+ *     (lattice table, the CTAs' unit ranges of a balanced split and per-CTA
+ *     partial records), 256-byte aligned.
  *   skyrme_batch_create: validates the states (precision 32 only), encodes
  *     the lattice table for the default tile shape and uploads it (a
  *     synchronous copy); the handle owns no device memory.
