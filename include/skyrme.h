@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-#define SKYRME_ABI_VERSION 4
+#define SKYRME_ABI_VERSION 5
 
 typedef enum {
     SKYRME_OK = 0,
@@ -174,6 +174,43 @@ skyrme_status skyrme_flow_step(const skyrme_lattice *lat, double dt, int nsteps,
 skyrme_status skyrme_flow_host(const skyrme_lattice *lat, double dt, int nsteps, int mode,
                                skyrme_state *st, const void *field_in, void *field_out,
                                skyrme_report *report, void *stream);
+
+/* ---- work split of a single FP32 lattice's step ----
+ * The FP32 step streams the lattice as columns of 16 x 32 interior (y, z)
+ * sites along x, one persistent CTA per SM; each site of Section 3's
+ * iteration is computed the same way whatever the split, so the fields do
+ * not depend on it (the energy sums' order does, by FP64 rounding).
+ *   SKYRME_SPLIT_BALANCED: contiguous (column, x-plane) ranges, column by
+ *     column, with about the same number of streamed planes per CTA (a run
+ *     of r centres streams r + 4 planes).
+ *   SKYRME_SPLIT_LOCKSTEP: waves of whole columns (CTA b streams columns
+ *     b, b + G, ... for G CTAs), then the remaining columns' heads (one CTA
+ *     each) beside their tails (split over the other CTAs), so that
+ *     neighbouring columns are streamed at the same x and the halo rows they
+ *     share come from L2 instead of DRAM.
+ *   SKYRME_SPLIT_AUTO (the default): LOCKSTEP when the columns fit in one
+ *     wave (no more columns than CTAs) and it streams no more planes per CTA
+ *     than BALANCED, else BALANCED.
+ * skyrme_set_single_split sets the policy for the process (SKYRME_EINVAL for
+ * another value); launches and graphs take the policy in force when they are
+ * issued or captured.  skyrme_single_split returns it.
+ * skyrme_single_split_runs (host only, no device needed): the runs that
+ * `policy` gives an n[0] x n[1] x n[2] lattice on min(grid, units) CTAs
+ * (grid <= 256): for run k, runs[4k..4k+3] = {CTA, column, first interior
+ * plane, end plane (exclusive)}, column = (y tile) * ceil((n[2]-4)/32) +
+ * (z tile), planes counted from the first interior plane, each CTA's runs
+ * in the order it streams them.  Writes at most `cap` runs, returns the
+ * number of runs (-1 for invalid arguments); *chosen (nullable) receives the
+ * split taken (BALANCED or LOCKSTEP). */
+typedef enum {
+    SKYRME_SPLIT_AUTO = 0,
+    SKYRME_SPLIT_BALANCED = 1,
+    SKYRME_SPLIT_LOCKSTEP = 2
+} skyrme_single_split_policy;
+skyrme_status skyrme_set_single_split(int policy);
+int skyrme_single_split(void);
+int skyrme_single_split_runs(const int n[3], int grid, int policy, int *runs, int cap,
+                             int *chosen);
 /* ---- x-slab decomposition of one lattice ----
  * The step is a radius-2 stencil (Section 3: the 4th-order first, second and
  * mixed differences reach two sites along each axis), and the arrest rule

@@ -18,6 +18,7 @@ import numpy as np
 from . import _build
 
 NEWTON, ARRESTED, GRADIENT = 0, 1, 2
+SPLIT_AUTO, SPLIT_BALANCED, SPLIT_LOCKSTEP = 0, 1, 2
 SEED_VACUUM, SEED_RATIONAL_MAP, SEED_PRODUCT, SEED_NOISE = 0, 1, 2, 3
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "buffer too small", 3: "CUDA error",
@@ -127,6 +128,11 @@ _SIGNATURES = {
     "skyrme_batch_set_tile": (ctypes.c_int, [_P, ctypes.c_int]),
     "skyrme_batch_set_split": (ctypes.c_int, [_P, ctypes.c_int]),
     "skyrme_batch_split": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "skyrme_set_single_split": (ctypes.c_int, [ctypes.c_int]),
+    "skyrme_single_split": (ctypes.c_int, []),
+    "skyrme_single_split_runs": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                                ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                                ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "skyrme_batch_tile": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int)]),
@@ -406,6 +412,33 @@ def flow_host(lat: Lattice, dt: float, nsteps: int, mode: int, st: State, field_
                                          _stream_ptr(stream, st.device))
     _check(rc, "skyrme_flow_host")
     return _rep_dict(rep) if report else None
+
+
+def set_single_split(policy: int):
+    """skyrme_set_single_split: the process-wide work split of single FP32
+    lattices (SPLIT_AUTO, SPLIT_BALANCED or SPLIT_LOCKSTEP)."""
+    _check(load().skyrme_set_single_split(int(policy)), "skyrme_set_single_split")
+
+
+def single_split() -> int:
+    """skyrme_single_split: the policy in force."""
+    return int(load().skyrme_single_split())
+
+
+def single_split_runs(n, grid: int = 152, policy: int = SPLIT_AUTO):
+    """skyrme_single_split_runs (host only): the runs `policy` gives an
+    n[0] x n[1] x n[2] lattice on `grid` CTAs, as an int array of rows
+    (CTA, column, first plane, end plane), and the split taken."""
+    nn = (ctypes.c_int * 3)(*[int(v) for v in n])
+    chosen = ctypes.c_int(-1)
+    lib = load()
+    count = lib.skyrme_single_split_runs(nn, int(grid), int(policy), None, 0, ctypes.byref(chosen))
+    if count < 0:
+        raise ValueError(f"no split for n={tuple(n)}, grid={grid}, policy={policy}")
+    buf = (ctypes.c_int * max(1, 4 * count))()
+    got = lib.skyrme_single_split_runs(nn, int(grid), int(policy), buf, count, ctypes.byref(chosen))
+    assert got == count
+    return np.frombuffer(buf, dtype=np.int32)[:4 * count].reshape(count, 4).copy(), chosen.value
 
 
 def step_densities(lat: Lattice, dt: float, mode: int, st: State, stream=None):

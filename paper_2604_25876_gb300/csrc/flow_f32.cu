@@ -55,6 +55,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <string.h>
 
@@ -122,15 +123,51 @@ struct InstDesc {
     int fuse_fix;          // single lattice, ARRESTED: the step corrects its own mispredictions
 };
 
-// Unit ranges of the CTAs of a single-lattice launch: CTA b streams units
-// [start[b], start[b + 1]).  n = 0 selects the even split of the units.  The
-// host balances the ranges by their plane count (units plus the pipeline
-// fill of every run) rather than by units.
+// Unit ranges of the CTAs of a single-lattice launch.
+//   n > 0, the balanced split: CTA b streams units [start[b], start[b + 1])
+//     (column-major), the ranges balanced by their plane count (units plus
+//     the pipeline fill of every run) rather than by units.
+//   n = 0: the even split of the units.
+//   n = -2, the lockstep schedule: lw waves of whole columns (CTA b streams
+//     columns b, b + lg, ..., b + (lw - 1) lg, every CTA at the same x), then
+//     of the lr remaining columns CTA b < lr streams the head x < la of
+//     column lw lg + b while CTAs b >= lr stream the tails x >= la, tail units
+//     start[b] .. start[b + 1] (tail by tail).  Neighbouring columns are
+//     streamed side by side, so the halo rows they share are read from L2.
 constexpr int kSplitMax = 256;
 struct CtaSplit {
     int n;
+    int lw, lr, la, lg;
     int start[kSplitMax + 1];
 };
+
+// Units of CTA b under the lockstep schedule, and the run that starts at its
+// unit o (of o1): column, first interior plane (0-based) and length.
+__host__ __device__ __forceinline__ int lock_units(const CtaSplit &sp, int b, int nix)
+{
+    return sp.lw * nix + (b < sp.lr ? sp.la : sp.start[b + 1] - sp.start[b]);
+}
+__host__ __device__ __forceinline__ void lock_run(const CtaSplit &sp, int b, int nix, int o, int o1,
+                                                  int &col, int &xl, int &len)
+{
+    const int wu = sp.lw * nix;
+    if (o < wu) {
+        const int w = o / nix;
+        col = w * sp.lg + b;
+        xl = o - w * nix;
+        len = nix - xl;
+    } else if (b < sp.lr) {
+        col = sp.lw * sp.lg + b;
+        xl = o - wu;
+        len = sp.la - xl;
+    } else {
+        const int tn = nix - sp.la, t = sp.start[b] + (o - wu), c2 = t / tn;
+        col = sp.lw * sp.lg + c2;
+        xl = sp.la + (t - c2 * tn);
+        len = nix - xl;
+    }
+    len = len < o1 - o ? len : o1 - o;
+}
 
 // ------------------------------------------------------------- PTX helpers
 
@@ -1033,7 +1070,8 @@ __device__ __forceinline__ long long ld_acquire_s64(const long long *p)
 // (Its unit arithmetic is 32-bit: a 64-bit division here made the compiler
 // spill the main loop's registers.)
 template <int TY, int TZ>
-__device__ __forceinline__ void correct_own_sites(const InstDesc &D, long long u0, long long u1,
+__device__ __forceinline__ void correct_own_sites(const InstDesc &D, const CtaSplit &sp,
+                                                  long long u0, long long u1,
                                                   int cur, int fix, int ty, int tz)
 {
     // buffers selected by value, not by a run-time index into the parameter
@@ -1046,11 +1084,20 @@ __device__ __forceinline__ void correct_own_sites(const InstDesc &D, long long u
     // a single lattice's units (columns x interior planes) fit in an int
     const int nix = D.nix, nzt = D.nzt, w1 = (int)(u1 - D.unit_start);
     for (int us = (int)(u0 - D.unit_start); us < w1;) {
-        const int col = us / nix;
-        const int ue = min(w1, (col + 1) * nix);
-        const int xs = 2 + (us - col * nix);
-        const int xe = 2 + (ue - col * nix);
-        us = ue;
+        int col, xs, xe;
+        if (sp.n == -2) {
+            int xl, len;
+            lock_run(sp, blockIdx.x, nix, us, w1, col, xl, len);
+            xs = 2 + xl;
+            xe = xs + len;
+            us += len;
+        } else {
+            col = us / nix;
+            const int ue = min(w1, (col + 1) * nix);
+            xs = 2 + (us - col * nix);
+            xe = 2 + (ue - col * nix);
+            us = ue;
+        }
         const int y = 2 + (col / nzt) * TY + ty, z = 2 + (col % nzt) * TZ + tz;
         if (y > D.n1 - 3 || z > D.n2 - 3) continue;
         size_t si = (size_t)xs * ps + (size_t)y * D.n2 + z;
@@ -1136,10 +1183,13 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
     const bool listed = !BATCHED && split.n > 0;
     const int *bstart = reinterpret_cast<const int *>(table + ninst);
     const bool blisted = BATCHED && split.n < 0;
-    const long long u0 = listed ? split.start[blockIdx.x]
+    const bool locked = !BATCHED && split.n == -2;
+    const long long u0 = locked ? 0
+                         : listed ? split.start[blockIdx.x]
                          : blisted ? bstart[blockIdx.x]
                                    : total_units * blockIdx.x / gridDim.x;
-    const long long u1 = listed ? split.start[blockIdx.x + 1]
+    const long long u1 = locked ? lock_units(split, blockIdx.x, one.nix)
+                         : listed ? split.start[blockIdx.x + 1]
                          : blisted ? bstart[blockIdx.x + 1]
                                    : total_units * (blockIdx.x + 1) / gridDim.x;
     int inst = 0;
@@ -1172,12 +1222,23 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
         Acc a32 = {};
 
         while (us < seg_hi && !failed) {
-            const long long local = us - D.unit_start;
-            const long long col = local / nix;
-            const long long ue = min(seg_hi, D.unit_start + (col + 1) * (long long)nix);
-            const int xs = 2 + (int)(local - col * nix);
-            const int xe = 2 + (int)(ue - D.unit_start - col * nix);  // exclusive
-            us = ue;
+            long long col;
+            int xs, xe;  // xe exclusive
+            if (locked) {
+                int c, xl, len;
+                lock_run(split, blockIdx.x, nix, (int)us, (int)seg_hi, c, xl, len);
+                col = c;
+                xs = 2 + xl;
+                xe = xs + len;
+                us += len;
+            } else {
+                const long long local = us - D.unit_start;
+                col = local / nix;
+                const long long ue = min(seg_hi, D.unit_start + (col + 1) * (long long)nix);
+                xs = 2 + (int)(local - col * nix);
+                xe = 2 + (int)(ue - D.unit_start - col * nix);
+                us = ue;
+            }
             const int y0 = 2 + (int)(col / nzt) * TY, z0 = 2 + (int)(col % nzt) * TZ;
             const int y = y0 + ty, z = z0 + tz;
             const bool valid = (y <= n1 - 3) && (z <= n2 - 3);
@@ -1308,11 +1369,13 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
             if (fx == 2) {
                 if (tid == 0) atomicExch(&one.ctrl->status, (int)DEV_TIMEOUT);
             } else if (fx != 0) {
-                const bool listed2 = split.n > 0;
-                const long long v0 = listed2 ? split.start[blockIdx.x] : total_units * blockIdx.x / gridDim.x;
-                const long long v1 =
-                    listed2 ? split.start[blockIdx.x + 1] : total_units * (blockIdx.x + 1) / gridDim.x;
-                correct_own_sites<TY, TZ>(one, v0, v1, sm.cur_used, fx, tid / TZ, tid % TZ);
+                const bool listed2 = split.n > 0, locked2 = split.n == -2;
+                const long long v0 = locked2 ? 0
+                                     : listed2 ? split.start[blockIdx.x] : total_units * blockIdx.x / gridDim.x;
+                const long long v1 = locked2 ? lock_units(split, blockIdx.x, one.nix)
+                                     : listed2 ? split.start[blockIdx.x + 1]
+                                               : total_units * (blockIdx.x + 1) / gridDim.x;
+                correct_own_sites<TY, TZ>(one, split, v0, v1, sm.cur_used, fx, tid / TZ, tid % TZ);
             }
         }
     }
@@ -1714,17 +1777,10 @@ static int greedy_split(long long units, int nix, double cap, int max_ctas, int 
 }
 
 // Unit ranges for `grid` CTAs whose largest plane count is as small as the
-// greedy cover allows (bisection on the cap); cached for the last geometry.
+// greedy cover allows (bisection on the cap).
 static bool balanced_split(long long units, int nix, int grid, CtaSplit &out)
 {
-    static thread_local long long key_units = -1;
-    static thread_local int key_nix = -1, key_grid = -1;
-    static thread_local CtaSplit cached;
-    if (units == key_units && nix == key_nix && grid == key_grid) {
-        out = cached;
-        return out.n > 0;
-    }
-    out.n = 0;
+    out = CtaSplit{};
     if (grid <= 0 || grid > kSplitMax || units > 0x7fffffffLL || units < grid) return false;
     double lo = (double)units / grid, hi = (double)units / grid + 2.0 * kRunFill + nix;
     for (int it = 0; it < 48; ++it) {
@@ -1734,9 +1790,130 @@ static bool balanced_split(long long units, int nix, int grid, CtaSplit &out)
     }
     out.n = greedy_split(units, nix, hi, grid, out.start);
     if (out.n > grid) out.n = 0;
-    key_units = units, key_nix = nix, key_grid = grid;
-    cached = out;
     return out.n > 0;
+}
+
+// Largest plane count of a cover (unit starts of n CTAs over columns of nix
+// planes).
+static long long max_planes(const int *start, int n, int nix)
+{
+    long long m = 0;
+    for (int b = 0; b < n; ++b) {
+        long long p = 0;
+        for (long long u = start[b]; u < start[b + 1];) {
+            const long long e = std::min<long long>(start[b + 1], (u / nix + 1) * nix);
+            p += e - u + kRunFill;
+            u = e;
+        }
+        m = std::max(m, p);
+    }
+    return m;
+}
+
+// The lockstep schedule (n = -2) of ncol = units / nix columns for `grid`
+// CTAs: W = ncol / grid waves of whole columns, then the R = ncol % grid
+// remaining columns' heads (x < a, one per CTA b < R) and tails (x >= a, a
+// balanced cover over the other CTAs), the head length a chosen so that the
+// heads' planes match the tails' largest.  Without waves, CTAs left without
+// a tail are not launched (lg: the CTAs to launch), so every launched CTA
+// streams at least one plane.  Returns the largest plane count of a CTA, or
+// -1 when the geometry has no such schedule.
+static long long lock_split(long long units, int nix, int grid, CtaSplit &out)
+{
+    out = CtaSplit{};
+    const long long ncol = nix > 0 ? units / nix : 0;
+    if (grid <= 0 || grid > kSplitMax || units > 0x7fffffffLL || ncol * nix != units || ncol == 0)
+        return -1;
+    const int W = (int)(ncol / grid), R = (int)(ncol % grid);
+    out.n = -2;
+    out.lw = W;
+    out.lr = R;
+    out.lg = grid;
+    const long long wave = (long long)W * (nix + kRunFill);
+    if (R == 0) return wave;
+    std::vector<int> ts(grid - R + 1);
+    int used = 0;  // tail CTAs given units by the last cover
+    auto tails = [&](int a) -> long long {
+        const int tn = nix - a, nt = grid - R;
+        const long long tu = (long long)R * tn;
+        double lo = (double)tu / nt, hi = lo + 2.0 * kRunFill + tn;
+        for (int it = 0; it < 40; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (greedy_split(tu, tn, mid, nt, ts.data()) <= nt) hi = mid;
+            else lo = mid;
+        }
+        const int n = greedy_split(tu, tn, hi, nt, ts.data());
+        if (n > nt) return -1;
+        for (int k = n + 1; k <= nt; ++k) ts[k] = ts[n];
+        used = n;
+        return max_planes(ts.data(), n, tn);
+    };
+    // the smallest a whose heads reach the tails' largest plane count, or
+    // the one before it
+    int lo = 1, hi = nix - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) / 2;
+        const long long t = tails(mid);
+        if (t >= 0 && t <= mid + kRunFill) hi = mid;
+        else lo = mid + 1;
+    }
+    long long best = -1;
+    int best_a = 0;
+    for (int a = std::max(1, lo - 1); a <= std::min(nix - 1, lo); ++a) {
+        const long long t = tails(a);
+        if (t < 0) continue;
+        const long long m = std::max<long long>(t, a + kRunFill);
+        if (best < 0 || m < best) best = m, best_a = a;
+    }
+    if (best < 0) return -1;
+    (void)tails(best_a);
+    out.la = best_a;
+    for (int k = 0; k <= grid - R; ++k) out.start[R + k] = ts[k];
+    if (W == 0) out.lg = R + used;
+    return wave + best;
+}
+
+// Single-lattice split policy (skyrme_set_single_split): process-wide.
+static std::atomic<int> g_single_split{SKYRME_SPLIT_AUTO};
+
+// The split of a single lattice's units among at most `grid` CTAs under
+// `policy`; *ctas receives the CTAs to launch.  AUTO takes the lockstep
+// schedule when the columns fit in one wave (ncol <= grid) and it streams no
+// more planes per CTA than the balanced split, else the balanced split: with
+// waves of several columns per CTA the lockstep schedule measured slower on
+// 512^3 (58.6 against 59.4 Gsite-updates/s) although it streams the same
+// planes.  Cached for the last geometry and policy.
+static void plan_single(long long units, int nix, int grid, int policy, CtaSplit &out, int *ctas)
+{
+    static thread_local long long key_units = -1;
+    static thread_local int key_nix = -1, key_grid = -1, key_policy = -1, key_ctas = 0;
+    static thread_local CtaSplit cached;
+    if (units == key_units && nix == key_nix && grid == key_grid && policy == key_policy) {
+        out = cached;
+        *ctas = key_ctas;
+        return;
+    }
+    CtaSplit bal, lk;
+    const bool have_bal = balanced_split(units, nix, grid, bal);
+    const long long bal_max = have_bal ? max_planes(bal.start, bal.n, nix) : -1;
+    long long lk_max = -1;
+    if (policy != SKYRME_SPLIT_BALANCED) lk_max = lock_split(units, nix, grid, lk);
+    bool use_lock = false;
+    if (policy == SKYRME_SPLIT_LOCKSTEP) use_lock = lk_max >= 0;
+    else if (policy == SKYRME_SPLIT_AUTO)
+        use_lock = lk_max >= 0 && units / nix <= grid && (!have_bal || lk_max <= bal_max);
+    if (use_lock) {
+        out = lk;
+        *ctas = lk.lg;
+    } else if (have_bal) {
+        out = bal;
+        *ctas = bal.n;
+    } else {
+        out = CtaSplit{};
+        *ctas = grid;
+    }
+    key_units = units, key_nix = nix, key_grid = grid, key_policy = policy, key_ctas = *ctas;
+    cached = out;
 }
 
 // The same cover for a batch: the lattices' columns concatenated, each
@@ -1832,7 +2009,7 @@ cudaError_t launch_iterations_f32_fast(const skyrme_lattice &lat, const FlowArgs
         return cudaErrorInvalidValue;
     int grid = grid_for(tile, false, ds[0].units);
     CtaSplit split;
-    if (balanced_split(ds[0].units, ds[0].nix, grid, split)) grid = split.n;
+    plan_single(ds[0].units, ds[0].nix, grid, g_single_split.load(), split, &grid);
     partition(ds, grid, a.step_parts, split.n > 0 ? split.start : nullptr);
 
     ds[0].slab_rec = a.slab_rec;
@@ -1984,7 +2161,7 @@ static skyrme_status batch_launch(skyrme_batch *b, int nsteps, int dry, cudaStre
     InstDesc dummy;
     memset(&dummy, 0, sizeof(dummy));
     // split.n = -1: the ranges follow the table in device memory
-    static const CtaSplit kBatchListed = {-1, {}};
+    static const CtaSplit kBatchListed = {-1};
     const CtaSplit &sp = b->split ? kBatchListed : kEvenSplit;
     for (int k = 0; k < nsteps; ++k) {
         const cudaError_t e =
@@ -2090,6 +2267,68 @@ skyrme_status skyrme_batch_split(const skyrme_batch *b, int *balanced)
     if (!b || !balanced) return SKYRME_EINVAL;
     *balanced = b->split;
     return SKYRME_OK;
+}
+
+skyrme_status skyrme_set_single_split(int policy)
+{
+    if (policy != SKYRME_SPLIT_AUTO && policy != SKYRME_SPLIT_BALANCED &&
+        policy != SKYRME_SPLIT_LOCKSTEP)
+        return SKYRME_EINVAL;
+    g_single_split.store(policy);
+    return SKYRME_OK;
+}
+
+int skyrme_single_split(void) { return g_single_split.load(); }
+
+int skyrme_single_split_runs(const int n[3], int grid, int policy, int *runs, int cap,
+                             int *chosen)
+{
+    if (!n || grid <= 0 || grid > kSplitMax || cap < 0 || (cap > 0 && !runs)) return -1;
+    if (policy != SKYRME_SPLIT_AUTO && policy != SKYRME_SPLIT_BALANCED &&
+        policy != SKYRME_SPLIT_LOCKSTEP)
+        return -1;
+    if (n[0] < 5 || n[1] < 5 || n[2] < 5) return -1;
+    // the single lattice's 16 x 32 columns
+    const int nyt = (n[1] - 4 + 15) / 16, nzt = (n[2] - 4 + 31) / 32, nix = n[0] - 4;
+    const long long units = (long long)nyt * nzt * nix;
+    if (units > 0x7fffffffLL) return -1;
+    grid = (int)std::min<long long>(grid, units);
+    CtaSplit sp;
+    int ctas = grid;
+    plan_single(units, nix, grid, policy, sp, &ctas);
+    if (chosen) *chosen = sp.n == -2 ? SKYRME_SPLIT_LOCKSTEP : SKYRME_SPLIT_BALANCED;
+    // walk every CTA's units as the step kernel does
+    int count = 0;
+    for (int b = 0; b < ctas; ++b) {
+        const bool locked = sp.n == -2;
+        const long long u0 = locked ? 0 : sp.n > 0 ? sp.start[b] : units * b / ctas;
+        const long long u1 = locked ? lock_units(sp, b, nix) : sp.n > 0 ? sp.start[b + 1]
+                                                                         : units * (b + 1) / ctas;
+        for (long long us = u0; us < u1;) {
+            int col, xs, xe;
+            if (locked) {
+                int xl, len;
+                lock_run(sp, b, nix, (int)us, (int)u1, col, xl, len);
+                xs = xl;
+                xe = xl + len;
+                us += len;
+            } else {
+                col = (int)(us / nix);
+                const long long ue = std::min<long long>(u1, (long long)(col + 1) * nix);
+                xs = (int)(us - (long long)col * nix);
+                xe = (int)(ue - (long long)col * nix);
+                us = ue;
+            }
+            if (count < cap) {
+                runs[4 * count + 0] = b;
+                runs[4 * count + 1] = col;
+                runs[4 * count + 2] = xs;
+                runs[4 * count + 3] = xe;
+            }
+            ++count;
+        }
+    }
+    return count;
 }
 
 skyrme_status skyrme_batch_autotune(skyrme_batch *b, int trials, void *stream, int *best_tile,

@@ -36,7 +36,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_abi_version_and_status_strings():
     lib = sk.load()
-    assert lib.skyrme_abi_version() == 4
+    assert lib.skyrme_abi_version() == 5
     assert lib.skyrme_status_string(0) == b"ok"
     assert lib.skyrme_status_string(4) == b"non-finite value detected"
 
