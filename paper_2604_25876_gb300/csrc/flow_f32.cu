@@ -757,6 +757,18 @@ __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &
         u = one_minus_phi0();
         br.a.x += fmaf(D.bmy2, ph.a.x, u * fmaf(D.bmw2 * u, u, D.bmz2));
     }
+    // det[phi, d_x phi, d_y phi, d_z phi] by the 2x2 minors s_AB of rows
+    // (phi, d_x) and c_AB of rows (d_y, d_z): {q_s0, s12, s34, q_s5} =
+    // {s01, (s02, s03), (s12, s13), s23}, {q0, q12, q34, q5} likewise for c
+    const float q_s0 = ph.a.x * dx.a.y - dx.a.x * ph.a.y;
+    const float2 s12 = __ffma2_rn(bc(-dx.a.x), ph.b, __fmul2_rn(bc(ph.a.x), dx.b));
+    const float2 s34 = __ffma2_rn(bc(-dx.a.y), ph.b, __fmul2_rn(bc(ph.a.y), dx.b));
+    const float q_s5 = ph.b.x * dx.b.y - dx.b.x * ph.b.y;
+    const float q0 = dyc.a.x * dzc.a.y - dzc.a.x * dyc.a.y;
+    const float2 q12 = __ffma2_rn(bc(-dzc.a.x), dyc.b, __fmul2_rn(bc(dyc.a.x), dzc.b));
+    const float2 q34 = __ffma2_rn(bc(-dzc.a.y), dyc.b, __fmul2_rn(bc(dyc.a.y), dzc.b));
+    const float q5 = dyc.b.x * dzc.b.y - dzc.b.x * dyc.b.y;
+    const float det = q_s0 * q5 - s12.x * q34.y + s12.y * q34.x + s34.x * q12.y - s34.y * q12.x + q_s5 * q0;
     float e6 = 0.f;
     if constexpr (SEX) {
         // Section 7.8 sextic term c6 D^2, D = det[phi, d_x phi, d_y phi, d_z phi]
@@ -771,26 +783,38 @@ __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &
         tmem_ld8(trec + 16, rs);
         tmem_ld4(trec + 24, rs + 8);
         tmem_wait_ld12(rs);
-        const float ph4[4] = {ph.a.x, ph.a.y, ph.b.x, ph.b.y};
-        const float u4[4] = {dx.a.x, dx.a.y, dx.b.x, dx.b.y};
-        const float v4[4] = {dyc.a.x, dyc.a.y, dyc.b.x, dyc.b.y};
-        const float w4[4] = {dzc.a.x, dzc.a.y, dzc.b.x, dzc.b.y};
-        float P[4], Qx[4], Qy[4], Qz[4];
-        cross3<float>(u4, v4, w4, P);
-        cross3<float>(ph4, v4, w4, Qx);
-        cross3<float>(ph4, u4, w4, Qy);
-        cross3<float>(ph4, u4, v4, Qz);
-        const float Dd = ph4[0] * P[0] + ph4[1] * P[1] + ph4[2] * P[2] + ph4[3] * P[3];
-        const P4 qx = {make_float2(-Qx[0], -Qx[1]), make_float2(-Qx[2], -Qx[3])};
-        const P4 qy = {make_float2(Qy[0], Qy[1]), make_float2(Qy[2], Qy[3])};
-        const P4 qz = {make_float2(-Qz[0], -Qz[1]), make_float2(-Qz[2], -Qz[3])};
+        // the cofactor rows of M = [phi; u; v; w] (rows): P = dD/dphi and
+        // q_i = dD/d(u_i), each a sum of three products of an entry of the
+        // other row of its pair with the minors of the opposite pair
+        const float s01 = q_s0, s02 = s12.x, s03 = s12.y, s12v = s34.x, s13 = s34.y, s23 = q_s5;
+        const float c01 = q0, c02 = q12.x, c03 = q12.y, c12 = q34.x, c13 = q34.y, c23 = q5;
+        const float u0 = dx.a.x, u1 = dx.a.y, u2 = dx.b.x, u3 = dx.b.y;
+        const float p0 = ph.a.x, p1 = ph.a.y, p2 = ph.b.x, p3 = ph.b.y;
+        const float v0 = dyc.a.x, v1 = dyc.a.y, v2 = dyc.b.x, v3 = dyc.b.y;
+        const float w0 = dzc.a.x, w1 = dzc.a.y, w2 = dzc.b.x, w3 = dzc.b.y;
+        const P4 pp = {make_float2(fmaf(u3, c12, fmaf(-u2, c13, u1 * c23)),
+                                   fmaf(-u3, c02, fmaf(u2, c03, -u0 * c23))),
+                       make_float2(fmaf(u3, c01, fmaf(-u1, c03, u0 * c13)),
+                                   fmaf(-u2, c01, fmaf(u1, c02, -u0 * c12)))};
+        const P4 qx = {make_float2(fmaf(-p3, c12, fmaf(p2, c13, -p1 * c23)),
+                                   fmaf(p3, c02, fmaf(-p2, c03, p0 * c23))),
+                       make_float2(fmaf(-p3, c01, fmaf(p1, c03, -p0 * c13)),
+                                   fmaf(p2, c01, fmaf(-p1, c02, p0 * c12)))};
+        const P4 qy = {make_float2(fmaf(w3, s12v, fmaf(-w2, s13, w1 * s23)),
+                                   fmaf(-w3, s02, fmaf(w2, s03, -w0 * s23))),
+                       make_float2(fmaf(w3, s01, fmaf(-w1, s03, w0 * s13)),
+                                   fmaf(-w2, s01, fmaf(w1, s02, -w0 * s12v)))};
+        const P4 qz = {make_float2(fmaf(-v3, s12v, fmaf(v2, s13, -v1 * s23)),
+                                   fmaf(v3, s02, fmaf(-v2, s03, v0 * s23))),
+                       make_float2(fmaf(-v3, s01, fmaf(v1, s03, -v0 * s13)),
+                                   fmaf(v2, s01, fmaf(-v1, s02, v0 * s12v)))};
+        const float Dd = det;
         const P4 dyy = {make_float2(rs[0], rs[1]), make_float2(rs[2], rs[3])};
         const P4 dzz = {make_float2(rs[4], rs[5]), make_float2(rs[6], rs[7])};
         const P4 dyz = {make_float2(rs[8], rs[9]), make_float2(rs[10], rs[11])};
-        const float dDx = dot(qx, dxx) + dot(qy, dxy) + dot(qz, dxz);
-        const float dDy = dot(qx, dxy) + dot(qy, dyy) + dot(qz, dyz);
-        const float dDz = dot(qx, dxz) + dot(qy, dyz) + dot(qz, dzz);
-        const P4 pp = {make_float2(P[0], P[1]), make_float2(P[2], P[3])};
+        const float dDx = hsum(dot2(qz, dxz, dot2(qy, dxy, __ffma2_rn(qx.b, dxx.b, __fmul2_rn(qx.a, dxx.a)))));
+        const float dDy = hsum(dot2(qz, dyz, dot2(qy, dyy, __ffma2_rn(qx.b, dxy.b, __fmul2_rn(qx.a, dxy.a)))));
+        const float dDz = hsum(dot2(qz, dzz, dot2(qy, dyz, __ffma2_rn(qx.b, dxz.b, __fmul2_rn(qx.a, dxz.a)))));
         const P4 sx = fma(bc(dDz), qz, fma(bc(dDy), qy, fma(bc(dDx), qx, mul(bc(Dd * (1.f / 3.f)), pp))));
         br = fma(bc(-D.c6b), sx, br);
         e6 = D.c6 * Dd * Dd;
@@ -812,16 +836,6 @@ __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &
     const P4 pn = mul(bc(r), t);
     const float sq = axx * axx + Cayy * Cayy + Cazz * Cazz + 2.f * (axy * axy + axz * axz + Cayz * Cayz);
     const float e4 = 0.5f * (tra * tra - sq);
-    // det[phi, d_x phi, d_y phi, d_z phi] by 2x2 minors of rows (phi, d_x), (d_y, d_z)
-    const float q_s0 = ph.a.x * dx.a.y - dx.a.x * ph.a.y;
-    const float2 s12 = __ffma2_rn(bc(-dx.a.x), ph.b, __fmul2_rn(bc(ph.a.x), dx.b));
-    const float2 s34 = __ffma2_rn(bc(-dx.a.y), ph.b, __fmul2_rn(bc(ph.a.y), dx.b));
-    const float q_s5 = ph.b.x * dx.b.y - dx.b.x * ph.b.y;
-    const float q0 = dyc.a.x * dzc.a.y - dzc.a.x * dyc.a.y;
-    const float2 q12 = __ffma2_rn(bc(-dzc.a.x), dyc.b, __fmul2_rn(bc(dyc.a.x), dzc.b));
-    const float2 q34 = __ffma2_rn(bc(-dzc.a.y), dyc.b, __fmul2_rn(bc(dyc.a.y), dzc.b));
-    const float q5 = dyc.b.x * dzc.b.y - dzc.b.x * dyc.b.y;
-    const float det = q_s0 * q5 - s12.x * q34.y + s12.y * q34.x + s34.x * q12.y - s34.y * q12.x + q_s5 * q0;
     if (valid) {
         __stcs(phiout + si, st4(pn));
         if (mode != MODE_GRADIENT) __stcs(vout + si, st4(vnew));
