@@ -218,6 +218,17 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t pari
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
+// The same wait that also gives up once *flag is set (another warp's wait
+// failed); the flag is read only when the phase is not complete at once.
+__device__ __forceinline__ bool mbar_wait_flag(unsigned long long *bar, uint32_t parity,
+                                               const volatile int *flag)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (*flag == 0 && global_ns() - t0 < kWaitLimitNs)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
 __device__ __forceinline__ void tma_plane(void *dst, const CUtensorMap *map,
                                           unsigned long long *bar, int c0, int c1, int c2)
 {
@@ -615,7 +626,7 @@ struct CtaSync {
 // rows) into DY for the mixed d_yz of this plane.
 template <int TY, int TZ>
 __device__ __forceinline__ void arrive_plane(const float4 (*P)[TZ + 4], float4 (*DY)[TZ + 4],
-                                             const InstDesc &D, int tid, int ty, int tz,
+                                             const InstDesc &D, int halo_off, int ty, int tz,
                                              PlaneVals &rv, P4 &dyy, P4 &dzz)
 {
     const float2 w8 = kW8(), wm16 = kWm16(), w30 = kW30();
@@ -632,14 +643,12 @@ __device__ __forceinline__ void arrive_plane(const float4 (*P)[TZ + 4], float4 (
     {  // each warp fills the z-halo columns of u_y of its own rows, one
        // component per lane (a packed 4-vector stencil would idle 28 lanes);
        // the same roundings as fd1u
-        constexpr int ROWS = 32 / TZ, RS = 4 * (TZ + 4);  // floats per haloed row
-        const int lane = tid & 31;
-        if (lane < 16 * ROWS) {
-            const int hr = (tid >> 5) * ROWS + (lane >> 4), ci = (lane >> 2) & 3, k = lane & 3;
-            const int hc = ci < 2 ? ci : TZ + ci;
-            const float *pc = reinterpret_cast<const float *>(&P[hr][hc]) + k;
+        // (halo_off: the lane's float offset in both arrays, -1 for the idle lanes)
+        constexpr int RS = 4 * (TZ + 4);  // floats per haloed row
+        if (halo_off >= 0) {
+            const float *pc = reinterpret_cast<const float *>(P) + halo_off;
             const float m2 = pc[0], m1 = pc[RS], p1 = pc[3 * RS], p2 = pc[4 * RS];
-            reinterpret_cast<float *>(&DY[hr][hc])[k] = __fmaf_rn(w8.x, __fsub_rn(p1, m1), __fsub_rn(m2, p2));
+            reinterpret_cast<float *>(DY)[halo_off] = __fmaf_rn(w8.x, __fsub_rn(p1, m1), __fsub_rn(m2, p2));
         }
     }
     rv.phi = c;
@@ -1159,6 +1168,18 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     const int tid = threadIdx.x;
     const int ty = tid / TZ, tz = tid % TZ;
+    // the d_y halo column this lane fills in every plane: one component of
+    // the two z-halo columns at each end of the warp's rows (16 lanes per row)
+    int halo_off = -1;
+    {
+        constexpr int ROWS = 32 / TZ;
+        const int lane = tid & 31;
+        if (lane < 16 * ROWS) {
+            const int hr = (tid >> 5) * ROWS + (lane >> 4), ci = (lane >> 2) & 3, k = lane & 3;
+            const int hc = ci < 2 ? ci : TZ + ci;
+            halo_off = 4 * (hr * (TZ + 4) + hc) + k;
+        }
+    }
     // a single lattice's next step may start its prologue as soon as an SM
     // frees up (its grid-dependency wait below keeps it off this step's data)
     if constexpr (!BATCHED) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -1281,10 +1302,12 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
                     if (pp > pl) break;
                     const int s = g % NSLOT;
                     const uint32_t par = (g / NSLOT) & 1u;
-                    if (!mbar_wait(&sm.bar[s], par)) sm.flag = 1;
+                    // a copy that never lands fails the step; the waits of the
+                    // group of five that follow give up at once
+                    if (!mbar_wait_flag(&sm.bar[s], par, &sm.flag)) sm.flag = 1;
                     float4(*DY)[TZ + 4] = sm.dy[g & 1];
                     P4 dyy, dzz;
-                    arrive_plane<TY, TZ>(sm.plane[s], DY, D, tid, ty, tz, ring[k], dyy, dzz);
+                    arrive_plane<TY, TZ>(sm.plane[s], DY, D, halo_off, ty, tz, ring[k], dyy, dzz);
                     // ---- centre x = pp - 2, whose in-plane record is that of plane g - 2
                     const uint32_t g3n = g3 == 2 ? 0 : g3 + 1;  // (g + 1) % 3 == (g - 2) % 3
                     const int x = pp - 2;
@@ -1313,10 +1336,6 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
                             }
                         }
                     }
-                    if (*(volatile int *)&sm.flag) {
-                        failed = true;
-                        break;
-                    }
                     plane_record<TY, TZ, SEX>(DY, D, ty, tz, ring[k], dyy, dzz, twarp + RECC * g3);
                     if constexpr (SEX) {
                         const float zr[4] = {ring[k].dz.a.x, ring[k].dz.a.y, ring[k].dz.b.x, ring[k].dz.b.y};
@@ -1325,6 +1344,8 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
                     ++g;
                     g3 = g3n;
                 }
+                // a failed copy is noticed once per group of five planes
+                if (*(volatile int *)&sm.flag) failed = true;
                 // FP32 partial sums cover at most 40 planes before entering the double-float sums
                 if ((++nouter & 7) == 0) flush(acc, amax, THREADS, a32);
             }
