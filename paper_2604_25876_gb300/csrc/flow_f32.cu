@@ -643,9 +643,9 @@ __device__ __forceinline__ void arrive_plane(const float4 (*P)[TZ + 4], float4 (
     {  // each warp fills the z-halo columns of u_y of its own rows, one
        // component per lane (a packed 4-vector stencil would idle 28 lanes);
        // the same roundings as fd1u
-        // (halo_off: the lane's float offset in both arrays, -1 for the idle lanes)
+        // (halo_off: the lane's float offset in both arrays)
         constexpr int RS = 4 * (TZ + 4);  // floats per haloed row
-        if (halo_off >= 0) {
+        {
             const float *pc = reinterpret_cast<const float *>(P) + halo_off;
             const float m2 = pc[0], m1 = pc[RS], p1 = pc[3 * RS], p2 = pc[4 * RS];
             reinterpret_cast<float *>(DY)[halo_off] = __fmaf_rn(w8.x, __fsub_rn(p1, m1), __fsub_rn(m2, p2));
@@ -1170,15 +1170,13 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
     const int ty = tid / TZ, tz = tid % TZ;
     // the d_y halo column this lane fills in every plane: one component of
     // the two z-halo columns at each end of the warp's rows (16 lanes per row)
-    int halo_off = -1;
+    int halo_off;
     {
         constexpr int ROWS = 32 / TZ;
-        const int lane = tid & 31;
-        if (lane < 16 * ROWS) {
-            const int hr = (tid >> 5) * ROWS + (lane >> 4), ci = (lane >> 2) & 3, k = lane & 3;
-            const int hc = ci < 2 ? ci : TZ + ci;
-            halo_off = 4 * (hr * (TZ + 4) + hc) + k;
-        }
+        const int lane = (tid & 31) % (16 * ROWS);  // the spare lanes repeat the first ones
+        const int hr = (tid >> 5) * ROWS + (lane >> 4), ci = (lane >> 2) & 3, k = lane & 3;
+        const int hc = ci < 2 ? ci : TZ + ci;
+        halo_off = 4 * (hr * (TZ + 4) + hc) + k;
     }
     // a single lattice's next step may start its prologue as soon as an SM
     // frees up (its grid-dependency wait below keeps it off this step's data)
@@ -1295,6 +1293,7 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
             }
             PlaneVals ring[5];
             int nouter = 0;
+            size_t si = (size_t)(pf - 2) * plane_stride + col_off;  // of the centre x = pp - 2
             for (int base = pf; base <= pl && !failed; base += 5) {
 #pragma unroll
                 for (int k = 0; k < 5; ++k) {
@@ -1321,7 +1320,7 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
                                                        twarp + kDzCol + 4 * ((k + 3) % 5),
                                                        twarp + kDzCol + 4 * ((k + 4) % 5)),
                                             &sm.vpl[s][ty][tz], use_v,
-                                            valid, phiout, vout, (size_t)x * plane_stride + col_off, a32);
+                                            valid, phiout, vout, si, a32);
                     // this warp is done with slot s; the last warp to leave it streams
                     // plane pp + NSLOT (and its velocity) into it
                     __syncwarp();
@@ -1343,6 +1342,7 @@ __global__ void __launch_bounds__(TY *TZ, 512 / (TY * TZ))
                     }
                     ++g;
                     g3 = g3n;
+                    si += plane_stride;
                 }
                 // a failed copy is noticed once per group of five planes
                 if (*(volatile int *)&sm.flag) failed = true;
