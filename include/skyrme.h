@@ -188,9 +188,9 @@ skyrme_status skyrme_flow_host(const skyrme_lattice *lat, double dt, int nsteps,
  *     each) beside their tails (split over the other CTAs), so that
  *     neighbouring columns are streamed at the same x and the halo rows they
  *     share come from L2 instead of DRAM.
- *   SKYRME_SPLIT_AUTO (the default): LOCKSTEP when the columns fit in one
- *     wave (no more columns than CTAs) and it streams no more planes per CTA
- *     than BALANCED, else BALANCED.
+ *   SKYRME_SPLIT_AUTO (the default): the split measured fastest, BALANCED
+ *     (LOCKSTEP moves fewer DRAM bytes but ran slower on every lattice too
+ *     large for L2).
  * skyrme_set_single_split sets the policy for the process (SKYRME_EINVAL for
  * another value); launches and graphs take the policy in force when they are
  * issued or captured.  skyrme_single_split returns it.

@@ -1912,12 +1912,12 @@ static long long lock_split(long long units, int nix, int grid, CtaSplit &out)
 static std::atomic<int> g_single_split{SKYRME_SPLIT_AUTO};
 
 // The split of a single lattice's units among at most `grid` CTAs under
-// `policy`; *ctas receives the CTAs to launch.  AUTO takes the lockstep
-// schedule when the columns fit in one wave (ncol <= grid) and it streams no
-// more planes per CTA than the balanced split, else the balanced split: with
-// waves of several columns per CTA the lockstep schedule measured slower on
-// 512^3 (58.6 against 59.4 Gsite-updates/s) although it streams the same
-// planes.  Cached for the last geometry and policy.
+// `policy`; *ctas receives the CTAs to launch.  AUTO takes the balanced
+// split: the lockstep schedule cuts the DRAM traffic (1.31x -> 1.02x of the
+// algorithmic bytes on 256^3) but measured slower wherever the step is not
+// L2-resident (256^3: 57.1 against 58.2, 512^3: 61.5 against 63.3
+// Gsite-updates/s), and equal on 128^3.  Cached for the last geometry and
+// policy.
 static void plan_single(long long units, int nix, int grid, int policy, CtaSplit &out, int *ctas)
 {
     static thread_local long long key_units = -1;
@@ -1930,13 +1930,9 @@ static void plan_single(long long units, int nix, int grid, int policy, CtaSplit
     }
     CtaSplit bal, lk;
     const bool have_bal = balanced_split(units, nix, grid, bal);
-    const long long bal_max = have_bal ? max_planes(bal.start, bal.n, nix) : -1;
     long long lk_max = -1;
-    if (policy != SKYRME_SPLIT_BALANCED) lk_max = lock_split(units, nix, grid, lk);
-    bool use_lock = false;
-    if (policy == SKYRME_SPLIT_LOCKSTEP) use_lock = lk_max >= 0;
-    else if (policy == SKYRME_SPLIT_AUTO)
-        use_lock = lk_max >= 0 && units / nix <= grid && (!have_bal || lk_max <= bal_max);
+    if (policy == SKYRME_SPLIT_LOCKSTEP) lk_max = lock_split(units, nix, grid, lk);
+    const bool use_lock = policy == SKYRME_SPLIT_LOCKSTEP && lk_max >= 0;
     if (use_lock) {
         out = lk;
         *ctas = lk.lg;

@@ -50,21 +50,22 @@ def test_every_unit_is_streamed_once(n, policy, grid):
 
 
 @pytest.mark.parametrize("n", SIZES)
-def test_lockstep_streams_no_more_planes_than_balanced_where_auto_takes_it(n):
-    ncol, nix = geometry(n)
+def test_auto_is_the_balanced_split(n):
     bal, _ = sk.single_split_runs(n, 152, sk.SPLIT_BALANCED)
     auto, chosen = sk.single_split_runs(n, 152, sk.SPLIT_AUTO)
-    if chosen == sk.SPLIT_LOCKSTEP:
-        assert ncol <= min(152, ncol * nix)
-        assert plane_counts(auto).max() <= plane_counts(bal).max()
-    else:
-        assert np.array_equal(auto, bal)
+    assert chosen == sk.SPLIT_BALANCED
+    assert np.array_equal(auto, bal)
 
 
-def test_auto_takes_lockstep_for_one_wave_and_balanced_beyond():
-    assert sk.single_split_runs((256, 256, 256), 152, sk.SPLIT_AUTO)[1] == sk.SPLIT_LOCKSTEP
-    assert sk.single_split_runs((128, 128, 128), 152, sk.SPLIT_AUTO)[1] == sk.SPLIT_LOCKSTEP
-    assert sk.single_split_runs((512, 512, 512), 152, sk.SPLIT_AUTO)[1] == sk.SPLIT_BALANCED
+@pytest.mark.parametrize("n", SIZES)
+def test_lockstep_streams_no_more_planes_than_balanced_in_one_wave(n):
+    """Where the columns fit in one wave, the heads and tails are balanced as
+    well as the balanced split itself (the lockstep schedule costs no planes)."""
+    ncol, nix = geometry(n)
+    bal, _ = sk.single_split_runs(n, 152, sk.SPLIT_BALANCED)
+    lk, chosen = sk.single_split_runs(n, 152, sk.SPLIT_LOCKSTEP)
+    if chosen == sk.SPLIT_LOCKSTEP and ncol <= 152:
+        assert plane_counts(lk).max() <= plane_counts(bal).max()
 
 
 @pytest.mark.parametrize("n,G", [((512, 512, 512), 152), ((20, 324, 260), 152),
