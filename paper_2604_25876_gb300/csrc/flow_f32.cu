@@ -249,7 +249,7 @@ __device__ __forceinline__ void tma_plane(void *dst, const CUtensorMap *map,
 // lanes, warp w owns columns [C * (w / 4), C * (w / 4) + C) with
 // C = tmem_cols_per_warp.
 // Thread t of a warp reads and writes its own lane (the 32x32b shapes).
-// One in-plane record: 16 columns (13 values used), or 32 (25 used) in the
+// One in-plane record: 16 columns (12 values used), or 32 (24 used) in the
 // sextic kernels, which also carry d_yy, d_zz and d_yz phi to the centre.
 template <bool SEX> constexpr int rec_cols() { return SEX ? 32 : 16; }
 // the sextic variant also keeps the d_z phi part of its x-ring (5 planes of
@@ -292,10 +292,6 @@ __device__ __forceinline__ void tmem_st4(uint32_t taddr, const float *v)
 {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]) : "memory");
 }
-__device__ __forceinline__ void tmem_st1(uint32_t taddr, float v)
-{
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(taddr), "f"(v) : "memory");
-}
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v)
 {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];" : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]) : "r"(taddr) : "memory");
@@ -303,14 +299,6 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v)
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float *v)
 {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];" : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]) : "r"(taddr) : "memory");
-}
-__device__ __forceinline__ void tmem_ld1(uint32_t taddr, float &v)
-{
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=f"(v) : "r"(taddr) : "memory");
-}
-__device__ __forceinline__ void tmem_wait_ld13(float (&v)[13])
-{
-    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]), "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]) : : "memory");
 }
 __device__ __forceinline__ void tmem_wait_ld16(float (&v)[16])
 {
@@ -672,13 +660,16 @@ __device__ __forceinline__ void plane_record(const float4 (*DY)[TZ + 4], const I
     const P4 qin = fma(bc(2.f * ayz), dyz, fma(bc(azz), dzz, mul(bc(ayy), dyy)));
     const float gyv = hsum(dot2(dyz, dz, __ffma2_rn(dyy.b, dy.b, __fmul2_rn(dyy.a, dy.a))));
     const float gzv = hsum(dot2(dzz, dz, __ffma2_rn(dyz.b, dy.b, __fmul2_rn(dyz.a, dy.a))));
-    // columns 0-7 lin, qin; 8-11 g_y, g_z, a_yy, a_zz; 12 a_yz
+    // the centre needs a_yy, a_zz, a_yz only as a_yy + a_zz (in tr a) and
+    // a_yy^2 + a_zz^2 + 2 a_yz^2 (in the quartic density)
+    const float asum = ayy + azz;
+    const float asq = fmaf(2.f * ayz, ayz, fmaf(azz, azz, ayy * ayy));
+    // columns 0-7 lin, qin; 8-11 g_y, g_z, a_yy + a_zz, a_yy^2 + a_zz^2 + 2 a_yz^2
     const float r[12] = {lin.a.x, lin.a.y, lin.b.x, lin.b.y, qin.a.x, qin.a.y, qin.b.x, qin.b.y,
-                         gyv, gzv, ayy, azz};
+                         gyv, gzv, asum, asq};
     (void)THREADS;
     tmem_st8(trec, r);
     tmem_st4(trec + 8, r + 8);
-    tmem_st1(trec + 12, ayz);
     if constexpr (SEX) {
         // columns 16-27: N_yy, N_zz, N_yz
         const float r2[12] = {dyy.a.x, dyy.a.y, dyy.b.x, dyy.b.y, dzz.a.x, dzz.a.y, dzz.b.x, dzz.b.y,
@@ -705,11 +696,10 @@ __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &
     constexpr int THREADS = TY * TZ;
     const int mode = D.mode;
     const float2 dt = D.dt, dt2 = D.dt2;
-    float rv[13];
+    float rv[12];
     tmem_wait_st();  // this thread's earlier record stores have landed
     tmem_ld8(trec, rv);
     tmem_ld4(trec + 8, rv + 8);
-    tmem_ld1(trec + 12, rv[12]);
     // the sextic variant's d_z phi of M2, M1, C, Q1 (tdz: their columns)
     float zv[16];
     if constexpr (SEX) {
@@ -718,7 +708,7 @@ __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &
         tmem_ld4(tdz.z, zv + 8);
         tmem_ld4(tdz.w, zv + 12);
     }
-    tmem_wait_ld13(rv);
+    tmem_wait_ld12(rv);
     if constexpr (SEX) tmem_wait_ld16(zv);
     auto zp4 = [&](int i) -> P4 {
         return {make_float2(zv[4 * i], zv[4 * i + 1]), make_float2(zv[4 * i + 2], zv[4 * i + 3])};
@@ -728,8 +718,7 @@ __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &
 
     const P4 lin = {make_float2(rv[0], rv[1]), make_float2(rv[2], rv[3])};
     const P4 qin = {make_float2(rv[4], rv[5]), make_float2(rv[6], rv[7])};
-    const float Cgy = rv[8], Cgz = rv[9], Cayy = rv[10], Cazz = rv[11];
-    const float Cayz = rv[12];
+    const float Cgy = rv[8], Cgz = rv[9], Casum = rv[10], Casq = rv[11];
     (void)THREADS;
     const P4 ph = C.phi;
     // u_x and the negated second derivatives N_xx, N_xy, N_xz (the scales
@@ -740,7 +729,7 @@ __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &
     const P4 dxz = fd1(zM2, zM1, zQ1, Q2.dz, xc1, xc2);
     const P4 dyc = C.dy, dzc = zC;
     const float axx = dot(dx, dx), axy = dot(dx, dyc), axz = dot(dx, dzc);
-    const float tra = axx + Cayy + Cazz;
+    const float tra = axx + Casum;
     const P4 L = add(dxx, lin);  // -12h^2 Laplacian phi
     // g_i = sum_j d_ij phi.d_j phi and c_i = g_i - Laplacian.d_i phi, both
     // negated; nc_i = -c_i
@@ -843,7 +832,7 @@ __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &
     }
     const float r = rsqrtf(dot(t, t));
     const P4 pn = mul(bc(r), t);
-    const float sq = axx * axx + Cayy * Cayy + Cazz * Cazz + 2.f * (axy * axy + axz * axz + Cayz * Cayz);
+    const float sq = fmaf(axx, axx, Casq) + 2.f * fmaf(axy, axy, axz * axz);
     const float e4 = 0.5f * (tra * tra - sq);
     if (valid) {
         __stcs(phiout + si, st4(pn));
