@@ -218,16 +218,20 @@ __device__ __forceinline__ void site_physics(const T phi[4], const T d1[3][4], c
     const T a00 = dot(d1[0], d1[0]), a11 = dot(d1[1], d1[1]), a22 = dot(d1[2], d1[2]);
     const T a01 = dot(d1[0], d1[1]), a02 = dot(d1[0], d1[2]), a12 = dot(d1[1], d1[2]);
     const T tra = a00 + a11 + a22;
-    T L[4];
+    // c_i = g_i - Laplacian(phi) . d_i phi with g_i = sum_j d_ij phi . d_j phi;
+    // the j = i terms cancel, so c_i = sum_{j != i} d_ij phi . d_j phi
+    // - (sum_{j != i} d_jj phi) . d_i phi
+    T L[4], L12[4], L02[4], L01[4];
 #pragma unroll
-    for (int A = 0; A < 4; ++A) L[A] = d2[0][A] + d2[1][A] + d2[2][A];
-    // g_i = sum_j d_ij phi . d_j phi ;  s_i = Laplacian(phi) . d_i phi
-    const T g0 = dot(d2[0], d1[0]) + dot(dm[0], d1[1]) + dot(dm[1], d1[2]);
-    const T g1 = dot(dm[0], d1[0]) + dot(d2[1], d1[1]) + dot(dm[2], d1[2]);
-    const T g2 = dot(dm[1], d1[0]) + dot(dm[2], d1[1]) + dot(d2[2], d1[2]);
-    const T c0 = g0 - dot(L, d1[0]);
-    const T c1 = g1 - dot(L, d1[1]);
-    const T c2 = g2 - dot(L, d1[2]);
+    for (int A = 0; A < 4; ++A) {
+        L12[A] = d2[1][A] + d2[2][A];
+        L02[A] = d2[0][A] + d2[2][A];
+        L01[A] = d2[0][A] + d2[1][A];
+        L[A] = d2[0][A] + L12[A];
+    }
+    const T c0 = dot(dm[0], d1[1]) + dot(dm[1], d1[2]) - dot(L12, d1[0]);
+    const T c1 = dot(dm[0], d1[0]) + dot(dm[2], d1[2]) - dot(L02, d1[1]);
+    const T c2 = dot(dm[1], d1[0]) + dot(dm[2], d1[1]) - dot(L01, d1[2]);
     const T one_tra = T(1) + tra;
     const T b01 = T(2) * a01, b02 = T(2) * a02, b12 = T(2) * a12;
     T G[4];

@@ -17,10 +17,10 @@ sk = pytest.importorskip("paper_2604_25876_gb300")
 DEV = "cuda:0"
 
 
-def flow(n, h, m, dt, nsteps, policy, phi):
+def flow(n, h, m, dt, nsteps, policy, phi, **model):
     sk.set_single_split(policy)
     try:
-        lat = sk.Lattice(n, h, m, 32)
+        lat = sk.Lattice(n, h, m, 32, **model)
         st = sk.State(lat, torch.device(DEV))
         sk.load_field(lat, st, phi)
         rep = sk.flow_step(lat, dt, nsteps, sk.ARRESTED, st)
@@ -52,3 +52,18 @@ def test_lockstep_and_balanced_splits_agree(n, h, m, dt, nsteps, need_fix):
         assert ra["fixups"] > 0
     assert ra["E"] == pytest.approx(rb["E"], rel=1e-13)
     assert ra["B"] == pytest.approx(rb["B"], rel=1e-12, abs=1e-13)
+
+
+@pytest.mark.parametrize("model", [{"m_w": 1.0}, {"c6": 1.0}], ids=["potentials", "sextic"])
+def test_splits_agree_for_the_extension_variants(model):
+    """The potentials and sextic instantiations of the step share the run
+    decode; a wave of whole columns, then heads and tails."""
+    n, h, m, dt, nsteps = (20, 324, 260), 0.1, 1.0, 0.004, 8
+    phi = oracle.seed_rational_map(n, h, 1, 1.0).astype(np.float32)
+    fa, va, ra = flow(n, h, m, dt, nsteps, sk.SPLIT_LOCKSTEP, phi, **model)
+    fb, vb, rb = flow(n, h, m, dt, nsteps, sk.SPLIT_BALANCED, phi, **model)
+    assert ra["status"] == 0 and rb["status"] == 0 and ra["steps"] == nsteps
+    np.testing.assert_array_equal(fa, fb)
+    np.testing.assert_array_equal(va, vb)
+    assert ra["arrests"] == rb["arrests"]
+    assert ra["E"] == pytest.approx(rb["E"], rel=1e-13)
