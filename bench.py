@@ -41,11 +41,12 @@ BYTES_PER_SITE_F32 = 64   # read phi, v; write phi', v' (16 B each)
 BYTES_PER_SITE_F64 = 128
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0     # GB/s, used only when the measured peaks file is absent
-# FP operations per site-update (FMA = 2): the arithmetic the FP64 tile kernel
-# executes per interior site, which evaluates each formula once per site
-# (ncu op counts dadd + dmul + 2 dfma of one launch on a 64^3 lattice, divided
-# by its 60^3 interior sites; the hand tallies of the formulas give 590 and
-# 860: the rest is the square root and division sequences and the sums)
+# FP operations per site-update (FMA = 2): the formulas evaluated plainly, once
+# per site, as the FP64 tile kernel first did (ncu op counts dadd + dmul +
+# 2 dfma of one launch on a 64^3 lattice, divided by its 60^3 interior sites;
+# the hand tallies of the formulas give 590 and 860: the rest is the square
+# root and division sequences and the sums).  The kernels now cancel terms
+# and share minors, and execute fewer; these counts stay the definition.
 FLOPS_PER_SITE = 621      # the standard model
 FLOPS_PER_SITE_EXT = 888  # with the Section 7.8 potentials and sextic term
 FLOPS_PER_SITE_POT = 638  # potentials only (the standard count + their 17-operation tally)

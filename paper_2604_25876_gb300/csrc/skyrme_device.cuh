@@ -147,19 +147,6 @@ template <typename T> struct ExtModel {
     T my2, mz2, mw2, c6;
 };
 
-// n with n . x = det[x; a; b; c] (rows), by 2x2 minors of (b, c).
-template <typename T>
-__device__ __forceinline__ void cross3(const T a[4], const T b[4], const T c[4], T n[4])
-{
-    const T m01 = b[0] * c[1] - b[1] * c[0], m02 = b[0] * c[2] - b[2] * c[0];
-    const T m03 = b[0] * c[3] - b[3] * c[0], m12 = b[1] * c[2] - b[2] * c[1];
-    const T m13 = b[1] * c[3] - b[3] * c[1], m23 = b[2] * c[3] - b[3] * c[2];
-    n[0] = a[1] * m23 - a[2] * m13 + a[3] * m12;
-    n[1] = a[2] * m03 - a[0] * m23 - a[3] * m02;
-    n[2] = a[0] * m13 - a[1] * m03 + a[3] * m01;
-    n[3] = a[1] * m02 - a[0] * m12 - a[2] * m01;
-}
-
 // Adds the extension terms to the Euler-Lagrange gradient G (before the
 // tangent projection); returns their potential density in e0x, the sextic
 // density in e6 and 1 - phi^0 in u.
@@ -170,9 +157,14 @@ __device__ __forceinline__ void cross3(const T a[4], const T b[4], const T c[4],
 //   d_i D = sum_j Q_j . d_i d_j phi.  The 4 D P collects D P and the divergence
 //   of the cofactors, sum_i d_i Q_i = -3 P (the d_i d_j phi parts cancel in
 //   pairs because d_i d_j = d_j d_i on the lattice too).
+// P and the Q_i are the cofactor rows of M = [phi; d_x phi; d_y phi; d_z phi],
+// formed from the 2x2 minors s_AB of the rows (phi, d_x phi) and c_AB of
+// (d_y phi, d_z phi) (AB = 01, 02, 03, 12, 13, 23) that the charge density's
+// determinant D = det M uses too, three products each.
 template <typename T>
 __device__ __forceinline__ void extension_terms(const T phi[4], const T d1[3][4], const T d2[3][4],
-                                                const T dm[3][4], const ExtModel<T> &x, T G[4],
+                                                const T dm[3][4], const ExtModel<T> &x,
+                                                const T (&sm)[6], const T (&cm)[6], T D, T G[4],
                                                 T &e0x, T &e6, T &u)
 {
     u = one_minus_phi0<T>(phi);
@@ -184,15 +176,18 @@ __device__ __forceinline__ void extension_terms(const T phi[4], const T d1[3][4]
     // arithmetic; FP32 flows without the sextic term run on the streaming kernel
     if constexpr (sizeof(T) == 8)
         if (x.c6 == T(0)) return;
-    T P[4], Q0[4], Q1[4], Q2[4];
-    cross3<T>(d1[0], d1[1], d1[2], P);
-    cross3<T>(phi, d1[1], d1[2], Q0);
-    cross3<T>(phi, d1[0], d1[2], Q1);
-    cross3<T>(phi, d1[0], d1[1], Q2);
-#pragma unroll
-    for (int A = 0; A < 4; ++A) Q0[A] = -Q0[A], Q2[A] = -Q2[A];
+    const T s01 = sm[0], s02 = sm[1], s03 = sm[2], s12 = sm[3], s13 = sm[4], s23 = sm[5];
+    const T c01 = cm[0], c02 = cm[1], c03 = cm[2], c12 = cm[3], c13 = cm[4], c23 = cm[5];
+    const T *p = phi, *uu = d1[0], *v = d1[1], *w = d1[2];
+    const T P[4] = {uu[1] * c23 - uu[2] * c13 + uu[3] * c12, -uu[0] * c23 + uu[2] * c03 - uu[3] * c02,
+                    uu[0] * c13 - uu[1] * c03 + uu[3] * c01, -uu[0] * c12 + uu[1] * c02 - uu[2] * c01};
+    const T Q0[4] = {-p[1] * c23 + p[2] * c13 - p[3] * c12, p[0] * c23 - p[2] * c03 + p[3] * c02,
+                     -p[0] * c13 + p[1] * c03 - p[3] * c01, p[0] * c12 - p[1] * c02 + p[2] * c01};
+    const T Q1[4] = {w[1] * s23 - w[2] * s13 + w[3] * s12, -w[0] * s23 + w[2] * s03 - w[3] * s02,
+                     w[0] * s13 - w[1] * s03 + w[3] * s01, -w[0] * s12 + w[1] * s02 - w[2] * s01};
+    const T Q2[4] = {-v[1] * s23 + v[2] * s13 - v[3] * s12, v[0] * s23 - v[2] * s03 + v[3] * s02,
+                     -v[0] * s13 + v[1] * s03 - v[3] * s01, v[0] * s12 - v[1] * s02 + v[2] * s01};
     auto dot = [](const T *a, const T *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2] + a[3] * b[3]; };
-    const T D = dot(phi, P);
     const T dD0 = dot(Q0, d2[0]) + dot(Q1, dm[0]) + dot(Q2, dm[1]);
     const T dD1 = dot(Q0, dm[0]) + dot(Q1, d2[1]) + dot(Q2, dm[2]);
     const T dD2 = dot(Q0, dm[1]) + dot(Q1, dm[2]) + dot(Q2, d2[2]);
@@ -244,8 +239,26 @@ __device__ __forceinline__ void site_physics(const T phi[4], const T d1[3][4], c
         G[A] = T(-2) * brace;
     }
     G[0] -= T(2) * m2;
+    // D = det[phi, d_x phi, d_y phi, d_z phi] by the 2x2 minors of the rows
+    // (phi, d_x phi) and (d_y phi, d_z phi): formed here when the sextic
+    // cofactors need them, at the end otherwise (shorter live ranges)
+    T sm[6], cm[6], det = T(0);
+    auto minors = [&]() {
+        const T *r0 = phi, *r1 = d1[0], *r2 = d1[1], *r3 = d1[2];
+        sm[0] = r0[0] * r1[1] - r1[0] * r0[1], sm[1] = r0[0] * r1[2] - r1[0] * r0[2];
+        sm[2] = r0[0] * r1[3] - r1[0] * r0[3], sm[3] = r0[1] * r1[2] - r1[1] * r0[2];
+        sm[4] = r0[1] * r1[3] - r1[1] * r0[3], sm[5] = r0[2] * r1[3] - r1[2] * r0[3];
+        cm[0] = r2[0] * r3[1] - r3[0] * r2[1], cm[1] = r2[0] * r3[2] - r3[0] * r2[2];
+        cm[2] = r2[0] * r3[3] - r3[0] * r2[3], cm[3] = r2[1] * r3[2] - r3[1] * r2[2];
+        cm[4] = r2[1] * r3[3] - r3[1] * r2[3], cm[5] = r2[2] * r3[3] - r3[2] * r2[3];
+        det = sm[0] * cm[5] - sm[1] * cm[4] + sm[2] * cm[3] + sm[3] * cm[2] - sm[4] * cm[1] +
+              sm[5] * cm[0];
+    };
     T e0x = T(0), u0 = T(0);
-    if constexpr (EXT) extension_terms<T>(phi, d1, d2, dm, *ext, G, e0x, *e6, u0);
+    if constexpr (EXT) {
+        minors();
+        extension_terms<T>(phi, d1, d2, dm, *ext, sm, cm, det, G, e0x, *e6, u0);
+    }
     const T Gphi = G[0] * phi[0] + G[1] * phi[1] + G[2] * phi[2] + G[3] * phi[3];
 #pragma unroll
     for (int A = 0; A < 4; ++A) F[A] = Gphi * phi[A] - G[A];
@@ -255,21 +268,8 @@ __device__ __forceinline__ void site_physics(const T phi[4], const T d1[3][4], c
     dens[1] = T(0.5) * (tra * tra - sq);
     if constexpr (EXT) dens[2] = T(2) * m2 * u0 + e0x;
     else dens[2] = T(2) * m2 * one_minus_phi0<T>(phi);
-    // b = -(1/2 pi^2) det[phi, d_x phi, d_y phi, d_z phi] (Laplace expansion in 2x2 minors)
-    const T *r0 = phi, *r1 = d1[0], *r2 = d1[1], *r3 = d1[2];
-    const T s0 = r0[0] * r1[1] - r1[0] * r0[1];
-    const T s1 = r0[0] * r1[2] - r1[0] * r0[2];
-    const T s2 = r0[0] * r1[3] - r1[0] * r0[3];
-    const T s3 = r0[1] * r1[2] - r1[1] * r0[2];
-    const T s4 = r0[1] * r1[3] - r1[1] * r0[3];
-    const T s5 = r0[2] * r1[3] - r1[2] * r0[3];
-    const T q5 = r2[2] * r3[3] - r3[2] * r2[3];
-    const T q4 = r2[1] * r3[3] - r3[1] * r2[3];
-    const T q3 = r2[1] * r3[2] - r3[1] * r2[2];
-    const T q2 = r2[0] * r3[3] - r3[0] * r2[3];
-    const T q1 = r2[0] * r3[2] - r3[0] * r2[2];
-    const T q0 = r2[0] * r3[1] - r3[0] * r2[1];
-    const T det = s0 * q5 - s1 * q4 + s2 * q3 + s3 * q2 - s4 * q1 + s5 * q0;
+    // b = -(1/2 pi^2) D
+    if constexpr (!EXT) minors();
     dens[3] = T(-0.050660591821168885) * det;  // -1/(2 pi^2)
 }
 
