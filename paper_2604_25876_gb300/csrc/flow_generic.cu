@@ -43,10 +43,9 @@ template <typename T> struct FlowParams {
     Ctrl *ctrl;
     double *parts;
     int n0, n1, n2;
-    T inv_h, inv_h2, m2, dt;
-    ExtModel<T> ext;  // Section 7.8 extension terms (used by EXT instantiations)
-    T w1, w2;      // first-derivative weights / h
-    T v1, v2, v0;  // second-derivative weights / h^2
+    T m2, dt;
+    ExtModel<T> ext;     // Section 7.8 extension terms (used by EXT instantiations)
+    StencilScale<T> sc;  // scales of the unscaled derivatives
     double h3;
     int mode;
     double *slab_rec;  // x-slab: the step's record goes here, the decision is made later
@@ -102,22 +101,29 @@ __device__ __forceinline__ void wait_tile_async()
     asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
-// Scaled stencils: w1 (p1 - m1) + w2 (p2 - m2) and v1 (p1 + m1) + v2 (p2 + m2) + v0 c
-template <typename T> __device__ __forceinline__ T sd1(T m2v, T m1v, T p1v, T p2v, T w1, T w2)
+// The Section 3 stencils without their 1/h factors (StencilScale carries
+// them): u = 8 (p1 - m1) - (p2 - m2) = 12h d phi; the pure second derivative
+// negated, N = (p2 + m2) + 30 c - 16 (p1 + m1) = -12h^2 dd phi; and the mixed
+// one from the u of the other direction on the same scale,
+// N = -(2/3) (p1 - m1) + (1/12) (p2 - m2).
+template <typename T> __device__ __forceinline__ T sd1u(T m2v, T m1v, T p1v, T p2v)
 {
-    return w1 * (p1v - m1v) + w2 * (p2v - m2v);
+    return fma(T(8), p1v - m1v, m2v - p2v);
+}
+template <typename T> __device__ __forceinline__ T sd2n(T m2v, T m1v, T c, T p1v, T p2v)
+{
+    return fma(T(-16), p1v + m1v, fma(T(30), c, p2v + m2v));
+}
+template <typename T> __device__ __forceinline__ T sdmix(T m2v, T m1v, T p1v, T p2v)
+{
+    return fma(T(-2.0 / 3.0), p1v - m1v, T(1.0 / 12.0) * (p2v - m2v));
 }
 template <typename T>
-__device__ __forceinline__ T sd2(T m2v, T m1v, T c, T p1v, T p2v, T v1, T v2, T v0)
+__device__ __forceinline__ vec4_t<T> sd1uv(const vec4_t<T> &m2v, const vec4_t<T> &m1v,
+                                           const vec4_t<T> &p1v, const vec4_t<T> &p2v)
 {
-    return v1 * (p1v + m1v) + v2 * (p2v + m2v) + v0 * c;
-}
-template <typename T>
-__device__ __forceinline__ vec4_t<T> sd1v(const vec4_t<T> &m2v, const vec4_t<T> &m1v,
-                                          const vec4_t<T> &p1v, const vec4_t<T> &p2v, T w1, T w2)
-{
-    return make4<T>(sd1<T>(m2v.x, m1v.x, p1v.x, p2v.x, w1, w2), sd1<T>(m2v.y, m1v.y, p1v.y, p2v.y, w1, w2),
-                    sd1<T>(m2v.z, m1v.z, p1v.z, p2v.z, w1, w2), sd1<T>(m2v.w, m1v.w, p1v.w, p2v.w, w1, w2));
+    return make4<T>(sd1u<T>(m2v.x, m1v.x, p1v.x, p2v.x), sd1u<T>(m2v.y, m1v.y, p1v.y, p2v.y),
+                    sd1u<T>(m2v.z, m1v.z, p1v.z, p2v.z), sd1u<T>(m2v.w, m1v.w, p1v.w, p2v.w));
 }
 
 // Shared-memory layout of the tile kernels: the haloed field tile, then
@@ -135,28 +141,29 @@ template <typename T, int TZ> constexpr size_t tile_smem_bytes()
     return (size_t)(kTileBufs<T> * G::TILEN + G::DXN + G::DYN) * sizeof(vec4_t<T>);
 }
 
-// Stage d_x phi and d_y phi of the tile (all threads), from the loaded tile.
-// Entries whose stencil leaves the lattice hold garbage that only sites
-// outside the interior read.
+// Stage u_x and u_y (12h d_x phi, 12h d_y phi) of the tile (all threads),
+// from the loaded tile.  Entries whose stencil leaves the lattice hold
+// garbage that only sites outside the interior read.
 template <int TZ, typename T>
 __device__ __forceinline__ void stage_first_derivatives(const vec4_t<T> *tile, vec4_t<T> *dxs,
-                                                        vec4_t<T> *dys, T w1, T w2)
+                                                        vec4_t<T> *dys)
 {
     using G = TileG<TZ>;
     const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
     auto P = [&](int tx, int ty, int tz) -> const vec4_t<T> & { return tile[(tx * G::SY + ty) * G::SZ + tz]; };
     for (int i = tid; i < G::DXN; i += GTHREADS) {
         const int lz = i % G::SZ, ly = (i / G::SZ) % G::SY, lx = i / (G::SZ * G::SY);
-        dxs[i] = sd1v<T>(P(lx, ly, lz), P(lx + 1, ly, lz), P(lx + 3, ly, lz), P(lx + 4, ly, lz), w1, w2);
+        dxs[i] = sd1uv<T>(P(lx, ly, lz), P(lx + 1, ly, lz), P(lx + 3, ly, lz), P(lx + 4, ly, lz));
     }
     for (int i = tid; i < G::DYN; i += GTHREADS) {
         const int lz = i % G::SZ, ly = (i / G::SZ) % G::TY, lx = i / (G::SZ * G::TY);
-        dys[i] = sd1v<T>(P(lx + 2, ly, lz), P(lx + 2, ly + 1, lz), P(lx + 2, ly + 3, lz),
-                         P(lx + 2, ly + 4, lz), w1, w2);
+        dys[i] = sd1uv<T>(P(lx + 2, ly, lz), P(lx + 2, ly + 1, lz), P(lx + 2, ly + 3, lz),
+                          P(lx + 2, ly + 4, lz));
     }
 }
 
-// All derivatives of the site at local interior coordinate (lx, ly, lz).
+// All derivatives of the site at local interior coordinate (lx, ly, lz),
+// without their 1/h factors (u, N of the unscaled stencils above).
 template <int TZ, typename T>
 __device__ __forceinline__ void tile_derivatives(const vec4_t<T> *tile, const vec4_t<T> *dxs,
                                                  const vec4_t<T> *dys, int lx, int ly, int lz,
@@ -170,7 +177,7 @@ __device__ __forceinline__ void tile_derivatives(const vec4_t<T> *tile, const ve
     // d_x phi at (lx, ly + 2 + dy, lz + 2 + dz) and d_y phi at (lx, ly, lz + 2 + dz)
     auto DX = [&](int dy, int dz) -> vec4_t<T> { return dxs[(lx * G::SY + ly + 2 + dy) * G::SZ + lz + 2 + dz]; };
     auto DY = [&](int dz) -> vec4_t<T> { return dys[(lx * G::TY + ly) * G::SZ + lz + 2 + dz]; };
-    const T w1 = p.w1, w2 = p.w2, v1 = p.v1, v2 = p.v2, v0 = p.v0;
+    (void)p;
     const vec4_t<T> c = P(0, 0, 0);
     const int off[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
 #pragma unroll
@@ -182,9 +189,9 @@ __device__ __forceinline__ void tile_derivatives(const vec4_t<T> *tile, const ve
 #pragma unroll
         for (int A = 0; A < 4; ++A) {
             if (i == 2)
-                d1[i][A] = sd1<T>(comp<T>(m2v, A), comp<T>(m1v, A), comp<T>(p1v, A), comp<T>(p2v, A), w1, w2);
-            d2[i][A] = sd2<T>(comp<T>(m2v, A), comp<T>(m1v, A), comp<T>(c, A), comp<T>(p1v, A),
-                              comp<T>(p2v, A), v1, v2, v0);
+                d1[i][A] = sd1u<T>(comp<T>(m2v, A), comp<T>(m1v, A), comp<T>(p1v, A), comp<T>(p2v, A));
+            d2[i][A] = sd2n<T>(comp<T>(m2v, A), comp<T>(m1v, A), comp<T>(c, A), comp<T>(p1v, A),
+                               comp<T>(p2v, A));
         }
     }
     const vec4_t<T> dx0 = DX(0, 0), dy0 = DY(0);
@@ -196,9 +203,9 @@ __device__ __forceinline__ void tile_derivatives(const vec4_t<T> *tile, const ve
         phi[A] = comp<T>(c, A);
         d1[0][A] = comp<T>(dx0, A);
         d1[1][A] = comp<T>(dy0, A);
-        dm[0][A] = sd1<T>(comp<T>(xym2, A), comp<T>(xym1, A), comp<T>(xyp1, A), comp<T>(xyp2, A), w1, w2);
-        dm[1][A] = sd1<T>(comp<T>(xzm2, A), comp<T>(xzm1, A), comp<T>(xzp1, A), comp<T>(xzp2, A), w1, w2);
-        dm[2][A] = sd1<T>(comp<T>(yzm2, A), comp<T>(yzm1, A), comp<T>(yzp1, A), comp<T>(yzp2, A), w1, w2);
+        dm[0][A] = sdmix<T>(comp<T>(xym2, A), comp<T>(xym1, A), comp<T>(xyp1, A), comp<T>(xyp2, A));
+        dm[1][A] = sdmix<T>(comp<T>(xzm2, A), comp<T>(xzm1, A), comp<T>(xzp1, A), comp<T>(xzp2, A));
+        dm[2][A] = sdmix<T>(comp<T>(yzm2, A), comp<T>(yzm1, A), comp<T>(yzp1, A), comp<T>(yzp2, A));
     }
 }
 
@@ -357,13 +364,13 @@ __global__ void __launch_bounds__(GTHREADS, kTileMinBlocks<T, EXT>) k_tile(FlowP
             load_tile<TZ, T>(tile, phi, x0, y0, z0, p.n0, p.n1, p.n2);
             __syncthreads();
         }
-        stage_first_derivatives<TZ, T>(tile, dxs, dys, p.w1, p.w2);
+        stage_first_derivatives<TZ, T>(tile, dxs, dys);
         __syncthreads();
         const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
         if (!((x <= p.n0 - 3) && (y <= p.n1 - 3) && (z <= p.n2 - 3))) continue;
         T ph[4], d1[3][4], d2[3][4], dm[3][4], F[4], dens[4], e6 = T(0);
         tile_derivatives<TZ, T>(tile, dxs, dys, lx, ly, lz, p, ph, d1, d2, dm);
-        site_physics<T, EXT>(ph, d1, d2, dm, p.m2, F, dens, &p.ext, &e6);
+        site_physics<T, EXT>(ph, d1, d2, dm, p.m2, p.sc, F, dens, &p.ext, &e6);
         const size_t s = site_index(x, y, z, p.n1, p.n2);
         if (KIND == 0) {
             T tv[4];
@@ -568,14 +575,15 @@ template <typename T> static FlowParams<T> make_params(const FlowArgs &a, double
     p.n0 = a.n[0];
     p.n1 = a.n[1];
     p.n2 = a.n[2];
-    p.inv_h = T(1.0 / a.h);
-    p.inv_h2 = T(1.0 / (a.h * a.h));
-    const double ih = 1.0 / a.h, ih2 = ih * ih;
-    p.w1 = T(2.0 / 3.0 * ih);
-    p.w2 = T(-1.0 / 12.0 * ih);
-    p.v1 = T(4.0 / 3.0 * ih2);
-    p.v2 = T(-1.0 / 12.0 * ih2);
-    p.v0 = T(-2.5 * ih2);
+    {
+        const double k1 = 1.0 / (12.0 * a.h);
+        p.sc.k1sq = T(k1 * k1);
+        p.sc.k1cu = T(k1 * k1 * k1);
+        p.sc.k1qu = T(k1 * k1 * k1 * k1);
+        p.sc.k1sx = T(k1 * k1 * k1 * k1 * k1 * k1);
+        p.sc.B = T(12.0 * k1 * k1 * k1 * k1);
+        p.sc.K144 = T(144.0 * a.h * a.h);
+    }
     p.m2 = T(a.m * a.m);
     p.ext.my2 = T(a.my * a.my);
     p.ext.mz2 = T(a.mz * a.mz);

@@ -147,6 +147,14 @@ template <typename T> struct ExtModel {
     T my2, mz2, mw2, c6;
 };
 
+// Scales of the unscaled derivatives the tile kernels carry: u_i = 12h d_i phi
+// and N_ij = -12h^2 d_ij phi, so d_i phi = k1 u_i with k1 = 1/(12h).
+template <typename T> struct StencilScale {
+    T k1sq, k1cu, k1qu, k1sx;  // k1^2, k1^3, k1^4, k1^6
+    T B;                       // k1^2 / (12h^2) = 12 k1^4 = 1/(1728 h^4)
+    T K144;                    // 144 h^2 = 1/k1^2
+};
+
 // Adds the extension terms to the Euler-Lagrange gradient G (before the
 // tangent projection); returns their potential density in e0x, the sextic
 // density in e6 and 1 - phi^0 in u.
@@ -160,12 +168,16 @@ template <typename T> struct ExtModel {
 // P and the Q_i are the cofactor rows of M = [phi; d_x phi; d_y phi; d_z phi],
 // formed from the 2x2 minors s_AB of the rows (phi, d_x phi) and c_AB of
 // (d_y phi, d_z phi) (AB = 01, 02, 03, 12, 13, 23) that the charge density's
-// determinant D = det M uses too, three products each.
+// determinant D = det M uses too, three products each.  Here in the unscaled
+// derivatives u, N (StencilScale): D, P, Q_i carry k1^3, k1^3, k1^2 and d_i D
+// carries -k1^2/(12h^2) = -12 k1^4, so the bracket is k1^6 [4 D P + 12 sum_i
+// dD_i Q_i] in the unscaled values.
 template <typename T>
 __device__ __forceinline__ void extension_terms(const T phi[4], const T d1[3][4], const T d2[3][4],
                                                 const T dm[3][4], const ExtModel<T> &x,
-                                                const T (&sm)[6], const T (&cm)[6], T D, T G[4],
-                                                T &e0x, T &e6, T &u)
+                                                const StencilScale<T> &sc, const T (&sm)[6],
+                                                const T (&cm)[6], T D, T G[4], T &e0x, T &e6,
+                                                T &u)
 {
     u = one_minus_phi0<T>(phi);
     const T u2 = u * u;
@@ -191,31 +203,36 @@ __device__ __forceinline__ void extension_terms(const T phi[4], const T d1[3][4]
     const T dD0 = dot(Q0, d2[0]) + dot(Q1, dm[0]) + dot(Q2, dm[1]);
     const T dD1 = dot(Q0, dm[0]) + dot(Q1, d2[1]) + dot(Q2, dm[2]);
     const T dD2 = dot(Q0, dm[1]) + dot(Q1, dm[2]) + dot(Q2, d2[2]);
-    const T two_c6 = T(2) * x.c6, four_D = T(4) * D;
+    const T two_c6 = T(2) * x.c6 * sc.k1sx, four_D = T(4) * D;
 #pragma unroll
     for (int A = 0; A < 4; ++A)
-        G[A] += two_c6 * (four_D * P[A] - dD0 * Q0[A] - dD1 * Q1[A] - dD2 * Q2[A]);
-    e6 = x.c6 * D * D;
+        G[A] += two_c6 * (four_D * P[A] + T(12) * (dD0 * Q0[A] + dD1 * Q1[A] + dD2 * Q2[A]));
+    e6 = x.c6 * sc.k1sx * D * D;
 }
 
 // ------------------------------------------------------------ site physics
-// Inputs: phi (4), first derivatives d1[i][A], second derivatives d2[i][A]
-// (d_ii) and mixed dm[p][A] for p = xy, xz, yz, all already scaled by 1/h, 1/h^2.
-// Outputs: tangent force F (4) and densities {e2, e4, e0, b}; with EXT the
-// extension terms of `ext` are included (e0 then holds the whole potential)
-// and the sextic density goes to e6.
+// Inputs: phi (4) and its derivatives without their 1/h factors (StencilScale):
+// u[i][A] = 12h d_i phi^A, the negated pure second derivatives
+// N2[i][A] = -12h^2 d_ii phi^A and the mixed ones Nm[p][A] = -12h^2 d_p phi^A
+// for p = xy, xz, yz.  Outputs: tangent force F (4) and densities
+// {e2, e4, e0, b}; with EXT the extension terms of `ext` are included (e0 then
+// holds the whole potential) and the sextic density goes to e6.
+// With a_ij = k1^2 A_ij (A_ij = u_i.u_j), d_ij phi = -N_ij / (12h^2) and
+// B = k1^2 / (12h^2), the brace of the Euler-Lagrange equation is
+// -B [L_N (144h^2 + tr A) + sum_i u_i C_i - H], L_N = sum_i N_ii,
+// C_i = sum_{j != i} N_ij.u_j - (sum_{j != i} N_jj).u_i (the j = i terms of
+// g_i and of the Laplacian's part cancel) and H = sum_ij N_ij A_ij, so that
+// G = -2 brace - 2 m^2 e_0 = 2 B [...] - 2 m^2 e_0.
 template <typename T, bool EXT = false>
 __device__ __forceinline__ void site_physics(const T phi[4], const T d1[3][4], const T d2[3][4],
-                                             const T dm[3][4], T m2, T F[4], T dens[4],
-                                             const ExtModel<T> *ext = nullptr, T *e6 = nullptr)
+                                             const T dm[3][4], T m2, const StencilScale<T> &sc,
+                                             T F[4], T dens[4], const ExtModel<T> *ext = nullptr,
+                                             T *e6 = nullptr)
 {
     auto dot = [](const T *a, const T *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2] + a[3] * b[3]; };
     const T a00 = dot(d1[0], d1[0]), a11 = dot(d1[1], d1[1]), a22 = dot(d1[2], d1[2]);
     const T a01 = dot(d1[0], d1[1]), a02 = dot(d1[0], d1[2]), a12 = dot(d1[1], d1[2]);
     const T tra = a00 + a11 + a22;
-    // c_i = g_i - Laplacian(phi) . d_i phi with g_i = sum_j d_ij phi . d_j phi;
-    // the j = i terms cancel, so c_i = sum_{j != i} d_ij phi . d_j phi
-    // - (sum_{j != i} d_jj phi) . d_i phi
     T L[4], L12[4], L02[4], L01[4];
 #pragma unroll
     for (int A = 0; A < 4; ++A) {
@@ -227,16 +244,17 @@ __device__ __forceinline__ void site_physics(const T phi[4], const T d1[3][4], c
     const T c0 = dot(dm[0], d1[1]) + dot(dm[1], d1[2]) - dot(L12, d1[0]);
     const T c1 = dot(dm[0], d1[0]) + dot(dm[2], d1[2]) - dot(L02, d1[1]);
     const T c2 = dot(dm[1], d1[0]) + dot(dm[2], d1[1]) - dot(L01, d1[2]);
-    const T one_tra = T(1) + tra;
+    const T k_tra = sc.K144 + tra;
     const T b01 = T(2) * a01, b02 = T(2) * a02, b12 = T(2) * a12;
+    const T twoB = T(2) * sc.B;
     T G[4];
 #pragma unroll
     for (int A = 0; A < 4; ++A) {
-        // d_ij phi^A a_ij over all i, j (symmetric)
+        // N_ij^A A_ij over all i, j (symmetric)
         const T Ha = d2[0][A] * a00 + d2[1][A] * a11 + d2[2][A] * a22 + dm[0][A] * b01 +
                      dm[1][A] * b02 + dm[2][A] * b12;
-        const T brace = L[A] * one_tra + d1[0][A] * c0 + d1[1][A] * c1 + d1[2][A] * c2 - Ha;
-        G[A] = T(-2) * brace;
+        const T bracket = L[A] * k_tra + d1[0][A] * c0 + d1[1][A] * c1 + d1[2][A] * c2 - Ha;
+        G[A] = twoB * bracket;
     }
     G[0] -= T(2) * m2;
     // D = det[phi, d_x phi, d_y phi, d_z phi] by the 2x2 minors of the rows
@@ -257,20 +275,21 @@ __device__ __forceinline__ void site_physics(const T phi[4], const T d1[3][4], c
     T e0x = T(0), u0 = T(0);
     if constexpr (EXT) {
         minors();
-        extension_terms<T>(phi, d1, d2, dm, *ext, sm, cm, det, G, e0x, *e6, u0);
+        extension_terms<T>(phi, d1, d2, dm, *ext, sc, sm, cm, det, G, e0x, *e6, u0);
     }
     const T Gphi = G[0] * phi[0] + G[1] * phi[1] + G[2] * phi[2] + G[3] * phi[3];
 #pragma unroll
     for (int A = 0; A < 4; ++A) F[A] = Gphi * phi[A] - G[A];
 
-    dens[0] = tra;
+    // e2 = tr a = k1^2 tr A, e4 = k1^4 (tr A^2 - A_ij A_ij) / 2
+    dens[0] = sc.k1sq * tra;
     const T sq = a00 * a00 + a11 * a11 + a22 * a22 + T(2) * (a01 * a01 + a02 * a02 + a12 * a12);
-    dens[1] = T(0.5) * (tra * tra - sq);
+    dens[1] = sc.k1qu * (T(0.5) * (tra * tra - sq));
     if constexpr (EXT) dens[2] = T(2) * m2 * u0 + e0x;
     else dens[2] = T(2) * m2 * one_minus_phi0<T>(phi);
-    // b = -(1/2 pi^2) D
+    // b = -(1/2 pi^2) D, D = k1^3 det of the unscaled rows
     if constexpr (!EXT) minors();
-    dens[3] = T(-0.050660591821168885) * det;  // -1/(2 pi^2)
+    dens[3] = (T(-0.050660591821168885) * sc.k1cu) * det;  // -1/(2 pi^2)
 }
 
 // ------------------------------------------------------ block reductions
