@@ -213,7 +213,7 @@ template <typename T>
 __device__ __forceinline__ void normalise_store(vec4_t<T> *dst, const T t[4])
 {
     const T nn = t[0] * t[0] + t[1] * t[1] + t[2] * t[2] + t[3] * t[3];
-    const T r = T(1) / sqrt(nn);
+    const T r = rsqrt(nn);  // within an ulp of 1/sqrt, without its division
     store4<T>(dst, make4<T>(t[0] * r, t[1] * r, t[2] * r, t[3] * r));
 }
 
