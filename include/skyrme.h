@@ -161,9 +161,10 @@ skyrme_status skyrme_flow_step(const skyrme_lattice *lat, double dt, int nsteps,
                                skyrme_state *st, skyrme_report *report, void *stream);
 /* skyrme_flow_host: one job on host data through a device state: the field
  * field_in (host; n0*n1*n2 sites of 4 components in the lattice's precision,
- * index ((x*n1)+y)*n2+z) is copied into phi[0] and loaded as by
- * skyrme_load_field (vacuum outer layers, zero velocity, a fresh control
- * block), nsteps iterations run as skyrme_flow_step runs them (Section 3),
+ * index ((x*n1)+y)*n2+z) is loaded as by skyrme_load_field (vacuum outer
+ * layers, zero velocity, a fresh control block): a pinned buffer is read by
+ * the load kernel over the host link, any other is copied into phi[0] first;
+ * then nsteps iterations run as skyrme_flow_step runs them (Section 3),
  * and the final field is copied to field_out (host, same layout; it may be
  * field_in).  Every iteration flips the current buffers, so the result is
  * phi[nsteps & 1]; the copies are queued behind the flow on `stream` without

@@ -389,9 +389,26 @@ skyrme_status skyrme_flow_host(const skyrme_lattice *lat, double dt, int nsteps,
     CKDEV(state_on_device(st));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t bytes = (size_t)lat->n[0] * lat->n[1] * lat->n[2] * 4 * (lat->precision == 64 ? 8 : 4);
-    CK(cudaMemcpyAsync(st->phi[0], field_in, bytes, cudaMemcpyHostToDevice, s), "upload field");
-    rc = skyrme_load_field(lat, st, stream);
-    if (rc != SKYRME_OK) return rc;
+    // a pinned input is read by the load kernel itself over the host link (the
+    // copy engine moves it no faster), so the upload and the load are one pass;
+    // any other input is copied into phi[0] first
+    const void *direct = nullptr;
+    {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, field_in) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+            at.devicePointer && (reinterpret_cast<uintptr_t>(at.devicePointer) % 32) == 0)
+            direct = at.devicePointer;
+        (void)cudaGetLastError();
+    }
+    if (direct) {
+        FlowArgs l = make_args(*lat, *st, 0.0, MODE_ARRESTED);
+        CK(launch_reset_ctrl(l.ctrl, s), "reset control block");
+        CK(launch_load_finish(*lat, l, s, direct), "load field from host");
+    } else {
+        CK(cudaMemcpyAsync(st->phi[0], field_in, bytes, cudaMemcpyHostToDevice, s), "upload field");
+        rc = skyrme_load_field(lat, st, stream);
+        if (rc != SKYRME_OK) return rc;
+    }
     FlowArgs a = make_args(*lat, *st, dt, mode);
     rc = run_iterations(*lat, a, nsteps, s);
     if (rc != SKYRME_OK) return rc;

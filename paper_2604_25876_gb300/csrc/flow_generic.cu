@@ -460,9 +460,12 @@ template <typename T> __global__ void __launch_bounds__(512, 2) k_fixup(FlowPara
     }
 }
 
-// phi[1] <- phi[0]; outer layers <- vacuum in both; velocities <- 0.
-template <typename T> __global__ void k_load_finish(FlowParams<T> p)
+// phi[1] <- phi[0] (read from src instead when it is given: a caller's field
+// in pinned host memory, read over the host link); outer layers <- vacuum in
+// both; velocities <- 0.
+template <typename T> __global__ void k_load_finish(FlowParams<T> p, const vec4_t<T> *src)
 {
+    const vec4_t<T> *in = src ? src : p.phi[0];
     const size_t total = (size_t)p.n0 * p.n1 * p.n2;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
          i += (size_t)gridDim.x * blockDim.x) {
@@ -471,7 +474,7 @@ template <typename T> __global__ void k_load_finish(FlowParams<T> p)
         const int x = (int)(i / ((size_t)p.n2 * p.n1));
         const bool inner = x >= 2 && x <= p.n0 - 3 && y >= 2 && y <= p.n1 - 3 && z >= 2 &&
                            z <= p.n2 - 3;
-        vec4_t<T> f = inner ? load4<T>(p.phi[0] + i) : make4<T>(T(1), T(0), T(0), T(0));
+        vec4_t<T> f = inner ? load4<T>(in + i) : make4<T>(T(1), T(0), T(0), T(0));
         store4<T>(p.phi[0] + i, f);
         store4<T>(p.phi[1] + i, f);
         store4<T>(p.vel[0] + i, make4<T>(T(0), T(0), T(0), T(0)));
@@ -682,13 +685,16 @@ cudaError_t launch_fixup(const skyrme_lattice &lat, const FlowArgs &a, cudaStrea
     return cudaGetLastError();
 }
 
-cudaError_t launch_load_finish(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s)
+cudaError_t launch_load_finish(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s,
+                               const void *src)
 {
     const size_t total = (size_t)lat.n[0] * lat.n[1] * lat.n[2];
     if (lat.precision == 64)
-        k_load_finish<double><<<pointwise_blocks(total), 256, 0, s>>>(make_params<double>(a, a.step_parts));
+        k_load_finish<double><<<pointwise_blocks(total), 256, 0, s>>>(
+            make_params<double>(a, a.step_parts), static_cast<const vec4_t<double> *>(src));
     else
-        k_load_finish<float><<<pointwise_blocks(total), 256, 0, s>>>(make_params<float>(a, a.step_parts));
+        k_load_finish<float><<<pointwise_blocks(total), 256, 0, s>>>(
+            make_params<float>(a, a.step_parts), static_cast<const vec4_t<float> *>(src));
     return cudaGetLastError();
 }
 

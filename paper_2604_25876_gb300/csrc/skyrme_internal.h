@@ -72,7 +72,9 @@ cudaError_t launch_fixup(const skyrme_lattice &lat, const FlowArgs &a, cudaStrea
 cudaError_t launch_energy(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s);
 cudaError_t launch_forces(const skyrme_lattice &lat, const FlowArgs &a, void *force, void *dens,
                           cudaStream_t s);
-cudaError_t launch_load_finish(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s);
+// src (nullable): a device-accessible copy of the field to read instead of phi[0]
+cudaError_t launch_load_finish(const skyrme_lattice &lat, const FlowArgs &a, cudaStream_t s,
+                               const void *src = nullptr);
 cudaError_t launch_reset_ctrl(void *ctrl, cudaStream_t s);
 // Sum nslabs slab records (8 doubles each, slab order) and run the lattice's
 // end-of-step bookkeeping: arrest decision, predictor, fix flag, buffer flip.
