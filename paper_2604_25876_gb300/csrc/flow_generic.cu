@@ -104,8 +104,8 @@ __device__ __forceinline__ void wait_tile_async()
 // The Section 3 stencils without their 1/h factors (StencilScale carries
 // them): u = 8 (p1 - m1) - (p2 - m2) = 12h d phi; the pure second derivative
 // negated, N = (p2 + m2) + 30 c - 16 (p1 + m1) = -12h^2 dd phi; and the mixed
-// one from the u of the other direction on the same scale,
-// N = -(2/3) (p1 - m1) + (1/12) (p2 - m2).
+// one as the same first-derivative stencil of the u of the other direction,
+// M = 8 (p1 - m1) - (p2 - m2) = 144h^2 d_ij phi = -12 N_ij.
 template <typename T> __device__ __forceinline__ T sd1u(T m2v, T m1v, T p1v, T p2v)
 {
     return fma(T(8), p1v - m1v, m2v - p2v);
@@ -113,10 +113,6 @@ template <typename T> __device__ __forceinline__ T sd1u(T m2v, T m1v, T p1v, T p
 template <typename T> __device__ __forceinline__ T sd2n(T m2v, T m1v, T c, T p1v, T p2v)
 {
     return fma(T(-16), p1v + m1v, fma(T(30), c, p2v + m2v));
-}
-template <typename T> __device__ __forceinline__ T sdmix(T m2v, T m1v, T p1v, T p2v)
-{
-    return fma(T(-2.0 / 3.0), p1v - m1v, T(1.0 / 12.0) * (p2v - m2v));
 }
 template <typename T>
 __device__ __forceinline__ vec4_t<T> sd1uv(const vec4_t<T> &m2v, const vec4_t<T> &m1v,
@@ -203,9 +199,9 @@ __device__ __forceinline__ void tile_derivatives(const vec4_t<T> *tile, const ve
         phi[A] = comp<T>(c, A);
         d1[0][A] = comp<T>(dx0, A);
         d1[1][A] = comp<T>(dy0, A);
-        dm[0][A] = sdmix<T>(comp<T>(xym2, A), comp<T>(xym1, A), comp<T>(xyp1, A), comp<T>(xyp2, A));
-        dm[1][A] = sdmix<T>(comp<T>(xzm2, A), comp<T>(xzm1, A), comp<T>(xzp1, A), comp<T>(xzp2, A));
-        dm[2][A] = sdmix<T>(comp<T>(yzm2, A), comp<T>(yzm1, A), comp<T>(yzp1, A), comp<T>(yzp2, A));
+        dm[0][A] = sd1u<T>(comp<T>(xym2, A), comp<T>(xym1, A), comp<T>(xyp1, A), comp<T>(xyp2, A));
+        dm[1][A] = sd1u<T>(comp<T>(xzm2, A), comp<T>(xzm1, A), comp<T>(xzp1, A), comp<T>(xzp2, A));
+        dm[2][A] = sd1u<T>(comp<T>(yzm2, A), comp<T>(yzm1, A), comp<T>(yzp1, A), comp<T>(yzp2, A));
     }
 }
 

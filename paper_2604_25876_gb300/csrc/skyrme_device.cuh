@@ -200,9 +200,11 @@ __device__ __forceinline__ void extension_terms(const T phi[4], const T d1[3][4]
     const T Q2[4] = {-v[1] * s23 + v[2] * s13 - v[3] * s12, v[0] * s23 - v[2] * s03 + v[3] * s02,
                      -v[0] * s13 + v[1] * s03 - v[3] * s01, v[0] * s12 - v[1] * s02 + v[2] * s01};
     auto dot = [](const T *a, const T *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2] + a[3] * b[3]; };
-    const T dD0 = dot(Q0, d2[0]) + dot(Q1, dm[0]) + dot(Q2, dm[1]);
-    const T dD1 = dot(Q0, dm[0]) + dot(Q1, d2[1]) + dot(Q2, dm[2]);
-    const T dD2 = dot(Q0, dm[1]) + dot(Q1, dm[2]) + dot(Q2, d2[2]);
+    // mixed derivatives arrive as M = -12 N (site_physics)
+    constexpr T kM = T(-1.0 / 12.0);
+    const T dD0 = fma(kM, dot(Q1, dm[0]) + dot(Q2, dm[1]), dot(Q0, d2[0]));
+    const T dD1 = fma(kM, dot(Q0, dm[0]) + dot(Q2, dm[2]), dot(Q1, d2[1]));
+    const T dD2 = fma(kM, dot(Q0, dm[1]) + dot(Q1, dm[2]), dot(Q2, d2[2]));
     const T two_c6 = T(2) * x.c6 * sc.k1sx, four_D = T(4) * D;
 #pragma unroll
     for (int A = 0; A < 4; ++A)
@@ -213,8 +215,8 @@ __device__ __forceinline__ void extension_terms(const T phi[4], const T d1[3][4]
 // ------------------------------------------------------------ site physics
 // Inputs: phi (4) and its derivatives without their 1/h factors (StencilScale):
 // u[i][A] = 12h d_i phi^A, the negated pure second derivatives
-// N2[i][A] = -12h^2 d_ii phi^A and the mixed ones Nm[p][A] = -12h^2 d_p phi^A
-// for p = xy, xz, yz.  Outputs: tangent force F (4) and densities
+// N2[i][A] = -12h^2 d_ii phi^A and the mixed ones M[p][A] = 144h^2 d_p phi^A
+// = -12 N_p for p = xy, xz, yz (the -1/12 rides on factors formed anyway).  Outputs: tangent force F (4) and densities
 // {e2, e4, e0, b}; with EXT the extension terms of `ext` are included (e0 then
 // holds the whole potential) and the sextic density goes to e6.
 // With a_ij = k1^2 A_ij (A_ij = u_i.u_j), d_ij phi = -N_ij / (12h^2) and
@@ -241,11 +243,13 @@ __device__ __forceinline__ void site_physics(const T phi[4], const T d1[3][4], c
         L01[A] = d2[0][A] + d2[1][A];
         L[A] = d2[0][A] + L12[A];
     }
-    const T c0 = dot(dm[0], d1[1]) + dot(dm[1], d1[2]) - dot(L12, d1[0]);
-    const T c1 = dot(dm[0], d1[0]) + dot(dm[2], d1[2]) - dot(L02, d1[1]);
-    const T c2 = dot(dm[1], d1[0]) + dot(dm[2], d1[1]) - dot(L01, d1[2]);
+    constexpr T kM = T(-1.0 / 12.0);  // N_ij = kM M_ij
+    const T c0 = fma(kM, dot(dm[0], d1[1]) + dot(dm[1], d1[2]), -dot(L12, d1[0]));
+    const T c1 = fma(kM, dot(dm[0], d1[0]) + dot(dm[2], d1[2]), -dot(L02, d1[1]));
+    const T c2 = fma(kM, dot(dm[1], d1[0]) + dot(dm[2], d1[1]), -dot(L01, d1[2]));
     const T k_tra = sc.K144 + tra;
-    const T b01 = T(2) * a01, b02 = T(2) * a02, b12 = T(2) * a12;
+    // 2 a_ij for the mixed terms, with kM
+    const T b01 = T(-1.0 / 6.0) * a01, b02 = T(-1.0 / 6.0) * a02, b12 = T(-1.0 / 6.0) * a12;
     const T twoB = T(2) * sc.B;
     T G[4];
 #pragma unroll
