@@ -95,9 +95,12 @@ struct InstDesc {
     // one 64-bit operand.  The kernels carry the derivatives without their
     // 1/(12h), 1/(12h^2) factors: u_i = 12h d_i phi = 8 (p1 - m1) - (p2 - m2),
     // and every second derivative negated on one scale, N_ij = -12h^2 d_ij phi:
-    // the pure ones as (p2 + m2) + 30 c - 16 (p1 + m1), the mixed ones as
-    // -(2/3)(p1 - m1) + (1/12)(p2 - m2) of the u_i (weights the same for every
-    // lattice: kW8 ... kXm2).  The force then comes out as F / B,
+    // the pure ones as (p2 + m2) + 30 c - 16 (p1 + m1), the mixed N_yz (and
+    // N_xy, N_xz in the sextic variant) as -(2/3)(p1 - m1) + (1/12)(p2 - m2)
+    // of the u_i; the other kernels take N_xy, N_xz as -1/12 of the
+    // first-derivative stencil of u_y, u_z along x, the factor applied where
+    // they enter (weights the same for every lattice: kW8 ... kXm2).  The
+    // force then comes out as F / B,
     // B = 1/(1728 h^4); B moves into the time step and the mass terms, and
     // the sums are scaled in the finish.
     float2 dt, dt2;        // dt and 2 dt B
@@ -725,20 +728,31 @@ __device__ __forceinline__ void centre_site(const InstDesc &D, const PlaneVals &
     // are those of the descriptor's stencil weights)
     const P4 dx = fd1u(M2.phi, M1.phi, Q1.phi, Q2.phi, kW8());
     const P4 dxx = fd2n(M2.phi, M1.phi, ph, Q1.phi, Q2.phi, kWm16(), kW30());
-    const P4 dxy = fd1(M2.dy, M1.dy, Q1.dy, Q2.dy, xc1, xc2);
-    const P4 dxz = fd1(zM2, zM1, zQ1, Q2.dz, xc1, xc2);
+    // the mixed derivatives along x: the sextic variant takes them on the
+    // N scale (weights xc1, xc2); the others as the first-derivative
+    // stencil of the u_i, M_xi = 144h^2 d_xi phi = -12 N_xi, with the
+    // factor kS = -1/12 applied where they enter
+    constexpr float kS = SEX ? 1.f : -1.f / 12.f;
+    const P4 dxy = SEX ? fd1(M2.dy, M1.dy, Q1.dy, Q2.dy, xc1, xc2) : fd1u(M2.dy, M1.dy, Q1.dy, Q2.dy, kW8());
+    const P4 dxz = SEX ? fd1(zM2, zM1, zQ1, Q2.dz, xc1, xc2) : fd1u(zM2, zM1, zQ1, Q2.dz, kW8());
     const P4 dyc = C.dy, dzc = zC;
     const float axx = dot(dx, dx), axy = dot(dx, dyc), axz = dot(dx, dzc);
     const float tra = axx + Casum;
     const P4 L = add(dxx, lin);  // -12h^2 Laplacian phi
     // g_i = sum_j d_ij phi.d_j phi and c_i = g_i - Laplacian.d_i phi, both
     // negated; nc_i = -c_i
-    const float gx = hsum(dot2(dxz, dzc, dot2(dxy, dyc, __ffma2_rn(dxx.b, dx.b, __fmul2_rn(dxx.a, dx.a)))));
-    const float gy = dot(dxy, dx) + Cgy;
-    const float gz = dot(dxz, dx) + Cgz;
+    float gx;
+    if constexpr (SEX) {
+        gx = hsum(dot2(dxz, dzc, dot2(dxy, dyc, __ffma2_rn(dxx.b, dx.b, __fmul2_rn(dxx.a, dx.a)))));
+    } else {
+        const float2 gxm = dot2(dxz, dzc, __ffma2_rn(dxy.b, dyc.b, __fmul2_rn(dxy.a, dyc.a)));
+        gx = hsum(__ffma2_rn(bc(kS), gxm, __ffma2_rn(dxx.b, dx.b, __fmul2_rn(dxx.a, dx.a))));
+    }
+    const float gy = fmaf(kS, dot(dxy, dx), Cgy);
+    const float gz = fmaf(kS, dot(dxz, dx), Cgz);
     const float ncx = dot(L, dx) - gx, ncy = dot(L, dyc) - gy, ncz = dot(L, dzc) - gz;
     // -d_ij phi a_ij summed over i, j
-    const P4 Ha = fma(bc(2.f * axz), dxz, fma(bc(2.f * axy), dxy, fma(bc(axx), dxx, qin)));
+    const P4 Ha = fma(bc(2.f * kS * axz), dxz, fma(bc(2.f * kS * axy), dxy, fma(bc(axx), dxx, qin)));
     // brace of the Euler-Lagrange equation / B; G = -2 B (brace + m^2 e_0 / B)
     P4 br = fma(bc(ncz), dzc, fma(bc(ncy), dyc, fma(bc(ncx), dx, fma(bc(D.negK - tra), L, Ha))));
     br.a.x += D.bm2;
