@@ -389,7 +389,9 @@ def run_ours(args, ws, rank, local):
     if rank == 0 and not args.no_extras:
         out["e2e"] = run_e2e(sk, torch, dev, wl, K)
         if prec == 32:
-            out["fp64_gpu"] = run_fp64_compare(sk, torch, dev, wl, K + W, rep, alu["fp64_tflops"])
+            # as many iterations as the FP32 flow ran (warm-up, timed pass and
+            # repeats), so that the two energies are of the same iteration
+            out["fp64_gpu"] = run_fp64_compare(sk, torch, dev, wl, rep["steps"], rep, alu["fp64_tflops"])
         if not wl.extended:
             out["diagnostics"] = run_diagnostics(sk, torch, dev, wl, alu["fp64_tflops"])
             if prec == 32:
