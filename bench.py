@@ -544,11 +544,12 @@ def run_slab_leg(sk, torch, dev, wl, iters, nslabs=2):
             "status": sorted({int(r["status"]) for r in reps})}
 
 
-def run_batched(sk, torch, dev, ws, rank, steps=200):
-    """The batched workload: 64 smoothed-noise lattices with sides drawn from
-    {64,...,128}, sharded over the ranks, one persistent launch per iteration
-    replayed from a CUDA graph after the autotuner has chosen the tile."""
-    wls = workloads.batched_noise(count=64, steps=steps)
+def run_batched(sk, torch, dev, ws, rank, steps=200, count=64):
+    """The batched workload: `count` (64) smoothed-noise lattices with sides
+    drawn from {64,...,128}, sharded over the ranks, one persistent launch per
+    iteration replayed from a CUDA graph after the autotuner has chosen the
+    tile."""
+    wls = workloads.batched_noise(count=count, steps=steps)
     mine = [wls[i] for i in shard_indices(len(wls), rank, ws)]
     lats, states = [], []
     for w in mine:
@@ -899,6 +900,9 @@ def main():
                     help="extra passes of the K timed iterations, reported as a spread")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the e2e, FP64 and CPU-baseline legs")
+    ap.add_argument("--batched-only", type=int, default=0, metavar="COUNT",
+                    help="run only the batched leg, on COUNT lattices for --steps iterations "
+                         "(a smaller batch for profiling); prints its record")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -914,7 +918,17 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    out = run_ours(args, ws, rank, local)
+    if args.batched_only > 0:
+        import torch
+
+        import paper_2604_25876_gb300 as sk
+        dev = torch.device("cuda", local)
+        torch.cuda.set_device(dev)
+        sk.load()
+        out = run_batched(sk, torch, dev, ws, rank, steps=max(100, args.steps // 100 * 100),
+                          count=args.batched_only)
+    else:
+        out = run_ours(args, ws, rank, local)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if ws > 1:
