@@ -96,3 +96,12 @@ def test_fingerprints_ignore_comments_and_layout_but_not_code():
     assert bench.source_code_only(code) == bench.source_code_only(
         "/* a block\n comment */ int f(int a)\n{ return a + 1; }")
     assert bench.source_code_only(code) != bench.source_code_only(code.replace("+ 1", "+ 2"))
+
+
+def test_a_smaller_batch_is_the_head_of_the_batched_recipe():
+    """`bench.py --batched-only COUNT` (a batch for profiling) runs the first
+    COUNT lattices of the 64-lattice recipe, so its profile describes the
+    same size mix."""
+    head = [(w.n, w.seed, w.dt) for w in workloads.batched_noise(count=16, steps=200)]
+    full = [(w.n, w.seed, w.dt) for w in workloads.batched_noise(count=64, steps=200)]
+    assert head == full[:16]
