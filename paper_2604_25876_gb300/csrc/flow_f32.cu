@@ -1918,7 +1918,7 @@ static std::atomic<int> g_single_split{SKYRME_SPLIT_AUTO};
 // `policy`; *ctas receives the CTAs to launch.  AUTO takes the balanced
 // split: the lockstep schedule cuts the DRAM traffic (1.31x -> 1.02x of the
 // algorithmic bytes on 256^3) but measured slower wherever the step is not
-// L2-resident (256^3: 57.1 against 58.2, 512^3: 61.5 against 63.3
+// L2-resident (256^3: 57.8 against 59.4, 512^3: 62.2 against 64.3
 // Gsite-updates/s), and equal on 128^3.  Cached for the last geometry and
 // policy.
 static void plan_single(long long units, int nix, int grid, int policy, CtaSplit &out, int *ctas)
